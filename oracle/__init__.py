@@ -1,0 +1,205 @@
+"""CPU oracle for the shuffle + inner hash join (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (``libmdj.so`` and its
+Python binding) never does, and it shares no code with it.
+
+The arithmetic lives in ``oracle.c`` (plain C, compiled with gcc into
+``liboracle.so`` next to it); this module only marshals numpy arrays, plus one
+independent nested-loop join (``brute_force``) used to pin the C sort-merge on
+tiny inputs.  What each function computes is the plain definition of the
+operation named in Sec. V-B ("cuDF Merge", Fig. 8 and Fig. 9(b,c)) of the
+paper: a hash-partitioned shuffle followed by an inner equi-join.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so with gcc (portable flags only)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _SRC, "-o", tmp])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        u64, u32, i32, vp = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_void_p
+        lib.oracle_fmix64.restype = u64
+        lib.oracle_fmix64.argtypes = [u64]
+        lib.oracle_partition_of.restype = u32
+        lib.oracle_partition_of.argtypes = [ctypes.c_int64, u32]
+        lib.oracle_partition.restype = i32
+        lib.oracle_partition.argtypes = [vp, i32, u64, u32, vp, vp]
+        lib.oracle_merge.restype = i32
+        lib.oracle_merge.argtypes = [vp, u64, vp, u64, i32, vp, vp, u64, ctypes.POINTER(u64)]
+        lib.oracle_count_checksum.restype = i32
+        lib.oracle_count_checksum.argtypes = [vp, vp, i32, u64, vp, vp, i32, u64, i32,
+                                              ctypes.POINTER(u64), ctypes.POINTER(u64)]
+        lib.oracle_fmix64_array.restype = None
+        lib.oracle_fmix64_array.argtypes = [vp, u64, vp]
+        lib.oracle_partition_ids.restype = None
+        lib.oracle_partition_ids.argtypes = [vp, i32, u64, u32, vp]
+        lib.oracle_checksum_terms.restype = None
+        lib.oracle_checksum_terms.argtypes = [vp, i32, vp, i32, u64, vp, i32, u64, vp, vp]
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _key_array(keys) -> np.ndarray:
+    keys = np.ascontiguousarray(keys)
+    if keys.dtype not in (np.int32, np.int64):
+        raise TypeError(f"oracle keys must be int32 or int64, got {keys.dtype}")
+    return keys
+
+
+def _bits(pay) -> np.ndarray:
+    pay = np.ascontiguousarray(pay)
+    if pay.dtype.itemsize == 4:
+        return pay.view(np.uint32)
+    if pay.dtype.itemsize == 8:
+        return pay.view(np.uint64)
+    raise TypeError(f"payload width must be 4 or 8 bytes, got {pay.dtype}")
+
+
+# ----------------------------------------------------------------- hashing
+
+def fmix64(x: np.ndarray) -> np.ndarray:
+    """MurmurHash3 64-bit finalizer applied elementwise (uint64 in, uint64 out)."""
+    x = np.ascontiguousarray(x, dtype=np.uint64)
+    out = np.empty_like(x)
+    _load().oracle_fmix64_array(_ptr(x), x.size, _ptr(out))
+    return out
+
+
+def partition_ids(keys, P: int) -> np.ndarray:
+    """p = fmix64(sext64(key)) mod P for every key (uint32)."""
+    keys = _key_array(keys)
+    out = np.empty(keys.size, dtype=np.uint32)
+    _load().oracle_partition_ids(_ptr(keys), keys.dtype.itemsize, keys.size, P, _ptr(out))
+    return out
+
+
+# --------------------------------------------------------------- partition
+
+def partition(keys, P: int):
+    """Stable hash partition: returns (offsets int64[P+1], perm uint32[n])."""
+    keys = _key_array(keys)
+    offsets = np.empty(P + 1, dtype=np.int64)
+    perm = np.empty(keys.size, dtype=np.uint32)
+    rc = _load().oracle_partition(_ptr(keys), keys.dtype.itemsize, keys.size, P,
+                                  _ptr(offsets), _ptr(perm))
+    if rc != 0:
+        raise ValueError("oracle_partition failed")
+    return offsets, perm
+
+
+def partition_table(cols, key_col: int, P: int):
+    """Stable partition of a whole table (list of 1-D arrays).
+
+    Returns (offsets, row_ids, partitioned columns): column j of the output is
+    the input column gathered by row_ids.
+    """
+    offsets, perm = partition(cols[key_col], P)
+    return offsets, perm, [np.ascontiguousarray(np.asarray(c)[perm]) for c in cols]
+
+
+# ------------------------------------------------------------------- merge
+
+def merge_pairs(lkeys, rkeys):
+    """Inner equi-join row pairs (lrow, rrow), canonical order (key, lrow, rrow)."""
+    lkeys, rkeys = _key_array(lkeys), _key_array(rkeys)
+    if lkeys.dtype != rkeys.dtype:
+        raise TypeError("left and right key columns must have the same dtype")
+    lib = _load()
+    m = ctypes.c_uint64(0)
+    dummy = np.empty(1, dtype=np.uint32)
+    rc = lib.oracle_merge(_ptr(lkeys), lkeys.size, _ptr(rkeys), rkeys.size,
+                          lkeys.dtype.itemsize, _ptr(dummy), _ptr(dummy), 0, ctypes.byref(m))
+    if rc != 0:
+        raise ValueError("oracle_merge failed")
+    lrow = np.empty(m.value, dtype=np.uint32)
+    rrow = np.empty(m.value, dtype=np.uint32)
+    rc = lib.oracle_merge(_ptr(lkeys), lkeys.size, _ptr(rkeys), rkeys.size,
+                          lkeys.dtype.itemsize, _ptr(lrow), _ptr(rrow), m.value, ctypes.byref(m))
+    if rc != 0:
+        raise ValueError("oracle_merge failed")
+    return lrow, rrow
+
+
+def merge_table(left_cols, right_cols, key_col_l: int = 0, key_col_r: int = 0):
+    """The full merge result in canonical order.
+
+    Output schema: key, left_row, right_row, then the left non-key columns in
+    order, then the right non-key columns in order (values gathered, bits
+    preserved).
+    """
+    lrow, rrow = merge_pairs(left_cols[key_col_l], right_cols[key_col_r])
+    lk = np.asarray(left_cols[key_col_l])
+    return {
+        "key": lk[lrow],
+        "left_row": lrow,
+        "right_row": rrow,
+        "left_cols": [np.asarray(c)[lrow] for j, c in enumerate(left_cols) if j != key_col_l],
+        "right_cols": [np.asarray(c)[rrow] for j, c in enumerate(right_cols) if j != key_col_r],
+    }
+
+
+def brute_force(lkeys, rkeys):
+    """Nested-loop inner join (independent of the C code) for tiny inputs.
+
+    Every (i, j) with lkeys[i] == rkeys[j], sorted by (key, i, j).
+    """
+    lk = np.asarray(lkeys).astype(np.int64)
+    rk = np.asarray(rkeys).astype(np.int64)
+    if lk.size * rk.size > 50_000_000:
+        raise ValueError("brute_force is for tiny inputs only")
+    li, rj = np.nonzero(lk[:, None] == rk[None, :])
+    order = np.lexsort((rj, li, lk[li]))
+    return li[order].astype(np.uint32), rj[order].astype(np.uint32)
+
+
+# ------------------------------------------------------- count + checksum
+
+def checksum_terms(lkeys, lpay, rpay):
+    """Per-row checksum terms f(l) (left) and g(r) (right), uint64."""
+    lkeys = _key_array(lkeys)
+    lb, rb = _bits(lpay), _bits(rpay)
+    f = np.empty(lkeys.size, dtype=np.uint64)
+    g = np.empty(rb.size, dtype=np.uint64)
+    _load().oracle_checksum_terms(_ptr(lkeys), lkeys.dtype.itemsize, _ptr(lb), lb.dtype.itemsize,
+                                  lkeys.size, _ptr(rb), rb.dtype.itemsize, rb.size, _ptr(f), _ptr(g))
+    return f, g
+
+
+def count_checksum(lkeys, lpay, rkeys, rpay):
+    """(pair count, sum over pairs of f(l)*g(r) mod 2^64), by key groups."""
+    lkeys, rkeys = _key_array(lkeys), _key_array(rkeys)
+    if lkeys.dtype != rkeys.dtype:
+        raise TypeError("left and right key columns must have the same dtype")
+    lb, rb = _bits(lpay), _bits(rpay)
+    cnt, chk = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    rc = _load().oracle_count_checksum(_ptr(lkeys), _ptr(lb), lb.dtype.itemsize, lkeys.size,
+                                       _ptr(rkeys), _ptr(rb), rb.dtype.itemsize, rkeys.size,
+                                       lkeys.dtype.itemsize, ctypes.byref(cnt), ctypes.byref(chk))
+    if rc != 0:
+        raise ValueError("oracle_count_checksum failed")
+    return cnt.value, chk.value

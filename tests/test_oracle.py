@@ -1,0 +1,228 @@
+"""Pins for the CPU oracle, against facts that do not come from the oracle itself.
+
+The paper prints no output values for the merge (all its plots are figures,
+Sec. V-B/V-C), so the oracle is pinned by: a hand-worked example, an
+independent nested-loop join on tiny inputs, the closed form of the
+match-fraction generator, the count identity m = sum_k lc(k) rc(k), explicit
+pair enumeration for the checksum, partition invariants, and the data volumes
+the paper states per worker.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2101_08878_gb300 import datagen
+
+I64_MIN = np.iinfo(np.int64).min
+I64_MAX = np.iinfo(np.int64).max
+
+
+# ------------------------------------------------------------------ hashing
+
+def test_fmix64_fixes_zero():
+    # Every step of the finalizer (xor-shift, odd multiply) maps 0 to 0; a
+    # stray added constant or a wrong seed would not.
+    assert int(oracle.fmix64(np.zeros(1, np.uint64))[0]) == 0
+
+
+def test_fmix64_is_a_bijection_on_a_sample():
+    # fmix64 is a composition of invertible maps, so distinct inputs never collide.
+    rng = np.random.default_rng(1)
+    x = np.unique(np.concatenate([np.arange(1 << 20, dtype=np.uint64),
+                                  rng.integers(0, 2**64 - 1, 1 << 20, dtype=np.uint64, endpoint=True)]))
+    y = oracle.fmix64(x)
+    assert np.unique(y).size == x.size
+
+
+def test_fmix64_avalanche():
+    # Strict avalanche: flipping any input bit flips each output bit with
+    # probability ~1/2.  A dropped xor-shift or multiply breaks this badly.
+    rng = np.random.default_rng(2)
+    x = rng.integers(0, 2**64 - 1, 4000, dtype=np.uint64, endpoint=True)
+    hx = oracle.fmix64(x)
+    worst = 0.0
+    for bit in range(64):
+        d = hx ^ oracle.fmix64(x ^ np.uint64(1 << bit))
+        bits = np.unpackbits(d.view(np.uint8).reshape(-1, 8), axis=1)
+        p = bits.mean(axis=0)
+        worst = max(worst, float(np.abs(p - 0.5).max()))
+    assert worst < 0.06, worst
+
+
+def test_partition_ids_sign_extend_int32():
+    # int32 and int64 columns holding equal values must hash to equal partitions.
+    v = np.array([-5, -1, 0, 1, 7, 2**31 - 1, -(2**31)], dtype=np.int64)
+    for P in (1, 2, 8, 37, 65536):
+        assert np.array_equal(oracle.partition_ids(v, P), oracle.partition_ids(v.astype(np.int32), P))
+
+
+def test_partition_ids_uniform():
+    n, P = 1_000_000, 8
+    c = np.bincount(oracle.partition_ids(np.arange(n, dtype=np.int64), P), minlength=P)
+    sigma = math.sqrt(n * (1 / P) * (1 - 1 / P))
+    assert np.all(np.abs(c - n / P) < 5 * sigma), c
+
+
+def test_partition_power_of_two_uses_low_bits():
+    # For P = 2^k, h mod P is the low k bits of h.
+    keys = np.arange(-1000, 1000, dtype=np.int64)
+    h = oracle.fmix64(keys.view(np.uint64))
+    for k in (1, 3, 10, 16):
+        assert np.array_equal(oracle.partition_ids(keys, 1 << k), (h & np.uint64((1 << k) - 1)).astype(np.uint32))
+
+
+# ---------------------------------------------------------------- partition
+
+@pytest.mark.parametrize("P", [1, 2, 3, 8, 64, 1000, 65536])
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
+def test_partition_invariants(P, dtype):
+    rng = np.random.default_rng(P)
+    n = 20_000
+    keys = rng.integers(-50_000, 50_000, n).astype(dtype)
+    offsets, perm = oracle.partition(keys, P)
+    pid = oracle.partition_ids(keys, P)
+    # a permutation of 0..n-1
+    assert np.array_equal(np.sort(perm), np.arange(n, dtype=np.uint32))
+    # offsets are the exclusive prefix sum of the partition sizes
+    assert offsets[0] == 0 and offsets[-1] == n
+    assert np.array_equal(np.diff(offsets), np.bincount(pid, minlength=P))
+    for p in range(min(P, 70)):
+        seg = perm[offsets[p]:offsets[p + 1]]
+        assert np.all(pid[seg] == p)
+        assert np.all(np.diff(seg.astype(np.int64)) > 0)  # stable: input order kept
+
+
+def test_partition_empty_and_single():
+    off, perm = oracle.partition(np.zeros(0, np.int64), 4)
+    assert list(off) == [0, 0, 0, 0, 0] and perm.size == 0
+    off, perm = oracle.partition(np.array([42], np.int64), 1)
+    assert list(off) == [0, 1] and list(perm) == [0]
+
+
+def test_partition_table_gathers_columns():
+    keys = np.array([5, 9, 5, 1, 9, 9], np.int64)
+    pay = np.arange(6, dtype=np.float64) / 10
+    off, rid, (pk, pp) = oracle.partition_table([keys, pay], 0, 3)
+    assert np.array_equal(pk, keys[rid]) and np.array_equal(pp.view(np.uint64), pay[rid].view(np.uint64))
+
+
+# -------------------------------------------------------------------- merge
+
+def test_merge_hand_worked_example():
+    # left  rows: 0:k3 1:k1 2:k3 3:k7      right rows: 0:k3 1:k3 2:k9 3:k1
+    # pairs by key: k1 -> (1,3); k3 -> (0,0) (0,1) (2,0) (2,1); k7, k9 unmatched.
+    l = np.array([3, 1, 3, 7], np.int64)
+    r = np.array([3, 3, 9, 1], np.int64)
+    lrow, rrow = oracle.merge_pairs(l, r)
+    assert list(zip(lrow.tolist(), rrow.tolist())) == [(1, 3), (0, 0), (0, 1), (2, 0), (2, 1)]
+
+
+CASES = [
+    # (n_l, n_r, key_range, dtype, seed)
+    (0, 0, 10, np.int64, 0),
+    (0, 50, 10, np.int64, 1),
+    (50, 0, 10, np.int64, 2),
+    (1, 1, 1, np.int64, 3),
+    (300, 400, 50, np.int64, 4),      # heavy duplicates
+    (1000, 1000, 5, np.int32, 5),     # very heavy duplicates
+    (2000, 1500, 100_000, np.int64, 6),
+    (2000, 2000, 3000, np.int32, 7),
+]
+
+
+@pytest.mark.parametrize("n_l,n_r,key_range,dtype,seed", CASES)
+def test_merge_matches_brute_force(n_l, n_r, key_range, dtype, seed):
+    (lk, _), (rk, _) = datagen.random_tables(n_l, n_r, key_range, seed, key_dtype=dtype)
+    got = oracle.merge_pairs(lk, rk)
+    want = oracle.brute_force(lk, rk)
+    assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+
+
+def test_merge_extreme_keys():
+    ext = np.array([I64_MIN, I64_MAX, 0, -1, I64_MIN, I64_MAX, I64_MIN + 1], np.int64)
+    r = np.array([I64_MAX, I64_MIN, I64_MIN, 5, -1, I64_MAX - 1], np.int64)
+    got = oracle.merge_pairs(ext, r)
+    want = oracle.brute_force(ext, r)
+    assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+    assert got[0].size == 2 * 2 + 2 * 1 + 1  # INT64_MIN: 2x2, INT64_MAX: 2x1, -1: 1x1
+
+
+def test_merge_count_identity():
+    # m = sum over keys of lc(k) * rc(k), counted with np.unique (no join).
+    (lk, _), (rk, _) = datagen.zipf_tables(20_000, 30_000, 2_000, 1.1, seed=9)
+    lu, lc = np.unique(lk, return_counts=True)
+    ru, rc = np.unique(rk, return_counts=True)
+    common, li, ri = np.intersect1d(lu, ru, return_indices=True)
+    m = int(np.sum(lc[li].astype(np.int64) * rc[ri].astype(np.int64)))
+    lrow, rrow = oracle.merge_pairs(lk, rk)
+    assert lrow.size == m
+    assert np.array_equal(lk[lrow], rk[rrow])
+
+
+@pytest.mark.parametrize("n_l,n_r,frac", [(1000, 1000, 0.3), (10_000, 25_000, 0.3), (5000, 3000, 0.9), (100, 100, 0.0)])
+def test_merge_closed_form_match_fraction(n_l, n_r, frac):
+    (lk, _), (rk, _) = datagen.match_fraction_tables(n_l, n_r, frac, seed=n_l + n_r)
+    lrow, rrow = oracle.merge_pairs(lk, rk)
+    assert lrow.size == math.floor(frac * n_r)
+    assert np.array_equal(lk[lrow], rk[rrow])
+    assert np.unique(rrow).size == rrow.size  # each right row meets one left row
+
+
+def test_merge_table_schema_and_bits():
+    (lk, lp), (rk, rp) = datagen.match_fraction_tables(500, 700, 0.5, seed=3)
+    # NaN payload bit patterns must survive untouched
+    lp = lp.copy()
+    lp.view(np.uint64)[::7] = np.uint64(0x7FF8DEADBEEF0001)
+    res = oracle.merge_table([lk, lp], [rk, rp])
+    assert np.array_equal(res["key"], lk[res["left_row"]])
+    assert np.array_equal(res["left_cols"][0].view(np.uint64), lp.view(np.uint64)[res["left_row"]])
+    assert np.array_equal(res["right_cols"][0].view(np.uint64), rp.view(np.uint64)[res["right_row"]])
+
+
+def test_merge_key_dtype_mismatch_rejected():
+    with pytest.raises(TypeError):
+        oracle.merge_pairs(np.zeros(3, np.int32), np.zeros(3, np.int64))
+
+
+# ----------------------------------------------------------- count/checksum
+
+@pytest.mark.parametrize("seed,dup", [(0, 50), (1, 5), (2, 100_000)])
+@pytest.mark.parametrize("pay", [np.float64, np.float32])
+def test_count_checksum_equals_pair_enumeration(seed, dup, pay):
+    (lk, lp), (rk, rp) = datagen.random_tables(700, 900, dup, seed, pay_dtype=pay)
+    cnt, chk = oracle.count_checksum(lk, lp, rk, rp)
+    li, rj = oracle.brute_force(lk, rk)
+    f, g = oracle.checksum_terms(lk, lp, rp)
+    mask = (1 << 64) - 1
+    want = 0
+    for a, b in zip(li.tolist(), rj.tolist()):
+        want = (want + int(f[a]) * int(g[b])) & mask
+    assert cnt == li.size
+    assert chk == want
+
+
+def test_checksum_terms_depend_on_every_field():
+    # f must change with the key, the left row and the payload bits; g with the
+    # right row and its payload bits (a dropped term would leave one fixed).
+    lk = np.array([1, 2, 1], np.int64)
+    lp = np.array([0.5, 0.5, 0.25])
+    rp = np.array([0.5, 0.25, 0.5])
+    f, g = oracle.checksum_terms(lk, lp, rp)
+    assert len(set(f.tolist())) == 3 and len(set(g.tolist())) == 3
+    f2, _ = oracle.checksum_terms(lk, lp + 1.0, rp)
+    assert not np.any(f2 == f)
+
+
+# --------------------------------------------------------- paper arithmetic
+
+def test_data_volume_matches_paper():
+    # Sec. V-B: 3.2 GB per worker at chunk size 1E8; Sec. V-C: 1.6 GB per GPU
+    # at 5E7 and 51.2 GB on 32 GPUs.  Reading: rows per table per worker, one
+    # 8-byte key + one 8-byte payload, two tables.
+    per_row = np.dtype(np.int64).itemsize + np.dtype(np.float64).itemsize
+    assert 1e8 * per_row * 2 == 3.2e9
+    assert 5e7 * per_row * 2 == 1.6e9
+    assert 32 * 5e7 * per_row * 2 == 51.2e9
+    assert [k * 3.2 for k in range(1, 7)] == pytest.approx([3.2, 6.4, 9.6, 12.8, 16.0, 19.2])
