@@ -1,0 +1,372 @@
+"""Benchmark of the shuffle + merge hot path on GB300.
+
+Workload: the plain shuffle + merge that emulates 8 workers of the paper's
+cuDF merge benchmark (Sec. V-B, Fig. 8: chunk size 1E8, shuffle, fraction
+match 0.3): P = 8 hash partitions, 100M left rows (int64 key = seeded
+permutation, float64 payload U[0,1)) and 100M right rows (30% of keys drawn
+from the left keys), synthetic data.  One step = one mdj_merge call: partition
+both tables, join every partition pair, read the output count back, write the
+joined rows.  Inputs (3.2 GB) are far larger than L2, so no flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mdj|reference]
+
+Prints one JSON line.  With N > 1 (launched by torchrun) every rank runs an
+independent replica on its own GPU (the path has no exchange between GPUs);
+value = all rows merged by all ranks / max-over-ranks time.
+The reference arm (--impl reference) times the CPU oracle (shuffle by a stable
+counting sort, then a sort-merge join per partition pair) on a bounded sample
+of the same workload, on this host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2101_08878_gb300 import datagen  # noqa: E402
+
+METRIC = "merge input rows/s & HBM-roofline %, batched vs plain; p50/p99 join latency"
+UNIT = "rows/s"
+N_LEFT = N_RIGHT = 100_000_000
+P = 8
+FRAC = 0.3
+SEED = 1
+WORKLOAD = "plain shuffle+merge, P=8 hash partitions, 100M x 100M rows, int64 key + float64 payload, match 0.3"
+
+# algorithmic bytes per row of each kernel (8-byte keys and payloads, 4-byte row ids)
+KEY, PAY, RID, OUT_ROW = 8, 8, 4, 32
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples taken while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        self.file = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.file.close()
+
+    def summary(self):
+        try:
+            lines = [ln.strip() for ln in open(self.file.name) if ln.strip()]
+            os.unlink(self.file.name)
+        except OSError:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU baseline
+
+def oracle_step(left, right, p):
+    """The CPU oracle as it stands: stable hash partition of both tables (the
+    shuffle), then a sort-merge inner join of every partition pair."""
+    import oracle
+    loff, _, lparts = oracle.partition_table(left, 0, p)
+    roff, _, rparts = oracle.partition_table(right, 0, p)
+    rows = 0
+    for q in range(p):
+        ls = [c[loff[q]:loff[q + 1]] for c in lparts]
+        rs = [c[roff[q]:roff[q + 1]] for c in rparts]
+        rows += oracle.merge_table(ls, rs)["key"].size
+    return rows
+
+
+def cpu_baseline(n_sample: int, reps: int = 1):
+    (lk, lp), (rk, rp) = datagen.match_fraction_tables(n_sample, n_sample, FRAC, seed=SEED + 1000)
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        m = oracle_step([lk, lp], [rk, rp], P)
+    dt = (time.perf_counter() - t0) / reps
+    assert m == math.floor(FRAC * n_sample)
+    return {"value": 2 * n_sample / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n_sample} x {n_sample} rows of the same generator (seed {SEED + 1000}), P={P}: "
+                      f"stable partition of both sides + sort-merge per partition, single thread, "
+                      f"{dt:.2f} s per merge"}
+
+
+# --------------------------------------------------------------- GPU arm
+
+ALG_BYTES_PER_ROW = {
+    # kernel: bytes the method must move per input row of one side
+    "hist": KEY,                                  # read keys
+    "scatter_stable": (KEY + PAY) + (KEY + PAY + RID),  # read row, write row + row id
+    "scatter_reserve": (KEY + PAY + RID) * 2,     # second level: read + write row and row id
+    "join_count": KEY,                            # read keys (build or probe side)
+}
+
+
+def run_gpu(args):
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2101_08878_gb300 import mdj
+
+    (lk, lp), (rk, rp) = datagen.match_fraction_tables(N_LEFT, N_RIGHT, FRAC, seed=SEED + rank)
+    left = [torch.from_numpy(lk).to(dev), torch.from_numpy(lp).to(dev)]
+    right = [torch.from_numpy(rk).to(dev), torch.from_numpy(rp).to(dev)]
+    m_expect = math.floor(FRAC * N_RIGHT)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def step():
+        res = mdj.mdj_merge(left, right, P)
+        assert res.nrows == m_expect, res.nrows
+        return res
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    mdj.profile_reset()
+    mdj.profile_enable(True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            res = step()
+            del res
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    mdj.profile_enable(False)
+    prof = mdj.profile_collect()
+    ms_total = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    rows_step = (N_LEFT + N_RIGHT) * world
+    value = rows_step / (ms_step / 1e3)
+
+    # ---- roofline: dominant kernel by total device time inside the timed region
+    peak, peak_kind = peaks()
+    launches = sum(v[0] for v in prof.values())
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    dom_name, (dom_launches, dom_ms) = dom
+    per_launch_ms = dom_ms / max(dom_launches, 1)
+    per_row = ALG_BYTES_PER_ROW.get(dom_name)
+    achieved = per_row * N_LEFT / (per_launch_ms / 1e3) / 1e9 if per_row else None
+    traffic = measured_traffic(dom_name)
+    b_alg_step = 64 * (N_LEFT + N_RIGHT) + OUT_ROW * m_expect
+    roofline = {
+        "bound": "hbm", "kernel": dom_name, "achieved": round(achieved, 1) if achieved else None,
+        "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None,
+        "traffic": traffic, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+        else "fallback 6800 GB/s", "launch_ms": round(per_launch_ms, 4),
+        "alg_bytes_per_launch": per_row * N_LEFT if per_row else None,
+    }
+    step_roof = {"alg_bytes": b_alg_step, "achieved_gbs": round(b_alg_step / (ms_step / 1e3) / 1e9, 1),
+                 "frac": round(b_alg_step / (ms_step / 1e3) / 1e9 / peak, 4)}
+    kernels = {k: {"launches": v[0], "ms_per_step": round(v[1] / args.steps, 4),
+                   "share": round(v[1] / max(sum(x[1] for x in prof.values()), 1e-9), 4)}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+
+    # ---- end to end: host (pinned) inputs -> device -> merge -> host result
+    e2e = None
+    if args.e2e_steps > 0:
+        hl = [torch.from_numpy(lk).pin_memory(), torch.from_numpy(lp).pin_memory()]
+        hr = [torch.from_numpy(rk).pin_memory(), torch.from_numpy(rp).pin_memory()]
+        del left[:], right[:]
+        torch.cuda.empty_cache()
+        out, h2d, d2h = mdj.merge_host(hl, hr, P)  # warm
+        del out
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            out, h2d, d2h = mdj.merge_host(hl, hr, P)
+            assert out.nrows == m_expect
+            del out
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.e2e_steps
+        if dist is not None:
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": rows_step / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": round(dt * 1e3, 3), "steps": args.e2e_steps}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_left": N_LEFT, "n_right": N_RIGHT, "P": P, "match_fraction": FRAC,
+                   "output_rows": m_expect, "seed": SEED, "l2": "inputs (3.2 GB) larger than L2; no flush",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline, "step_roofline": step_roof, "kernels": kernels, "gpu_launches": launches,
+        "e2e": e2e, "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_sample)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def measured_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from a committed ncu summary, if the
+    kernel source is unchanged since the capture (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    src = os.path.join(ROOT, "paper_2101_08878_gb300", "csrc")
+    try:
+        rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    except OSError:
+        return None
+    for r in rows:
+        kv = dict(x.split("=", 1) for x in r if "=" in x)
+        if kv.get("kernel") != kernel:
+            continue
+        h = hashlib.sha256(open(os.path.join(src, kv["file"]), "rb").read()).hexdigest()[:16]
+        if h != kv.get("src_sha"):
+            return None
+        return int(float(kv["bytes_per_row"]) * N_LEFT)
+    return None
+
+
+# ---------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return  # the CPU oracle runs once, on rank 0
+    import oracle
+    oracle.build()
+    n = args.ref_sample
+    (lk, lp), (rk, rp) = datagen.match_fraction_tables(n, n, FRAC, seed=SEED + 1000)
+    for _ in range(args.warmup):
+        oracle_step([lk, lp], [rk, rp], P)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        m = oracle_step([lk, lp], [rk, rp], P)
+    dt = (time.perf_counter() - t0) / args.steps
+    assert m == math.floor(FRAC * n)
+    value = 2 * n / dt
+    sample = (f"{n} x {n} rows per step of the same generator (seed {SEED + 1000}), P={P}: stable partition "
+              f"of both sides + sort-merge per partition, single thread")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get(
+            "WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_left": N_LEFT, "n_right": N_RIGHT, "P": P, "match_fraction": FRAC,
+                   "sample_rows_per_side": n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mdj", choices=["mdj", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-sample", type=int, default=10_000_000)
+    ap.add_argument("--ref-sample", type=int, default=2_000_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "mdj":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,205 @@
+/*
+ * mdj.h - C ABI of libmdj.so: a GB300 (sm_103a) hash-partitioned shuffle and
+ * inner hash join of two key/payload tables.
+ *
+ * What the calls compute comes from the cuDF merge workload of arXiv 2101.08878
+ * (Sec. V-B "cuDF Merge", Fig. 8, and Sec. V-C, Fig. 9(b,c)): tables are
+ * repartitioned by key hash ("Shuffle: True") so that equal keys meet in one
+ * partition, then each partition pair is merged.  The paper moves partitions
+ * between Dask workers over MPI (Sec. IV-B, the Isend/Irecv coroutines); on one
+ * GPU that exchange is the on-device scatter done by mdj_partition, and the
+ * partition region p in device memory plays worker p's receive buffer.  The
+ * paper names no hash, join algorithm or output layout; the readings below are
+ * this library's contract.
+ *
+ * Conventions shared by every call:
+ *  - Pointers inside mdj_col / output arrays are DEVICE pointers of the current
+ *    CUDA device; structs passed by pointer (mdj_table, mdj_result, ...) live in
+ *    HOST memory.  Input columns are read-only and remain owned by the caller.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Every call is asynchronous on that stream, except mdj_join / mdj_merge /
+ *    mdj_count_checksum, which read one small count back to the host (one
+ *    stream synchronisation) before sizing their outputs.
+ *  - Workspace and join outputs come from the caller's allocator (mdj_allocator);
+ *    a NULL allocator means cudaMallocAsync / cudaFreeAsync on `stream`.
+ *  - Keys are signed integers (MDJ_I32 or MDJ_I64); both sides of a join must use
+ *    the same key dtype.  Every other column is a payload of width 4 or 8 bytes
+ *    whose bits are copied, never interpreted (NaN patterns survive).
+ *  - Row counts must be < 2^32 (row ids are uint32); larger inputs give
+ *    MDJ_ERR_TOO_LARGE.  Output counts and offsets are 64-bit.
+ *  - Hash: h = fmix64((uint64)(int64)key), the 64-bit finalizer of MurmurHash3;
+ *    partition p = h mod P (unsigned).  int32 and int64 keys with equal values
+ *    land in the same partition.
+ *  - Return value: MDJ_OK (0) or a negative mdj_status.  On error no output
+ *    buffer is left allocated and the caller's buffers hold unspecified data.
+ */
+#ifndef MDJ_H
+#define MDJ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define MDJ_API __attribute__((visibility("default")))
+#else
+#define MDJ_API
+#endif
+
+#define MDJ_VERSION 1
+#define MDJ_MAX_COLS 16      /* columns per table, key included */
+#define MDJ_MAX_PARTITIONS 65536u
+
+typedef enum {
+    MDJ_OK = 0,
+    MDJ_ERR_INVALID_ARG = -1,       /* null pointer, P == 0 or > 65536, bad key index, key dtype mismatch */
+    MDJ_ERR_UNSUPPORTED_DTYPE = -2, /* key not I32/I64, or a column of unknown dtype */
+    MDJ_ERR_TOO_LARGE = -3,         /* nrows >= 2^32 */
+    MDJ_ERR_OOM = -4,               /* the allocator returned NULL */
+    MDJ_ERR_CUDA = -5,              /* a CUDA runtime call failed */
+    MDJ_ERR_DEVICE_TIMEOUT = -6,    /* a bounded device-side wait gave up */
+    MDJ_ERR_INTERNAL = -7           /* a device-side consistency check failed */
+} mdj_status;
+
+typedef enum {
+    MDJ_I32 = 1,
+    MDJ_I64 = 2,
+    MDJ_F32 = 3,
+    MDJ_F64 = 4,
+    MDJ_U32 = 5,
+    MDJ_U64 = 6
+} mdj_dtype;
+
+/* One column: `data` is a device pointer to nrows elements of `dtype`. */
+typedef struct {
+    const void *data;
+    int32_t dtype;
+} mdj_col;
+
+/* A table: `ncols` columns (1..MDJ_MAX_COLS), all with `nrows` rows. */
+typedef struct {
+    const mdj_col *cols;
+    int32_t ncols;
+    uint64_t nrows;
+} mdj_table;
+
+/* Device-memory allocator.  alloc returns a device pointer aligned to at least
+ * 256 bytes (or NULL on failure) usable in stream order on `stream`;
+ * release gives it back in stream order. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *ctx, void *stream);
+    void (*release)(void *ptr, void *ctx, void *stream);
+    void *ctx;
+} mdj_allocator;
+
+/* A join result.  Every array has `nrows` elements and was obtained from the
+ * allocator passed to the call (release it with mdj_result_release).
+ *   key        : the join key (key dtype of the inputs)
+ *   left_row   : 0-based row index in the left input table
+ *   right_row  : 0-based row index in the right input table
+ *   left_cols  : the left table's non-key columns, in table order
+ *   right_cols : the right table's non-key columns, in table order
+ * Row order is unspecified; the rows, as a multiset, are exactly the inner
+ * equi-join (every pair (l, r) with key_L[l] == key_R[r], duplicates
+ * included).  With nrows == 0 every pointer is NULL. */
+typedef struct {
+    uint64_t nrows;
+    int32_t key_dtype;
+    int32_t n_left_cols;
+    int32_t n_right_cols;
+    int32_t left_dtypes[MDJ_MAX_COLS];
+    int32_t right_dtypes[MDJ_MAX_COLS];
+    void *key;
+    uint32_t *left_row;
+    uint32_t *right_row;
+    void *left_cols[MDJ_MAX_COLS];
+    void *right_cols[MDJ_MAX_COLS];
+} mdj_result;
+
+/*
+ * mdj_partition - the shuffle step (Sec. V-B, "Shuffle: True"; the exchange of
+ * Sec. IV-B done on one device).  Stable hash partition of table `in` by column
+ * `key_col` into P partitions.
+ *   out_cols[j]   : caller-allocated device buffer of nrows elements of column
+ *                   j's dtype; receives column j with the rows of partition 0
+ *                   first, then partition 1, ...; inside a partition rows keep
+ *                   their input order.
+ *   out_row_ids   : caller-allocated device uint32[nrows]; out_row_ids[i] is
+ *                   the input row now at position i.  May be NULL.
+ *   out_offsets   : caller-allocated device int64[P+1]; partition p occupies
+ *                   positions [out_offsets[p], out_offsets[p+1]).
+ * Output buffers must not overlap the inputs.  1 <= P <= 65536.  nrows may be 0.
+ * Workspace comes from `alloc` and is released before return (stream order).
+ */
+MDJ_API int mdj_partition(const mdj_table *in, int32_t key_col, uint32_t P,
+                  void *const *out_cols, uint32_t *out_row_ids, int64_t *out_offsets,
+                  const mdj_allocator *alloc, void *stream);
+
+/*
+ * mdj_join - the per-partition merge (Sec. V-B: "a merge operation is carried
+ * out" on the co-located partitions).  Inner equi-join of `left` (build side)
+ * and `right` (probe side) on left column `left_key` = right column
+ * `right_key`, with no shuffle.  Internally the rows are bucketed by hash so
+ * every hash table lives in one SM's shared memory; a count pass sizes the
+ * output (one count read back to the host), a write pass fills it.
+ * Outputs are allocated with `alloc` and described in *out.
+ */
+MDJ_API int mdj_join(const mdj_table *left, int32_t left_key, const mdj_table *right, int32_t right_key,
+             const mdj_allocator *alloc, void *stream, mdj_result *out);
+
+/*
+ * mdj_merge - the whole cuDF-merge hot path (Sec. V-B, Fig. 8: "Shuffle: True";
+ * P emulates P workers): hash-partition both tables into P partitions (the
+ * shuffle), then join every partition pair (left p with right p).  The result is
+ * the same multiset of rows as mdj_join for every P.
+ */
+MDJ_API int mdj_merge(const mdj_table *left, int32_t left_key, const mdj_table *right, int32_t right_key,
+              uint32_t P, const mdj_allocator *alloc, void *stream, mdj_result *out);
+
+/*
+ * mdj_count_checksum - the merge of mdj_merge without materialising its rows,
+ * for joins too large to store.  Returns (host pointers):
+ *   *count    = number of joined pairs = sum over keys of lc(k) * rc(k);
+ *   *checksum = sum over joined pairs (l, r) of f(l) * g(r) mod 2^64, with
+ *     f(l) = fmix64(sext64(key_L[l]) ^ 0x9E3779B97F4A7C15 * (l + 1) ^ bits(lpay[l]))
+ *     g(r) = fmix64(0xC2B2AE3D27D4EB4F * (r + 1) ^ bits(rpay[r]))
+ *   where lpay / rpay is the first non-key column of each side (bits
+ *   zero-extended to 64; 0 if the side has no other column) and l, r are
+ *   0-based input row indices.
+ * Synchronises `stream` before returning.
+ */
+MDJ_API int mdj_count_checksum(const mdj_table *left, int32_t left_key, const mdj_table *right,
+                       int32_t right_key, uint32_t P, const mdj_allocator *alloc, void *stream,
+                       uint64_t *count, uint64_t *checksum);
+
+/* Releases every array of *res with `alloc` (stream order) and zeroes *res. */
+MDJ_API void mdj_result_release(mdj_result *res, const mdj_allocator *alloc, void *stream);
+
+/* Static, human-readable text for a status code. */
+MDJ_API const char *mdj_status_string(int status);
+
+/* MDJ_VERSION of the loaded library. */
+MDJ_API int mdj_version(void);
+
+/*
+ * Per-kernel timing (tracing).  While enabled, every kernel the library
+ * launches is bracketed by CUDA events recorded on the launch stream.
+ * mdj_profile_collect synchronises those events and accumulates, per kernel
+ * name, the launch count and total device milliseconds; mdj_profile_get reads
+ * entry i (0 <= i < mdj_profile_count()).  Enabling adds two event records per
+ * launch; it is off by default.
+ */
+MDJ_API void mdj_profile_enable(int on);
+MDJ_API void mdj_profile_reset(void);
+MDJ_API int mdj_profile_collect(void);
+MDJ_API int mdj_profile_count(void);
+MDJ_API int mdj_profile_get(int i, const char **name, uint64_t *launches, double *total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MDJ_H */

@@ -1,0 +1,636 @@
+// The shuffle: hash partitioning of a table on the device.
+//
+// In the paper the shuffle moves partition p of every worker's table to worker
+// p over MPI (Sec. IV-B, the Isend/Irecv coroutines; Sec. V-B "Shuffle: True").
+// On one GPU that exchange is a scatter: partition p's region of the output
+// plays worker p's receive buffer.  Kernels:
+//
+//   k_hist       per-tile bucket histogram (warp match_any + shared counters);
+//                optionally also the per-sub-bucket totals of a two-level plan
+//   (scan)       exclusive scan of the bucket-major (bucket, tile) histogram
+//                matrix = the global base of every (bucket, tile) run
+//   k_scatter    stable local counting sort of a tile in shared memory, then
+//                every column leaves as coalesced runs (one per bucket)
+//                RESERVE variant (pass 2): rows already grouped by pass-1
+//                bucket are split further; each tile reserves its runs with
+//                one atomicAdd per (tile, bucket) - not stable, coalesced
+//
+// Every kernel is bandwidth-bound: no tensor cores, integer hashing only.
+#include <string.h>
+
+#include "mdj_internal.cuh"
+
+namespace mdj {
+namespace {
+
+constexpr int kNW = 16;                     // warps per scatter block
+constexpr int kRPL = 16;                    // rows per lane per tile
+constexpr uint32_t kTile = kNW * 32 * kRPL; // 8192 rows per tile
+constexpr int kHistThreads = 512;
+
+struct ColMove {
+  const void *src[MDJ_MAX_COLS];
+  void *dst[MDJ_MAX_COLS];
+  int32_t width[MDJ_MAX_COLS];
+  int32_t n;
+  int32_t key_index;
+};
+
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+size_t scatter_smem_bytes(uint32_t FL) {
+  return (size_t)kTile * 8 + (size_t)kTile * 4 + align16((size_t)kNW * FL * 2) + (size_t)FL * 8 + 40 * 4;
+}
+
+// ------------------------------------------------------------------ k_hist
+
+template <typename KeyT>
+__global__ void __launch_bounds__(kHistThreads) k_hist(const KeyT *__restrict__ keys, uint32_t n, BucketSpec bs,
+                                                       uint32_t F, uint32_t ntiles, uint32_t *__restrict__ hist,
+                                                       uint32_t *__restrict__ total2, uint32_t nsub) {
+  extern __shared__ uint32_t sh[];
+  uint32_t *cnt = sh;
+  uint32_t *cnt2 = sh + F;
+  if (total2)
+    for (uint32_t i = threadIdx.x; i < nsub; i += blockDim.x) cnt2[i] = 0;
+  constexpr int U = 4;
+  for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    for (uint32_t b = threadIdx.x; b < F; b += blockDim.x) cnt[b] = 0;
+    __syncthreads();
+    const uint32_t row0 = t * kTile;
+    const uint32_t end = min(row0 + kTile, n);
+    for (uint32_t base = row0; base < end; base += blockDim.x * U) {
+      KeyT kv[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        uint32_t r = base + u * blockDim.x + threadIdx.x;
+        kv[u] = r < end ? keys[r] : KeyT(0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        uint32_t r = base + u * blockDim.x + threadIdx.x;
+        bool valid = r < end;
+        uint32_t b = 0xFFFFFFFFu;
+        if (valid) {
+          uint64_t h = fmix64(key_bits(kv[u]));
+          if (total2) {
+            uint32_t sb = sub_bucket_of(h, bs);
+            b = bs.div == 1 ? sb : sb / bs.div;
+            atomicAdd(&cnt2[sb], 1u);
+          } else {
+            b = bucket_of(h, bs);
+          }
+        }
+        uint32_t peers = __match_any_sync(0xffffffffu, b);
+        if (valid && (peers & lanemask_lt()) == 0) atomicAdd(&cnt[b], (uint32_t)__popc(peers));
+      }
+    }
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < F; b += blockDim.x) hist[(size_t)b * ntiles + t] = cnt[b];
+    __syncthreads();
+  }
+  if (total2) {
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < nsub; i += blockDim.x)
+      if (cnt2[i]) atomicAdd(&total2[i], cnt2[i]);
+  }
+}
+
+// --------------------------------------------------------------- k_scatter
+
+// Direct path of a pass-2 tile whose rows span too many buckets for shared
+// memory (tiny or very skewed pass-1 buckets): warp-aggregated reservation,
+// each row written straight to its slot.
+template <typename KeyT>
+__device__ void scatter_direct(const KeyT (&kv)[kRPL], uint32_t wrow0, uint32_t rend, const BucketSpec &bs,
+                               uint32_t *__restrict__ cursors, const ColMove &cm,
+                               const uint32_t *__restrict__ rid_in, uint32_t *__restrict__ rid_out) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll 1
+  for (int c = 0; c < kRPL; c++) {
+    uint32_t r = wrow0 + c * 32 + lane;
+    bool valid = r < rend;
+    uint32_t fb = valid ? sub_bucket_of(fmix64(key_bits(kv[c])), bs) : 0xFFFFFFFFu;
+    uint32_t peers = __match_any_sync(0xffffffffu, fb);
+    int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (valid && lane == leader) base = atomicAdd(&cursors[fb], (uint32_t)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (!valid) continue;
+    uint32_t pos = base + __popc(peers & lanemask_lt());
+    for (int j = 0; j < cm.n; j++) {
+      if (cm.width[j] == 8) {
+        uint64_t v = j == cm.key_index ? (uint64_t)kv[c] : ((const uint64_t *)cm.src[j])[r];
+        ((uint64_t *)cm.dst[j])[pos] = v;
+      } else {
+        uint32_t v = j == cm.key_index ? (uint32_t)kv[c] : ((const uint32_t *)cm.src[j])[r];
+        ((uint32_t *)cm.dst[j])[pos] = v;
+      }
+    }
+    if (rid_out) rid_out[pos] = rid_in ? rid_in[r] : r;
+  }
+}
+
+template <typename KeyT, bool RESERVE>
+__global__ void __launch_bounds__(kNW * 32, 1)
+    k_scatter(const KeyT *__restrict__ keys, uint32_t n, BucketSpec bs, uint32_t F, uint32_t ntiles,
+              const uint32_t *__restrict__ tile_base, uint32_t *__restrict__ cursors, uint32_t F2, ColMove cm,
+              const uint32_t *__restrict__ rid_in, uint32_t *__restrict__ rid_out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const uint32_t FL = RESERVE ? kPass2SpanMax : F;
+  uint64_t *stage64 = (uint64_t *)smem;
+  uint32_t *stage32 = (uint32_t *)smem;
+  uint32_t *dstmap = (uint32_t *)(smem + (size_t)kTile * 8);
+  uint16_t *whist = (uint16_t *)(smem + (size_t)kTile * 12);
+  uint32_t *lstart = (uint32_t *)(smem + (size_t)kTile * 12 + align16((size_t)kNW * FL * 2));
+  uint32_t *gbase = lstart + FL;
+  uint32_t *scratch = gbase + FL;
+
+  const uint32_t t = blockIdx.x;
+  const uint32_t row0 = t * kTile;
+  const uint32_t rows = min(kTile, n - row0);
+  const uint32_t rend = row0 + rows;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t wrow0 = row0 + warp * 32 * kRPL;
+
+  KeyT kv[kRPL];
+#pragma unroll
+  for (int c = 0; c < kRPL; c++) {
+    uint32_t r = wrow0 + c * 32 + lane;
+    kv[c] = r < rend ? keys[r] : KeyT(0);
+  }
+
+  uint32_t Floc = F, lb0 = 0;
+  if (RESERVE) {
+    uint32_t b1f = sub_bucket_of(fmix64(key_bits(keys[row0])), bs) / F2;
+    uint32_t b1l = sub_bucket_of(fmix64(key_bits(keys[rend - 1])), bs) / F2;
+    lb0 = b1f * F2;
+    Floc = (b1l - b1f + 1) * F2;
+    if (Floc > kPass2SpanMax) {
+      scatter_direct<KeyT>(kv, wrow0, rend, bs, cursors, cm, rid_in, rid_out);
+      return;
+    }
+  }
+
+  // 1. per-warp stable ranks: warp w owns rows [wrow0, wrow0 + 32*kRPL) and
+  //    walks them in order, so (warp, rank) order is input order.
+  for (uint32_t i = threadIdx.x; i < (kNW * Floc + 1) / 2; i += blockDim.x) ((uint32_t *)whist)[i] = 0;
+  __syncthreads();
+  uint32_t pk[kRPL];
+  uint16_t *wh = whist + warp * Floc;
+#pragma unroll
+  for (int c = 0; c < kRPL; c++) {
+    uint32_t r = wrow0 + c * 32 + lane;
+    bool valid = r < rend;
+    uint32_t b = valid ? bucket_of(fmix64(key_bits(kv[c])), bs) - lb0 : 0xFFFFFFFFu;
+    uint32_t peers = __match_any_sync(0xffffffffu, b);
+    uint32_t rank = __popc(peers & lanemask_lt());
+    uint32_t old = valid ? wh[b] : 0u;
+    __syncwarp();
+    if (valid && rank == 0) wh[b] = (uint16_t)(old + __popc(peers));
+    __syncwarp();
+    pk[c] = (b << 16) | (old + rank);
+  }
+  __syncthreads();
+
+  // 2. per bucket: warp offsets (exclusive over warps) and the tile count
+  for (uint32_t b = threadIdx.x; b < Floc; b += blockDim.x) {
+    uint32_t run = 0;
+    for (int w = 0; w < kNW; w++) {
+      uint32_t c = whist[w * Floc + b];
+      whist[w * Floc + b] = (uint16_t)run;
+      run += c;
+    }
+    lstart[b] = run;
+  }
+  __syncthreads();
+  block_scan_array(lstart, Floc, scratch);
+
+  // 3. global base of each bucket's run
+  for (uint32_t b = threadIdx.x; b < Floc; b += blockDim.x) {
+    if (!RESERVE) {
+      gbase[b] = tile_base[(size_t)b * ntiles + t];
+    } else {
+      uint32_t e = b + 1 < Floc ? lstart[b + 1] : rows;
+      uint32_t cnt = e - lstart[b];
+      gbase[b] = cnt ? atomicAdd(&cursors[lb0 + b], cnt) : 0u;
+    }
+  }
+  __syncthreads();
+
+  // 4. sorted position of each row and its destination
+  uint32_t lp[kRPL];
+#pragma unroll
+  for (int c = 0; c < kRPL; c++) {
+    uint32_t r = wrow0 + c * 32 + lane;
+    lp[c] = 0;
+    if (r < rend) {
+      uint32_t b = pk[c] >> 16, lr = pk[c] & 0xFFFFu;
+      uint32_t wo = whist[warp * Floc + b];
+      lp[c] = lstart[b] + wo + lr;
+      dstmap[lp[c]] = gbase[b] + wo + lr;
+    }
+  }
+  __syncthreads();
+
+  // 5. every column: stage in sorted order, leave as runs
+  for (int j = 0; j < cm.n; j++) {
+    if (cm.width[j] == 8) {
+      const uint64_t *src = (const uint64_t *)cm.src[j];
+      uint64_t v[kRPL];
+#pragma unroll
+      for (int c = 0; c < kRPL; c++) {
+        uint32_t r = wrow0 + c * 32 + lane;
+        v[c] = j == cm.key_index ? (uint64_t)kv[c] : (r < rend ? src[r] : 0ull);
+      }
+#pragma unroll
+      for (int c = 0; c < kRPL; c++)
+        if (wrow0 + c * 32 + lane < rend) stage64[lp[c]] = v[c];
+      __syncthreads();
+      uint64_t *dst = (uint64_t *)cm.dst[j];
+      for (uint32_t i = threadIdx.x; i < rows; i += blockDim.x) dst[dstmap[i]] = stage64[i];
+      __syncthreads();
+    } else {
+      const uint32_t *src = (const uint32_t *)cm.src[j];
+      uint32_t v[kRPL];
+#pragma unroll
+      for (int c = 0; c < kRPL; c++) {
+        uint32_t r = wrow0 + c * 32 + lane;
+        v[c] = j == cm.key_index ? (uint32_t)kv[c] : (r < rend ? src[r] : 0u);
+      }
+#pragma unroll
+      for (int c = 0; c < kRPL; c++)
+        if (wrow0 + c * 32 + lane < rend) stage32[lp[c]] = v[c];
+      __syncthreads();
+      uint32_t *dst = (uint32_t *)cm.dst[j];
+      for (uint32_t i = threadIdx.x; i < rows; i += blockDim.x) dst[dstmap[i]] = stage32[i];
+      __syncthreads();
+    }
+  }
+  if (rid_out) {
+    uint32_t v[kRPL];
+#pragma unroll
+    for (int c = 0; c < kRPL; c++) {
+      uint32_t r = wrow0 + c * 32 + lane;
+      v[c] = rid_in ? (r < rend ? rid_in[r] : 0u) : r;
+    }
+#pragma unroll
+    for (int c = 0; c < kRPL; c++)
+      if (wrow0 + c * 32 + lane < rend) stage32[lp[c]] = v[c];
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < rows; i += blockDim.x) rid_out[dstmap[i]] = stage32[i];
+  }
+}
+
+// ------------------------------------------------------------ small kernels
+
+__global__ void k_bucket_starts(const uint32_t *__restrict__ hist, uint32_t F, uint32_t ntiles, uint32_t n,
+                                uint32_t *__restrict__ start) {
+  uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < F) start[b] = ntiles ? hist[(size_t)b * ntiles] : 0u;
+  if (b == F) start[F] = n;
+}
+
+// offsets of partition p in rows already sorted by p: first row with p' >= p
+template <typename KeyT>
+__global__ void k_offsets_bsearch(const KeyT *__restrict__ keys, uint32_t n, BucketSpec bs, uint32_t P,
+                                  uint32_t *__restrict__ off) {
+  uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p > P) return;
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    uint32_t mid = lo + (hi - lo) / 2;
+    if (mod_p(fmix64(key_bits(keys[mid])), bs) < p)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  off[p] = lo;
+}
+
+__global__ void k_two(uint32_t *p, uint32_t a, uint32_t b) {
+  p[0] = a;
+  p[1] = b;
+}
+
+__global__ void k_u32_to_i64(const uint32_t *__restrict__ a, int64_t *__restrict__ b, uint32_t n) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (int64_t)a[i];
+}
+
+// ------------------------------------------------------------- host passes
+
+int hist_grid(size_t smem) {
+  int per_sm = 1;
+  if (smem <= 48 * 1024) per_sm = 4;
+  else if (smem <= 100 * 1024) per_sm = 2;
+  return num_sms() * per_sm;
+}
+
+template <typename KeyT>
+int set_smem_attrs() {
+  static bool done = false;
+  if (done) return MDJ_OK;
+  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_scatter<KeyT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)scatter_smem_bytes(kMaxFanout)));
+  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_scatter<KeyT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)scatter_smem_bytes(kPass2SpanMax)));
+  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_hist<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)((kMaxFanout + kMaxSubBuckets) * 4)));
+  done = true;
+  return MDJ_OK;
+}
+
+// One stable scatter pass over n rows into F <= kMaxFanout buckets.  If
+// `start` is given it receives the F+1 bucket start positions.  If `total2` is
+// given, the pass also counts rows per sub-bucket (nsub entries, zeroed by the
+// caller) for a following RESERVE pass.
+template <typename KeyT>
+int stable_pass(Workspace &ws, const KeyT *keys, uint32_t n, const BucketSpec &bs, uint32_t F, const ColMove &cm,
+                const uint32_t *rid_in, uint32_t *rid_out, uint32_t *start, uint32_t *total2, uint32_t nsub) {
+  cudaStream_t s = ws.stream();
+  MDJ_TRY(set_smem_attrs<KeyT>());
+  const uint32_t ntiles = (n + kTile - 1) / kTile;
+  if (ntiles == 0) {
+    if (start) MDJ_CUDA_TRY(cudaMemsetAsync(start, 0, (size_t)(F + 1) * 4, s));
+    return MDJ_OK;
+  }
+  uint32_t *hist = (uint32_t *)ws.get((size_t)F * ntiles * 4);
+  if (!hist) return MDJ_ERR_OOM;
+  const size_t hsmem = (size_t)(F + (total2 ? nsub : 0)) * 4;
+  {
+    TraceScope tr("hist", s);
+    const unsigned hgrid = (unsigned)(ntiles < (uint32_t)hist_grid(hsmem) ? ntiles : (uint32_t)hist_grid(hsmem));
+    k_hist<KeyT><<<hgrid, kHistThreads, hsmem, s>>>(
+        keys, n, bs, F, ntiles, hist, total2, nsub);
+  }
+  MDJ_LAUNCH_CHECK();
+  MDJ_TRY(exclusive_scan_u32(ws, hist, hist, (size_t)F * ntiles));
+  if (start) {
+    TraceScope tr("bucket_starts", s);
+    k_bucket_starts<<<(F + 1 + 255) / 256, 256, 0, s>>>(hist, F, ntiles, n, start);
+  }
+  MDJ_LAUNCH_CHECK();
+  {
+    TraceScope tr("scatter_stable", s);
+    k_scatter<KeyT, false><<<ntiles, kNW * 32, scatter_smem_bytes(F), s>>>(keys, n, bs, F, ntiles, hist, nullptr, 1,
+                                                                          cm, rid_in, rid_out);
+  }
+  MDJ_LAUNCH_CHECK();
+  ws.give_back(hist);
+  return MDJ_OK;
+}
+
+// Pass 2 of a two-level plan: rows grouped by pass-1 bucket (sb / F2) are
+// split into final sub-buckets sb with atomic run reservation.
+template <typename KeyT>
+int reserve_pass(Workspace &ws, const KeyT *keys, uint32_t n, const BucketSpec &bs_sub, uint32_t F2,
+                 uint32_t *cursors, const ColMove &cm, const uint32_t *rid_in, uint32_t *rid_out) {
+  cudaStream_t s = ws.stream();
+  MDJ_TRY(set_smem_attrs<KeyT>());
+  const uint32_t ntiles = (n + kTile - 1) / kTile;
+  if (ntiles == 0) return MDJ_OK;
+  {
+    TraceScope tr("scatter_reserve", s);
+    k_scatter<KeyT, true><<<ntiles, kNW * 32, scatter_smem_bytes(kPass2SpanMax), s>>>(
+        keys, n, bs_sub, 0, ntiles, nullptr, cursors, F2, cm, rid_in, rid_out);
+  }
+  MDJ_LAUNCH_CHECK();
+  return MDJ_OK;
+}
+
+// Buffers of one partitioned copy of a table.
+struct TableBufs {
+  void *cols[MDJ_MAX_COLS];
+  uint32_t *rid;
+};
+
+int alloc_table_bufs(Workspace &ws, const mdj_table *t, TableBufs *b, bool with_rid) {
+  const size_t n = t->nrows;
+  for (int j = 0; j < t->ncols; j++) {
+    b->cols[j] = ws.get(n * dtype_width(t->cols[j].dtype));
+    if (!b->cols[j]) return MDJ_ERR_OOM;
+  }
+  b->rid = nullptr;
+  if (with_rid) {
+    b->rid = (uint32_t *)ws.get(n * 4);
+    if (!b->rid) return MDJ_ERR_OOM;
+  }
+  return MDJ_OK;
+}
+
+void release_table_bufs(Workspace &ws, const mdj_table *t, TableBufs *b) {
+  for (int j = 0; j < t->ncols; j++) ws.give_back(b->cols[j]);
+  if (b->rid) ws.give_back(b->rid);
+}
+
+ColMove make_move(const mdj_table *t, int32_t key_col, const void *const *src, void *const *dst) {
+  ColMove cm;
+  memset(&cm, 0, sizeof cm);
+  cm.n = t->ncols;
+  cm.key_index = key_col;
+  for (int j = 0; j < t->ncols; j++) {
+    cm.src[j] = src[j];
+    cm.dst[j] = dst[j];
+    cm.width[j] = dtype_width(t->cols[j].dtype);
+  }
+  return cm;
+}
+
+// Stable partition by p with P > kMaxFanout: two stable LSD digit passes
+// (p mod 1024, then p / 1024), which sort stably by p.  Writes into `dst`
+// buffers; `off` (device u32[P+1]) receives the partition offsets.
+template <typename KeyT>
+int lsd_partition(Workspace &ws, const mdj_table *t, int32_t key_col, uint32_t P, void *const *dst_cols,
+                  uint32_t *dst_rid, uint32_t *off) {
+  const uint32_t n = (uint32_t)t->nrows;
+  const void *src[MDJ_MAX_COLS];
+  for (int j = 0; j < t->ncols; j++) src[j] = t->cols[j].data;
+  TableBufs mid;
+  MDJ_TRY(alloc_table_bufs(ws, t, &mid, true));
+  const uint32_t d0 = kMaxFanout, d1 = (P + kMaxFanout - 1) / kMaxFanout;
+  ColMove cm0 = make_move(t, key_col, src, mid.cols);
+  MDJ_TRY(stable_pass<KeyT>(ws, (const KeyT *)src[key_col], n, make_digit_spec(P, 1, d0), d0, cm0, nullptr, mid.rid,
+                            nullptr, nullptr, 0));
+  ColMove cm1 = make_move(t, key_col, mid.cols, dst_cols);
+  MDJ_TRY(stable_pass<KeyT>(ws, (const KeyT *)mid.cols[key_col], n, make_digit_spec(P, d0, d1), d1, cm1, mid.rid,
+                            dst_rid, nullptr, nullptr, 0));
+  release_table_bufs(ws, t, &mid);
+  {
+    TraceScope tr("offsets_bsearch", ws.stream());
+    k_offsets_bsearch<KeyT><<<(P + 1 + 255) / 256, 256, 0, ws.stream()>>>((const KeyT *)dst_cols[key_col], n,
+                                                                         make_spec(P, 1, 1), P, off);
+  }
+  MDJ_LAUNCH_CHECK();
+  return MDJ_OK;
+}
+
+template <typename KeyT>
+int stable_partition_t(Workspace &ws, const mdj_table *t, int32_t key_col, uint32_t P, void *const *out_cols,
+                       uint32_t *out_rid, int64_t *out_offsets) {
+  cudaStream_t s = ws.stream();
+  const uint32_t n = (uint32_t)t->nrows;
+  uint32_t *off = (uint32_t *)ws.get((size_t)(P + 1) * 4);
+  if (!off) return MDJ_ERR_OOM;
+  uint32_t *rid = out_rid;
+  if (!rid && n > 0) {
+    // row ids are needed by the second LSD pass only; a single pass can skip them
+    if (P > kMaxFanout) {
+      rid = (uint32_t *)ws.get((size_t)n * 4);
+      if (!rid) return MDJ_ERR_OOM;
+    }
+  }
+  if (P <= kMaxFanout) {
+    const void *src[MDJ_MAX_COLS];
+    for (int j = 0; j < t->ncols; j++) src[j] = t->cols[j].data;
+    ColMove cm = make_move(t, key_col, src, out_cols);
+    MDJ_TRY(stable_pass<KeyT>(ws, (const KeyT *)src[key_col], n, make_spec(P, 1, 1), P, cm, nullptr, out_rid, off,
+                              nullptr, 0));
+  } else {
+    if (n == 0) {
+      MDJ_CUDA_TRY(cudaMemsetAsync(off, 0, (size_t)(P + 1) * 4, s));
+    } else {
+      MDJ_TRY(lsd_partition<KeyT>(ws, t, key_col, P, out_cols, rid, off));
+    }
+  }
+  {
+    TraceScope tr("offsets_i64", s);
+    k_u32_to_i64<<<(P + 1 + 255) / 256, 256, 0, s>>>(off, out_offsets, P + 1);
+  }
+  MDJ_LAUNCH_CHECK();
+  return MDJ_OK;
+}
+
+template <typename KeyT>
+int partition_side_t(Workspace &ws, const mdj_table *t, int32_t key_col, const Plan &plan, Side *out) {
+  cudaStream_t s = ws.stream();
+  const uint32_t n = (uint32_t)t->nrows;
+  const void *src[MDJ_MAX_COLS];
+  for (int j = 0; j < t->ncols; j++) src[j] = t->cols[j].data;
+
+  uint32_t *off = (uint32_t *)ws.get((size_t)(plan.nbuckets + 1) * 4);
+  if (!off) return MDJ_ERR_OOM;
+  TableBufs fin;
+  fin.rid = nullptr;
+  const void *key = src[key_col];
+  const void *const *cols = src;
+  const uint32_t *rid = nullptr;
+
+  if (!plan.partition) {
+    TraceScope tr("offsets_whole", s);
+    k_two<<<1, 1, 0, s>>>(off, 0u, n);
+    MDJ_LAUNCH_CHECK();
+  } else if (plan.lsd) {
+    MDJ_TRY(alloc_table_bufs(ws, t, &fin, true));
+    MDJ_TRY(lsd_partition<KeyT>(ws, t, key_col, plan.P, fin.cols, fin.rid, off));
+    key = fin.cols[key_col];
+    cols = fin.cols;
+    rid = fin.rid;
+  } else if (plan.F2 == 1) {
+    MDJ_TRY(alloc_table_bufs(ws, t, &fin, true));
+    ColMove cm = make_move(t, key_col, src, fin.cols);
+    MDJ_TRY(stable_pass<KeyT>(ws, (const KeyT *)key, n, make_spec(plan.P, plan.S, 1), plan.nbuckets, cm, nullptr,
+                              fin.rid, off, nullptr, 0));
+    key = fin.cols[key_col];
+    cols = fin.cols;
+    rid = fin.rid;
+  } else {
+    // pass 1: F1 = P*S/F2 stable buckets, counting the final sub-buckets too
+    uint32_t *cur = (uint32_t *)ws.get((size_t)(plan.nbuckets + 1) * 4);
+    if (!cur) return MDJ_ERR_OOM;
+    MDJ_CUDA_TRY(cudaMemsetAsync(off, 0, (size_t)(plan.nbuckets + 1) * 4, s));
+    TableBufs p1;
+    MDJ_TRY(alloc_table_bufs(ws, t, &p1, true));
+    ColMove cm1 = make_move(t, key_col, src, p1.cols);
+    MDJ_TRY(stable_pass<KeyT>(ws, (const KeyT *)key, n, make_spec(plan.P, plan.S, plan.F2), plan.F1, cm1, nullptr,
+                              p1.rid, nullptr, off, plan.nbuckets));
+    MDJ_TRY(exclusive_scan_u32(ws, off, off, plan.nbuckets + 1));
+    MDJ_CUDA_TRY(cudaMemcpyAsync(cur, off, (size_t)plan.nbuckets * 4, cudaMemcpyDeviceToDevice, s));
+    // pass 2
+    MDJ_TRY(alloc_table_bufs(ws, t, &fin, true));
+    ColMove cm2 = make_move(t, key_col, p1.cols, fin.cols);
+    MDJ_TRY(reserve_pass<KeyT>(ws, (const KeyT *)p1.cols[key_col], n, make_spec(plan.P, plan.S, 1), plan.F2, cur,
+                               cm2, p1.rid, fin.rid));
+    release_table_bufs(ws, t, &p1);
+    ws.give_back(cur);
+    key = fin.cols[key_col];
+    cols = fin.cols;
+    rid = fin.rid;
+  }
+
+  out->key = key;
+  out->key_dtype = t->cols[key_col].dtype;
+  out->ncols = 0;
+  for (int j = 0; j < t->ncols; j++) {
+    if (j == key_col) continue;
+    out->cols[out->ncols] = cols[j];
+    out->widths[out->ncols] = dtype_width(t->cols[j].dtype);
+    out->dtypes[out->ncols] = t->cols[j].dtype;
+    out->ncols++;
+  }
+  out->rid = rid;
+  out->off = off;
+  out->nrows = n;
+  return MDJ_OK;
+}
+
+}  // namespace
+
+Plan make_plan(uint64_t n_build, uint32_t P, uint32_t cap, bool force_partition) {
+  Plan pl;
+  pl.P = P;
+  pl.cap = cap;
+  // target mean build rows per sub-bucket: ~85% of a table, so that hash
+  // variance rarely overflows one table
+  const uint64_t target = (uint64_t)cap * 85 / 100;
+  uint64_t need = (n_build + target - 1) / target;
+  if (need < 1) need = 1;
+  if (P > kMaxFanout) {
+    pl.lsd = true;
+    pl.S = 1;
+    pl.nbuckets = P;
+    pl.F1 = P;
+    pl.F2 = 1;
+    return pl;
+  }
+  if (P == 1 && need == 1 && !force_partition) {
+    pl.partition = false;
+    pl.S = 1;
+    pl.nbuckets = 1;
+    return pl;
+  }
+  uint64_t S = (need + P - 1) / P;
+  if (S < 1) S = 1;
+  if ((uint64_t)P * S <= kMaxFanout) {
+    pl.S = (uint32_t)S;
+    pl.F1 = P * pl.S;
+    pl.F2 = 1;
+    pl.nbuckets = pl.F1;
+    return pl;
+  }
+  uint32_t S1 = kMaxFanout / P;
+  uint64_t F2 = (S + S1 - 1) / S1;
+  uint64_t max_f2 = kMaxSubBuckets / ((uint64_t)P * S1);
+  if (F2 > max_f2) F2 = max_f2;  // larger inputs: sub-buckets split into several tables
+  if (F2 > kPass2SpanMax / 2) F2 = kPass2SpanMax / 2;
+  if (F2 < 1) F2 = 1;
+  pl.F2 = (uint32_t)F2;
+  pl.S = S1 * pl.F2;
+  pl.F1 = P * S1;
+  pl.nbuckets = P * pl.S;
+  return pl;
+}
+
+int partition_side(Workspace &ws, const mdj_table *t, int32_t key_col, const Plan &plan, Side *out) {
+  if (t->cols[key_col].dtype == MDJ_I64) return partition_side_t<int64_t>(ws, t, key_col, plan, out);
+  return partition_side_t<int32_t>(ws, t, key_col, plan, out);
+}
+
+int stable_partition(Workspace &ws, const mdj_table *t, int32_t key_col, uint32_t P, void *const *out_cols,
+                     uint32_t *out_rid, int64_t *out_offsets) {
+  if (t->cols[key_col].dtype == MDJ_I64)
+    return stable_partition_t<int64_t>(ws, t, key_col, P, out_cols, out_rid, out_offsets);
+  return stable_partition_t<int32_t>(ws, t, key_col, P, out_cols, out_rid, out_offsets);
+}
+
+}  // namespace mdj

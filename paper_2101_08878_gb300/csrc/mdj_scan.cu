@@ -1,0 +1,101 @@
+// Device-wide exclusive scan (prefix sum), used for partition offsets, the
+// per-(bucket, tile) scatter bases, work-item offsets and output offsets.
+//
+// Three launches, no inter-block waits: (1) each block reduces one chunk,
+// (2) one block scans the chunk sums, (3) each block rescans its chunk and adds
+// its chunk's base.  Each element is read twice and written once.
+#include "mdj_internal.cuh"
+
+namespace mdj {
+namespace {
+
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 8;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+
+template <typename T>
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const T *__restrict__ in, size_t n, T *__restrict__ sums) {
+  __shared__ T scratch[33];
+  const size_t base = (size_t)blockIdx.x * kScanChunk + (size_t)threadIdx.x * kScanItems;
+  T s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; i++)
+    if (base + i < n) s += in[base + i];
+  T tot;
+  block_exclusive_scan<T>(s, scratch, &tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// One block: exclusive scan of `sums[0..m)` in place, chunk by chunk with a
+// running carry.
+template <typename T>
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(T *__restrict__ sums, size_t m) {
+  __shared__ T scratch[33];
+  T carry = 0;
+  for (size_t c0 = 0; c0 < m; c0 += kScanThreads) {
+    size_t i = c0 + threadIdx.x;
+    T v = i < m ? sums[i] : T(0);
+    T tot;
+    T ex = block_exclusive_scan<T>(v, scratch, &tot);
+    if (i < m) sums[i] = carry + ex;
+    carry += tot;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const T *__restrict__ in, T *__restrict__ out, size_t n,
+                                                            const T *__restrict__ sums) {
+  __shared__ T scratch[33];
+  const size_t base = (size_t)blockIdx.x * kScanChunk + (size_t)threadIdx.x * kScanItems;
+  T v[kScanItems];
+  T s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; i++) {
+    v[i] = base + i < n ? in[base + i] : T(0);
+    s += v[i];
+  }
+  T tot;
+  T run = block_exclusive_scan<T>(s, scratch, &tot) + sums[blockIdx.x];
+#pragma unroll
+  for (int i = 0; i < kScanItems; i++)
+    if (base + i < n) {
+      out[base + i] = run;
+      run += v[i];
+    }
+}
+
+template <typename T>
+int exclusive_scan(Workspace &ws, const T *in, T *out, size_t n) {
+  if (n == 0) return MDJ_OK;
+  const size_t nb = (n + kScanChunk - 1) / kScanChunk;
+  T *sums = (T *)ws.get(nb * sizeof(T));
+  if (!sums) return MDJ_ERR_OOM;
+  cudaStream_t s = ws.stream();
+  {
+    TraceScope tr("scan_reduce", s);
+    k_scan_reduce<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums);
+  }
+  {
+    TraceScope tr("scan_sums", s);
+    k_scan_sums<T><<<1, kScanThreads, 0, s>>>(sums, nb);
+  }
+  {
+    TraceScope tr("scan_down", s);
+    k_scan_down<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, sums);
+  }
+  MDJ_LAUNCH_CHECK();
+  ws.give_back(sums);
+  return MDJ_OK;
+}
+
+}  // namespace
+
+int exclusive_scan_u32(Workspace &ws, const uint32_t *in, uint32_t *out, size_t n) {
+  return exclusive_scan<uint32_t>(ws, in, out, n);
+}
+
+int exclusive_scan_u64(Workspace &ws, const uint64_t *in, uint64_t *out, size_t n) {
+  return exclusive_scan<uint64_t>(ws, in, out, n);
+}
+
+}  // namespace mdj

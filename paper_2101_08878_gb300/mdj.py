@@ -1,0 +1,331 @@
+"""ctypes binding of libmdj.so (declared in include/mdj.h).
+
+Argument marshalling only: every step of the shuffle and join runs in the
+library's CUDA kernels.  Device memory for workspace and outputs comes from
+PyTorch's caching allocator through an mdj_allocator callback, and every call
+runs on the current torch CUDA stream.  There is no CPU fallback: if the
+library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmdj.so")
+
+MDJ_MAX_COLS = 16
+MDJ_OK = 0
+STATUS = {
+    0: "MDJ_OK", -1: "MDJ_ERR_INVALID_ARG", -2: "MDJ_ERR_UNSUPPORTED_DTYPE", -3: "MDJ_ERR_TOO_LARGE",
+    -4: "MDJ_ERR_OOM", -5: "MDJ_ERR_CUDA", -6: "MDJ_ERR_DEVICE_TIMEOUT", -7: "MDJ_ERR_INTERNAL",
+}
+MDJ_I32, MDJ_I64, MDJ_F32, MDJ_F64, MDJ_U32, MDJ_U64 = 1, 2, 3, 4, 5, 6
+
+_TORCH_TO_MDJ = {
+    torch.int32: MDJ_I32, torch.int64: MDJ_I64, torch.float32: MDJ_F32, torch.float64: MDJ_F64,
+    torch.uint32: MDJ_U32, torch.uint64: MDJ_U64,
+}
+_MDJ_TO_TORCH = {v: k for k, v in _TORCH_TO_MDJ.items()}
+
+EXPORTED = [
+    "mdj_partition", "mdj_join", "mdj_merge", "mdj_count_checksum", "mdj_result_release",
+    "mdj_status_string", "mdj_version", "mdj_profile_enable", "mdj_profile_reset",
+    "mdj_profile_collect", "mdj_profile_count", "mdj_profile_get",
+]
+
+
+class MdjError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what} failed: {STATUS.get(status, status)} ({status})")
+        self.status = status
+
+
+# ---------------------------------------------------------------- C structs
+
+class MdjCol(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("dtype", ctypes.c_int32)]
+
+
+class MdjTable(ctypes.Structure):
+    _fields_ = [("cols", ctypes.POINTER(MdjCol)), ("ncols", ctypes.c_int32), ("nrows", ctypes.c_uint64)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class MdjAllocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("release", RELEASE_FN), ("ctx", ctypes.c_void_p)]
+
+
+class MdjResult(ctypes.Structure):
+    _fields_ = [
+        ("nrows", ctypes.c_uint64), ("key_dtype", ctypes.c_int32), ("n_left_cols", ctypes.c_int32),
+        ("n_right_cols", ctypes.c_int32), ("left_dtypes", ctypes.c_int32 * MDJ_MAX_COLS),
+        ("right_dtypes", ctypes.c_int32 * MDJ_MAX_COLS), ("key", ctypes.c_void_p),
+        ("left_row", ctypes.c_void_p), ("right_row", ctypes.c_void_p),
+        ("left_cols", ctypes.c_void_p * MDJ_MAX_COLS), ("right_cols", ctypes.c_void_p * MDJ_MAX_COLS),
+    ]
+
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+def load(path: str = LIB_PATH):
+    """Load libmdj.so (raises if it has not been built)."""
+    global _lib
+    with _lib_lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"libmdj.so not found at {path}: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(path)
+        vp, i32, u32, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64
+        P = ctypes.POINTER
+        lib.mdj_partition.restype = ctypes.c_int
+        lib.mdj_partition.argtypes = [P(MdjTable), i32, u32, P(vp), vp, vp, P(MdjAllocator), vp]
+        for name in ("mdj_join",):
+            f = getattr(lib, name)
+            f.restype = ctypes.c_int
+            f.argtypes = [P(MdjTable), i32, P(MdjTable), i32, P(MdjAllocator), vp, P(MdjResult)]
+        lib.mdj_merge.restype = ctypes.c_int
+        lib.mdj_merge.argtypes = [P(MdjTable), i32, P(MdjTable), i32, u32, P(MdjAllocator), vp, P(MdjResult)]
+        lib.mdj_count_checksum.restype = ctypes.c_int
+        lib.mdj_count_checksum.argtypes = [P(MdjTable), i32, P(MdjTable), i32, u32, P(MdjAllocator), vp,
+                                           P(u64), P(u64)]
+        lib.mdj_result_release.restype = None
+        lib.mdj_result_release.argtypes = [P(MdjResult), P(MdjAllocator), vp]
+        lib.mdj_status_string.restype = ctypes.c_char_p
+        lib.mdj_status_string.argtypes = [ctypes.c_int]
+        lib.mdj_version.restype = ctypes.c_int
+        lib.mdj_profile_enable.argtypes = [ctypes.c_int]
+        lib.mdj_profile_enable.restype = None
+        lib.mdj_profile_reset.restype = None
+        lib.mdj_profile_collect.restype = ctypes.c_int
+        lib.mdj_profile_count.restype = ctypes.c_int
+        lib.mdj_profile_get.restype = ctypes.c_int
+        lib.mdj_profile_get.argtypes = [ctypes.c_int, P(ctypes.c_char_p), P(u64), P(ctypes.c_double)]
+        _lib = lib
+        return lib
+
+
+# ------------------------------------------------------------ torch memory
+
+class TorchAllocator:
+    """mdj_allocator backed by torch's caching allocator on one device.
+
+    Buffers stay referenced in `live` until the library releases them or the
+    caller adopts them (join outputs)."""
+
+    def __init__(self, device: torch.device):
+        self.device = device
+        self.live = {}
+        self.failed = False
+        self._alloc = ALLOC_FN(self._on_alloc)
+        self._release = RELEASE_FN(self._on_release)
+        self.struct = MdjAllocator(self._alloc, self._release, None)
+
+    def _on_alloc(self, nbytes, ctx, stream):
+        try:
+            t = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=self.device)
+        except Exception:  # noqa: BLE001 - an allocation failure becomes MDJ_ERR_OOM
+            self.failed = True
+            return None
+        p = t.data_ptr()
+        self.live[p] = t
+        return p
+
+    def _on_release(self, ptr, ctx, stream):
+        if ptr:
+            self.live.pop(int(ptr), None)
+
+    def adopt(self, ptr, n: int, dtype: torch.dtype) -> torch.Tensor:
+        if not ptr or n == 0:
+            return torch.empty(0, dtype=dtype, device=self.device)
+        t = self.live.pop(int(ptr))
+        return t[: n * torch.empty((), dtype=dtype).element_size()].view(dtype)
+
+
+# ----------------------------------------------------------------- helpers
+
+def _table(cols: Sequence[torch.Tensor]):
+    if not 1 <= len(cols) <= MDJ_MAX_COLS:
+        raise ValueError(f"a table needs 1..{MDJ_MAX_COLS} columns")
+    n = cols[0].numel()
+    arr = (MdjCol * len(cols))()
+    for j, c in enumerate(cols):
+        if not c.is_cuda:
+            raise ValueError("columns must be CUDA tensors")
+        if c.dim() != 1 or c.numel() != n or not c.is_contiguous():
+            raise ValueError("columns must be contiguous 1-D tensors of equal length")
+        if c.dtype not in _TORCH_TO_MDJ:
+            raise TypeError(f"unsupported column dtype {c.dtype}")
+        arr[j].data = c.data_ptr() if n else None
+        arr[j].dtype = _TORCH_TO_MDJ[c.dtype]
+    return MdjTable(arr, len(cols), n), arr
+
+
+def _stream_handle(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def _check(rc: int, what: str):
+    if rc != MDJ_OK:
+        raise MdjError(rc, what)
+
+
+@dataclass
+class JoinResult:
+    """Columns of an inner join result (device tensors, nrows each)."""
+    nrows: int
+    key: torch.Tensor
+    left_row: torch.Tensor
+    right_row: torch.Tensor
+    left_cols: List[torch.Tensor]
+    right_cols: List[torch.Tensor]
+
+
+def _adopt_result(res: MdjResult, alloc: TorchAllocator) -> JoinResult:
+    m = int(res.nrows)
+    kd = _MDJ_TO_TORCH.get(res.key_dtype, torch.int64)
+    return JoinResult(
+        nrows=m,
+        key=alloc.adopt(res.key, m, kd),
+        left_row=alloc.adopt(res.left_row, m, torch.uint32),
+        right_row=alloc.adopt(res.right_row, m, torch.uint32),
+        left_cols=[alloc.adopt(res.left_cols[j], m, _MDJ_TO_TORCH[res.left_dtypes[j]])
+                   for j in range(res.n_left_cols)],
+        right_cols=[alloc.adopt(res.right_cols[j], m, _MDJ_TO_TORCH[res.right_dtypes[j]])
+                    for j in range(res.n_right_cols)],
+    )
+
+
+# --------------------------------------------------------------- public API
+
+def mdj_partition(cols: Sequence[torch.Tensor], key_col: int, P: int, row_ids: bool = True):
+    """Stable hash partition (see mdj.h).  Returns (offsets int64[P+1], row_ids uint32[n] or None, columns)."""
+    lib = load()
+    dev = cols[0].device
+    tab, keep = _table(cols)
+    n = tab.nrows
+    outs = [torch.empty(n, dtype=c.dtype, device=dev) for c in cols]
+    out_ptrs = (ctypes.c_void_p * len(cols))(*[o.data_ptr() if n else None for o in outs])
+    rid = torch.empty(n, dtype=torch.uint32, device=dev) if row_ids else None
+    offsets = torch.empty(P + 1, dtype=torch.int64, device=dev)
+    alloc = TorchAllocator(dev)
+    rc = lib.mdj_partition(ctypes.byref(tab), key_col, P, out_ptrs,
+                           rid.data_ptr() if (rid is not None and n) else None, offsets.data_ptr(),
+                           ctypes.byref(alloc.struct), _stream_handle(dev))
+    _check(rc, "mdj_partition")
+    return offsets, rid, outs
+
+
+def mdj_join(left_cols: Sequence[torch.Tensor], right_cols: Sequence[torch.Tensor],
+             left_key: int = 0, right_key: int = 0) -> JoinResult:
+    """Inner equi-join without shuffle (see mdj.h)."""
+    lib = load()
+    dev = left_cols[0].device
+    lt, lk = _table(left_cols)
+    rt, rk = _table(right_cols)
+    alloc = TorchAllocator(dev)
+    res = MdjResult()
+    rc = lib.mdj_join(ctypes.byref(lt), left_key, ctypes.byref(rt), right_key, ctypes.byref(alloc.struct),
+                      _stream_handle(dev), ctypes.byref(res))
+    _check(rc, "mdj_join")
+    return _adopt_result(res, alloc)
+
+
+def mdj_merge(left_cols: Sequence[torch.Tensor], right_cols: Sequence[torch.Tensor], P: int,
+              left_key: int = 0, right_key: int = 0) -> JoinResult:
+    """Hash shuffle into P partitions + per-partition inner join (see mdj.h)."""
+    lib = load()
+    dev = left_cols[0].device
+    lt, lk = _table(left_cols)
+    rt, rk = _table(right_cols)
+    alloc = TorchAllocator(dev)
+    res = MdjResult()
+    rc = lib.mdj_merge(ctypes.byref(lt), left_key, ctypes.byref(rt), right_key, P, ctypes.byref(alloc.struct),
+                       _stream_handle(dev), ctypes.byref(res))
+    _check(rc, "mdj_merge")
+    return _adopt_result(res, alloc)
+
+
+def mdj_count_checksum(left_cols: Sequence[torch.Tensor], right_cols: Sequence[torch.Tensor], P: int,
+                       left_key: int = 0, right_key: int = 0):
+    """(pair count, pair checksum) of the merge without materialising it (see mdj.h)."""
+    lib = load()
+    dev = left_cols[0].device
+    lt, lk = _table(left_cols)
+    rt, rk = _table(right_cols)
+    alloc = TorchAllocator(dev)
+    cnt, chk = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    rc = lib.mdj_count_checksum(ctypes.byref(lt), left_key, ctypes.byref(rt), right_key, P,
+                                ctypes.byref(alloc.struct), _stream_handle(dev), ctypes.byref(cnt),
+                                ctypes.byref(chk))
+    _check(rc, "mdj_count_checksum")
+    return cnt.value, chk.value
+
+
+def mdj_status_string(status: int) -> str:
+    return load().mdj_status_string(status).decode()
+
+
+def mdj_version() -> int:
+    return load().mdj_version()
+
+
+# ------------------------------------------------------------------ tracing
+
+def profile_enable(on: bool = True):
+    load().mdj_profile_enable(1 if on else 0)
+
+
+def profile_reset():
+    load().mdj_profile_reset()
+
+
+def profile_collect() -> dict:
+    """{kernel name: (launches, total device ms)} accumulated since the last reset."""
+    lib = load()
+    _check(lib.mdj_profile_collect(), "mdj_profile_collect")
+    out = {}
+    for i in range(lib.mdj_profile_count()):
+        name = ctypes.c_char_p()
+        launches = ctypes.c_uint64()
+        ms = ctypes.c_double()
+        _check(lib.mdj_profile_get(i, ctypes.byref(name), ctypes.byref(launches), ctypes.byref(ms)),
+               "mdj_profile_get")
+        out[name.value.decode()] = (launches.value, ms.value)
+    return out
+
+
+# --------------------------------------------------------------- host → host
+
+def merge_host(left_cols, right_cols, P: int, left_key: int = 0, right_key: int = 0,
+               device: Optional[torch.device] = None):
+    """End-to-end merge of host (pinned) tensors: copy in, mdj_merge, copy the
+    result out.  Returns (JoinResult with CPU tensors, h2d bytes, d2h bytes)."""
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    s = torch.cuda.current_stream(dev)
+    dl = [c.to(dev, non_blocking=True) for c in left_cols]
+    dr = [c.to(dev, non_blocking=True) for c in right_cols]
+    h2d = sum(c.numel() * c.element_size() for c in list(left_cols) + list(right_cols))
+    res = mdj_merge(dl, dr, P, left_key, right_key)
+    def host(t):
+        h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+        h.copy_(t, non_blocking=True)
+        return h
+    out = JoinResult(res.nrows, host(res.key), host(res.left_row), host(res.right_row),
+                     [host(c) for c in res.left_cols], [host(c) for c in res.right_cols])
+    s.synchronize()
+    d2h = sum(t.numel() * t.element_size() for t in [out.key, out.left_row, out.right_row, *out.left_cols,
+                                                      *out.right_cols])
+    return out, h2d, d2h

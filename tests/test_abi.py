@@ -1,0 +1,79 @@
+"""The C ABI library loads and exports every entry point include/mdj.h
+declares, and its host-side argument checks answer without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mdj.h")
+
+
+def declared():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"MDJ_API\s+[\w\s\*]*?\b(mdj_\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2101_08878_gb300 import _build, mdj
+    try:
+        _build.build()
+    except (OSError, RuntimeError) as e:  # no nvcc on this machine
+        pytest.skip(f"cannot build libmdj.so here: {e}")
+    return mdj.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared()
+    for n in ("mdj_partition", "mdj_join", "mdj_merge", "mdj_count_checksum", "mdj_result_release",
+              "mdj_status_string"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2101_08878_gb300 import mdj
+    names = declared()
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) <= set(mdj.EXPORTED) | set(names)
+    assert set(mdj.EXPORTED) == set(names)
+
+
+def test_version_and_status_strings(lib):
+    assert lib.mdj_version() == 1
+    assert lib.mdj_status_string(0) == b"ok"
+    assert b"invalid" in lib.mdj_status_string(-1)
+    assert lib.mdj_status_string(12345) == b"unknown status"
+
+
+def test_argument_checks_need_no_gpu(lib):
+    from paper_2101_08878_gb300.mdj import MdjCol, MdjResult, MdjTable
+    # null tables / bad key index / bad dtypes / P out of range are rejected
+    # before any CUDA call
+    res = MdjResult()
+    assert lib.mdj_merge(None, 0, None, 0, 8, None, None, ctypes.byref(res)) == -1
+    cols = (MdjCol * 1)()
+    cols[0].data = None
+    cols[0].dtype = 2  # I64, zero rows: null data allowed
+    t = MdjTable(cols, 1, 0)
+    assert lib.mdj_merge(ctypes.byref(t), 1, ctypes.byref(t), 0, 8, None, None, ctypes.byref(res)) == -1
+    assert lib.mdj_merge(ctypes.byref(t), 0, ctypes.byref(t), 0, 0, None, None, ctypes.byref(res)) == -1
+    assert lib.mdj_merge(ctypes.byref(t), 0, ctypes.byref(t), 0, 65537, None, None, ctypes.byref(res)) == -1
+    fcols = (MdjCol * 1)()
+    fcols[0].dtype = 4  # F64 key
+    ft = MdjTable(fcols, 1, 0)
+    assert lib.mdj_merge(ctypes.byref(ft), 0, ctypes.byref(ft), 0, 8, None, None, ctypes.byref(res)) == -2
+    icols = (MdjCol * 1)()
+    icols[0].dtype = 1  # I32 key vs I64 key
+    it = MdjTable(icols, 1, 0)
+    assert lib.mdj_merge(ctypes.byref(t), 0, ctypes.byref(it), 0, 8, None, None, ctypes.byref(res)) == -1
+    big = MdjTable(cols, 1, 1 << 32)
+    assert lib.mdj_merge(ctypes.byref(big), 0, ctypes.byref(t), 0, 8, None, None, ctypes.byref(res)) == -3
+    bad = (MdjCol * 1)()
+    bad[0].dtype = 99
+    bt = MdjTable(bad, 1, 0)
+    assert lib.mdj_partition(ctypes.byref(bt), 0, 4, None, None, None, None, None) == -2
+    many = MdjTable(cols, 17, 0)
+    assert lib.mdj_join(ctypes.byref(many), 0, ctypes.byref(t), 0, None, None, ctypes.byref(res)) == -1

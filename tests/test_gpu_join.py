@@ -1,0 +1,174 @@
+"""mdj_join / mdj_merge / mdj_count_checksum against the oracle, bit for bit
+after the canonical sort by (key, left_row, right_row)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from joinhelp import assert_same_result, gpu_result_np
+from paper_2101_08878_gb300 import datagen
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+I64_MIN, I64_MAX = np.iinfo(np.int64).min, np.iinfo(np.int64).max
+
+
+def _mdj():
+    from paper_2101_08878_gb300 import mdj
+    return mdj
+
+
+def _dev(cols):
+    return [torch.from_numpy(np.ascontiguousarray(c)).to(DEV) for c in cols]
+
+
+def _run(left, right, P=None, lk=0, rk=0):
+    mdj = _mdj()
+    if P is None:
+        res = mdj.mdj_join(_dev(left), _dev(right), lk, rk)
+    else:
+        res = mdj.mdj_merge(_dev(left), _dev(right), P, lk, rk)
+    torch.cuda.synchronize()
+    return gpu_result_np(res)
+
+
+def _check(left, right, P=None, lk=0, rk=0):
+    got = _run(left, right, P, lk, rk)
+    want = oracle.merge_table(left, right, lk, rk)
+    assert_same_result(got, want)
+    return got
+
+
+# ------------------------------------------------------------- small / edge
+
+@pytest.mark.parametrize("P", [None, 1, 8])
+@pytest.mark.parametrize("nl,nr", [(0, 0), (0, 100), (100, 0), (1, 1), (7, 5)])
+def test_empty_and_tiny(P, nl, nr):
+    (lk, lp), (rk, rp) = datagen.random_tables(nl, nr, 4, seed=nl * 31 + nr)
+    _check([lk, lp], [rk, rp], P)
+
+
+@pytest.mark.parametrize("P", [None, 1, 8, 64])
+@pytest.mark.parametrize("key_range", [3, 100, 10_000, 10**9])
+def test_duplicates(P, key_range):
+    (lk, lp), (rk, rp) = datagen.random_tables(3000, 5000, key_range, seed=key_range)
+    _check([lk, lp], [rk, rp], P)
+
+
+@pytest.mark.parametrize("P", [None, 8, 1000, 1024, 2000])
+def test_match_fraction_several_buckets(P):
+    (lk, lp), (rk, rp) = datagen.match_fraction_tables(200_000, 300_000, 0.3, seed=7)
+    got = _check([lk, lp], [rk, rp], P)
+    assert got["key"].size == math.floor(0.3 * 300_000)
+
+
+def test_int32_keys_f32_payloads_multi_column():
+    rng = np.random.default_rng(3)
+    (lk, lp), (rk, rp) = datagen.random_tables(40_000, 60_000, 20_000, seed=3, key_dtype=np.int32,
+                                               pay_dtype=np.float32)
+    l_extra = rng.integers(0, 2**63 - 1, lk.size, dtype=np.int64)
+    r_extra = rng.integers(-2**31, 2**31 - 1, rk.size).astype(np.int32)
+    # key in the middle of the left table, last on the right
+    left = [lp, lk, l_extra]
+    right = [rp, r_extra, rk]
+    _check(left, right, None, 1, 2)
+    _check(left, right, 32, 1, 2)
+
+
+def test_extreme_keys_and_nan_payloads():
+    rng = np.random.default_rng(4)
+    ext = np.array([I64_MIN, I64_MAX, 0, -1, I64_MIN + 1, I64_MAX - 1], np.int64)
+    lk = rng.choice(ext, 3000)
+    rk = rng.choice(ext, 2000)
+    lp = datagen.uniform_payload(rng, lk.size)
+    rp = datagen.uniform_payload(rng, rk.size)
+    lp.view(np.uint64)[::3] = np.uint64(0x7FF8000000000001)
+    rp.view(np.uint64)[::5] = np.uint64(0xFFF0DEADBEEF0000)
+    _check([lk, lp], [rk, rp], None)
+    _check([lk, lp], [rk, rp], 8)
+
+
+def test_heavy_key_exceeding_one_table():
+    # one key repeated more times than one shared-memory table holds: the
+    # bucket is split into several build chunks
+    rng = np.random.default_rng(5)
+    lk = np.concatenate([np.full(20_000, 42, np.int64), rng.integers(0, 10**6, 5000)])
+    rk = np.concatenate([np.full(300, 42, np.int64), rng.integers(0, 10**6, 5000)])
+    rng.shuffle(lk)
+    rng.shuffle(rk)
+    got = _check([lk, datagen.uniform_payload(rng, lk.size)], [rk, datagen.uniform_payload(rng, rk.size)], 4)
+    assert got["key"].size >= 20_000 * 300
+
+
+def test_P_invariance():
+    (lk, lp), (rk, rp) = datagen.zipf_tables(30_000, 50_000, 5_000, 1.1, seed=6)
+    base = _run([lk, lp], [rk, rp], None)
+    for P in (1, 3, 8, 64, 1025):
+        got = _run([lk, lp], [rk, rp], P)
+        assert_same_result(got, base)
+
+
+def test_two_level_plan():
+    # enough build rows that the plan needs a second partition pass
+    (lk, lp), (rk, rp) = datagen.match_fraction_tables(4_000_000, 2_000_000, 0.3, seed=8)
+    got = _check([lk, lp], [rk, rp], 8)
+    assert got["key"].size == math.floor(0.3 * 2_000_000)
+
+
+def test_config0_plain_merge_P1():
+    # plain inner merge, P = 1: 1M x 1M, unique left keys, match fraction 0.3
+    (lk, lp), (rk, rp) = datagen.match_fraction_tables(1_000_000, 1_000_000, 0.3, seed=0)
+    got = _check([lk, lp], [rk, rp], 1)
+    assert got["key"].size == 300_000
+
+
+def test_deterministic_for_unique_left():
+    (lk, lp), (rk, rp) = datagen.match_fraction_tables(100_000, 100_000, 0.5, seed=9)
+    mdj = _mdj()
+    a = mdj.mdj_merge(_dev([lk, lp]), _dev([rk, rp]), 8)
+    b = mdj.mdj_merge(_dev([lk, lp]), _dev([rk, rp]), 8)
+    assert torch.equal(a.key, b.key) and torch.equal(a.left_row, b.left_row)
+    assert torch.equal(a.right_row, b.right_row)
+
+
+# ---------------------------------------------------------- count/checksum
+
+@pytest.mark.parametrize("P", [1, 8, 64])
+@pytest.mark.parametrize("pay", [np.float64, np.float32])
+def test_count_checksum(P, pay):
+    (lk, lp), (rk, rp) = datagen.zipf_tables(40_000, 80_000, 3_000, 1.1, seed=P, pay_dtype=pay)
+    mdj = _mdj()
+    got = mdj.mdj_count_checksum(_dev([lk, lp]), _dev([rk, rp]), P)
+    assert got == oracle.count_checksum(lk, lp, rk, rp)
+
+
+def test_count_checksum_key_only_tables():
+    (lk, _), (rk, _) = datagen.random_tables(5000, 7000, 300, seed=12)
+    mdj = _mdj()
+    got = mdj.mdj_count_checksum(_dev([lk]), _dev([rk]), 8)
+    # no payload column: payload bits are 0 on both sides
+    want = oracle.count_checksum(lk, np.zeros(lk.size, np.uint64), rk, np.zeros(rk.size, np.uint64))
+    assert got == want
+
+
+# ------------------------------------------------------------------ errors
+
+def test_invalid_arguments():
+    mdj = _mdj()
+    k64 = torch.arange(10, device=DEV)
+    k32 = k64.int()
+    with pytest.raises(mdj.MdjError) as e:
+        mdj.mdj_merge([k64], [k32], 8)  # key dtype mismatch
+    assert e.value.status == -1
+    with pytest.raises(mdj.MdjError) as e:
+        mdj.mdj_merge([k64], [k64], 0)
+    assert e.value.status == -1
+    with pytest.raises(mdj.MdjError) as e:
+        mdj.mdj_merge([k64], [k64], 8, 1, 0)  # key column out of range
+    assert e.value.status == -1
+    with pytest.raises(mdj.MdjError) as e:
+        mdj.mdj_join([k64.float()], [k64.float()])
+    assert e.value.status == -2
