@@ -158,13 +158,19 @@ def cpu_baseline(n_sample: int, reps: int = 1):
 
 # --------------------------------------------------------------- GPU arm
 
-ALG_BYTES_PER_ROW = {
-    # kernel: bytes the method must move per input row of one side
-    "hist": KEY,                                  # read keys
-    "scatter_stable": (KEY + PAY) + (KEY + PAY + RID),  # read row, write row + row id
-    "scatter_reserve": (KEY + PAY + RID) * 2,     # second level: read + write row and row id
-    "join_count": KEY,                            # read keys (build or probe side)
-}
+def alg_bytes_per_launch(kernel: str, n_side: int, n_left: int, n_right: int, m: int):
+    """Bytes the method must move in one launch of `kernel` (8-byte keys and
+    payloads, 4-byte row ids); None for kernels outside the model."""
+    per_side = {
+        "hist": KEY,                                       # read keys
+        "scatter_stable": (KEY + PAY) + (KEY + PAY + RID),  # read row, write row + row id
+        "scatter_reserve": (KEY + PAY + RID) * 2,          # second level: read + write row and row id
+    }
+    if kernel in per_side:
+        return per_side[kernel] * n_side
+    if kernel in ("join_write", "join_write_exact"):
+        return (KEY + PAY + RID) * (n_left + n_right) + OUT_ROW * m  # read both sides, write the rows
+    return None
 
 
 def run_gpu(args):
@@ -233,8 +239,8 @@ def run_gpu(args):
     dom = max(prof.items(), key=lambda kv: kv[1][1])
     dom_name, (dom_launches, dom_ms) = dom
     per_launch_ms = dom_ms / max(dom_launches, 1)
-    per_row = ALG_BYTES_PER_ROW.get(dom_name)
-    achieved = per_row * N_LEFT / (per_launch_ms / 1e3) / 1e9 if per_row else None
+    alg = alg_bytes_per_launch(dom_name, N_LEFT, N_LEFT, N_RIGHT, m_expect)
+    achieved = alg / (per_launch_ms / 1e3) / 1e9 if alg else None
     traffic = measured_traffic(dom_name)
     b_alg_step = 64 * (N_LEFT + N_RIGHT) + OUT_ROW * m_expect
     roofline = {
@@ -242,7 +248,7 @@ def run_gpu(args):
         "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None,
         "traffic": traffic, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
         else "fallback 6800 GB/s", "launch_ms": round(per_launch_ms, 4),
-        "alg_bytes_per_launch": per_row * N_LEFT if per_row else None,
+        "alg_bytes_per_launch": alg,
     }
     step_roof = {"alg_bytes": b_alg_step, "achieved_gbs": round(b_alg_step / (ms_step / 1e3) / 1e9, 1),
                  "frac": round(b_alg_step / (ms_step / 1e3) / 1e9 / peak, 4)}
@@ -313,7 +319,7 @@ def measured_traffic(kernel: str):
         h = hashlib.sha256(open(os.path.join(src, kv["file"]), "rb").read()).hexdigest()[:16]
         if h != kv.get("src_sha"):
             return None
-        return int(float(kv["bytes_per_row"]) * N_LEFT)
+        return int(float(kv["bytes_per_unit"]) * N_LEFT)
     return None
 
 
@@ -359,9 +365,15 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=10_000_000)
     ap.add_argument("--ref-sample", type=int, default=2_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rows", type=int, default=None,
+                    help="rows per side (default 100M); smaller values are for profiling captures only")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mdj":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.rows:
+        global N_LEFT, N_RIGHT, WORKLOAD
+        N_LEFT = N_RIGHT = args.rows
+        WORKLOAD = WORKLOAD.replace("100M x 100M", f"{args.rows} x {args.rows}")
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -19,8 +19,9 @@ namespace mdj {
 // ------------------------------------------------------------------ limits
 
 constexpr uint32_t kMaxFanout = 1024;     // buckets of one stable scatter pass
+constexpr uint32_t kMergeFanout = 256;    // pass-1 buckets of a two-pass join plan
 constexpr uint32_t kMaxSubBuckets = 49152;  // final buckets of a two-pass plan
-constexpr uint32_t kPass2SpanMax = 2048;  // local buckets of one pass-2 tile
+constexpr uint32_t kPass2SpanMax = 1024;  // local buckets of one pass-2 tile
 
 // ------------------------------------------------------------------ hashing
 
@@ -44,19 +45,26 @@ __device__ __forceinline__ uint64_t key_bits(int64_t k) { return (uint64_t)k; }
 //   sb = p * S + floor(hi32(h) * S / 2^32)      (final sub-bucket, p-major)
 //   FB mode:    bucket = sb / div                (div = 1: the sub-bucket)
 //   DIGIT mode: bucket = (p / dmul) % dmod       (LSD digit of p)
+// With S = S1 * div, floor(x*S/2^32) / div = floor(x*S1/2^32) for any 32-bit x
+// (write x*S1 = s1*2^32 + lo: then x*S/2^32 = s1*div + lo*div/2^32 and
+// lo*div/2^32 < div), so the pass-1 bucket sb / div = p*S1 + floor(x*S1/2^32)
+// needs no division.
 struct BucketSpec {
   uint64_t P;
   uint64_t M;  // floor((2^64 - 1) / P), for the quotient estimate of h / P
   uint32_t S;
+  uint32_t S1;  // S / div
   uint32_t div;
   uint32_t dmul;
   uint32_t dmod;
+  int pow2;     // P is a power of two: h mod P = h & (P - 1)
   int digit_mode;
 };
 
 // h mod P by a one-correction Barrett reduction: q = umulhi(h, M) is the true
 // quotient or one less, so one conditional subtraction finishes.
 __device__ __forceinline__ uint32_t mod_p(uint64_t h, const BucketSpec &bs) {
+  if (bs.pow2) return (uint32_t)h & (uint32_t)(bs.P - 1);
   uint64_t q = __umul64hi(h, bs.M);
   uint64_t r = h - q * bs.P;
   if (r >= bs.P) r -= bs.P;
@@ -69,9 +77,9 @@ __device__ __forceinline__ uint32_t sub_bucket_of(uint64_t h, const BucketSpec &
 }
 
 __device__ __forceinline__ uint32_t bucket_of(uint64_t h, const BucketSpec &bs) {
-  if (bs.digit_mode) return (mod_p(h, bs) / bs.dmul) % bs.dmod;
-  uint32_t sb = sub_bucket_of(h, bs);
-  return bs.div == 1 ? sb : sb / bs.div;
+  uint32_t p = mod_p(h, bs);
+  if (bs.digit_mode) return (p / bs.dmul) % bs.dmod;
+  return p * bs.S1 + __umulhi((uint32_t)(h >> 32), bs.S1);
 }
 
 BucketSpec make_spec(uint32_t P, uint32_t S, uint32_t div);

@@ -2,21 +2,27 @@
 // (Sec. V-B: "a merge operation is carried out" after the shuffle).
 //
 // Both sides are bucketed with the same hash (partition p, then sub-bucket),
-// so equal keys share a bucket.  A work item is (bucket, chunk of at most
-// `cap` build rows); one block builds a hash table of that chunk in shared
-// memory and streams the bucket's probe rows past it.  Two passes:
+// so equal keys share a bucket.  A work item is (bucket, chunk of at most `cap`
+// build rows, chunk of probe rows); one block builds a hash table of the build
+// chunk in shared memory and probes the probe chunk against it.
 //
-//   count  - matches per item (and, for mdj_count_checksum, the pair checksum);
-//            an exclusive scan of the counts gives every item's output offset,
-//            and the grand total is the one value read back to the host
-//   write  - the same build + probe, each probe row writing its matches at its
-//            block-scanned position (output columns are structure-of-arrays)
+// Output (the two phases of a count-then-write materialisation, fused per
+// item): an item first counts its matches (block scan over its probe rows),
+// then learns where its rows go from the items before it by a decoupled
+// look-back over per-item counts (items are taken in order from an atomic
+// ticket, so every predecessor is already running; every wait is bounded), and
+// writes them there.  The output buffer is sized optimistically (max(n_L, n_R)
+// rows, exact whenever build keys are unique); if the join is larger, the
+// counts are already known, so one exact write pass at the recorded item
+// offsets follows.  The grand total is the one value read back to the host.
 //
 // Table layout (per block, shared memory): build keys keys_s[cap]; slot words
 // (tag16 << 16 | head+1) over 2^k >= 2*rows slots with linear probing; one
 // slot per DISTINCT key, with its member count cnt[] and a member chain nxt[]
 // through the build rows, so duplicate keys cost one slot and the probe finds a
-// key in O(1) however many copies it has.
+// key in O(1) however many copies it has.  Slots and tags come from a cheap
+// multiplicative hash of the key: bucket membership was already randomised by
+// the partition hash.
 #include <string.h>
 
 #include "mdj_internal.cuh"
@@ -25,10 +31,14 @@ namespace mdj {
 namespace {
 
 constexpr int kJoinThreads = 512;
+constexpr int kPF = 8;                                   // probe rows per thread per round
+constexpr uint32_t kWriteChunk = kPF * kJoinThreads;     // probe rows per write item (one round)
+constexpr uint32_t kCountChunk = 65536;                  // probe rows per count item
 constexpr uint32_t kDefaultCap = 4096;
 constexpr uint32_t kMaxCap = 16384;
-constexpr uint32_t kRightChunk = 65536;  // probe rows per work item
-constexpr int MODE_COUNT = 0, MODE_CHECKSUM = 1, MODE_WRITE = 2;
+constexpr uint64_t kWaitLimitNs = 1000000000ull;         // look-back wait bound: 1 s of device time
+constexpr uint32_t kPollLimit = 1u << 26;                // and a poll-count bound as a backstop
+constexpr uint64_t kFlagAgg = 1ull << 62, kFlagInc = 2ull << 62, kValMask = (1ull << 62) - 1;
 
 struct JSide {
   const void *key;
@@ -47,13 +57,21 @@ struct JOut {
   void *rcols[MDJ_MAX_COLS];
 };
 
+struct Item {
+  uint32_t lbeg, nl, rbeg, nr;
+};
+
+// flags[] words shared by the join kernels and the host
+enum { FLAG_OVERFLOW = 0, FLAG_TIMEOUT = 1, FLAG_ABORT = 2, FLAG_WORDS = 4 };
+
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 template <typename KeyT>
-size_t join_smem_bytes(uint32_t cap, int mode) {
-  const size_t t = 2 * (size_t)cap;
+size_t join_smem_bytes(uint32_t cap, bool fsum) {
+  size_t t = 32;
+  while (t < 2 * (size_t)cap) t *= 2;  // slots of the largest table
   size_t b = align16((size_t)cap * sizeof(KeyT) + (size_t)cap * 2) + t * 8;
-  if (mode == MODE_CHECKSUM) b += t * 8;
+  if (fsum) b += t * 8;
   return b;
 }
 
@@ -70,200 +88,370 @@ __device__ __forceinline__ uint64_t term_g(uint32_t rrow, uint64_t pbits) {
   return fmix64((0xC2B2AE3D27D4EB4FULL * ((uint64_t)rrow + 1)) ^ pbits);
 }
 
-// Work items of bucket b: ceil(nl / cap) build chunks x ceil(nr / kRightChunk)
-// probe chunks (0 when either side is empty).
+// In-table position: top logt bits of key * golden-ratio constant; tag: bits 32..47.
+__device__ __forceinline__ void slot_tag(uint64_t kb, uint32_t logt, uint32_t &slot, uint32_t &tag) {
+  const uint64_t g = kb * 0x9E3779B97F4A7C15ULL;
+  slot = (uint32_t)(g >> (64 - logt));
+  tag = (uint32_t)(g >> 32) & 0xFFFFu;
+}
+
+// ------------------------------------------------------------- work items
+
+// Items of bucket b: ceil(nl / cap) build chunks x ceil(nr / rch) probe chunks
+// (0 when either side is empty).
 __global__ void k_items(const uint32_t *__restrict__ offL, const uint32_t *__restrict__ offR, uint32_t nb, uint32_t cap,
-                        uint64_t *__restrict__ items) {
+                        uint32_t rch, uint64_t *__restrict__ items) {
   uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b < nb) {
     uint64_t nl = offL[b + 1] - offL[b], nr = offR[b + 1] - offR[b];
-    items[b] = (nl && nr) ? ((nl + cap - 1) / cap) * ((nr + kRightChunk - 1) / kRightChunk) : 0ull;
+    items[b] = (nl && nr) ? ((nl + cap - 1) / cap) * ((nr + rch - 1) / rch) : 0ull;
   } else if (b == nb) {
     items[nb] = 0;
   }
 }
 
-template <typename KeyT, int MODE>
-__global__ void __launch_bounds__(kJoinThreads, 2)
-    k_join(JSide L, JSide R, const uint64_t *__restrict__ item_off, uint32_t nb, uint32_t nitems, uint32_t cap,
-           uint64_t *__restrict__ item_cnt, unsigned long long *__restrict__ chk, const uint64_t *__restrict__ out_off,
-           JOut out) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  KeyT *keys_s = (KeyT *)smem;
-  uint16_t *nxt = (uint16_t *)(smem + (size_t)cap * sizeof(KeyT));
-  uint32_t *slots = (uint32_t *)(smem + align16((size_t)cap * sizeof(KeyT) + (size_t)cap * 2));
-  uint32_t *cnt = slots + 2 * cap;
-  uint64_t *fsum = (uint64_t *)(cnt + 2 * cap);
-  __shared__ uint32_t s_item[3];
-  __shared__ uint32_t scratch32[33];
-  __shared__ uint64_t scratch64[33];
-
-  const KeyT *__restrict__ Lkey = (const KeyT *)L.key;
-  const KeyT *__restrict__ Rkey = (const KeyT *)R.key;
-  for (uint32_t it = blockIdx.x; it < nitems; it += gridDim.x) {
-    if (threadIdx.x == 0) {
-      uint32_t lo = 0, hi = nb - 1;  // last bucket b with item_off[b] <= it
-      while (lo < hi) {
-        uint32_t mid = (lo + hi + 1) / 2;
-        if (item_off[mid] <= it)
-          lo = mid;
-        else
-          hi = mid - 1;
-      }
-      const uint32_t local = (uint32_t)(it - item_off[lo]);
-      const uint32_t nr = R.off[lo + 1] - R.off[lo];
-      const uint32_t nrc = (nr + kRightChunk - 1) / kRightChunk;
-      s_item[0] = lo;
-      s_item[1] = local / nrc;
-      s_item[2] = local % nrc;
+// One descriptor per item: its build and probe row ranges.
+__global__ void k_expand(const uint32_t *__restrict__ offL, const uint32_t *__restrict__ offR, uint32_t nb,
+                         uint32_t cap, uint32_t rch, const uint64_t *__restrict__ item_off, uint32_t nitems,
+                         Item *__restrict__ desc) {
+  for (uint32_t it = blockIdx.x * blockDim.x + threadIdx.x; it < nitems; it += gridDim.x * blockDim.x) {
+    uint32_t lo = 0, hi = nb - 1;  // last bucket b with item_off[b] <= it
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) / 2;
+      if (item_off[mid] <= it)
+        lo = mid;
+      else
+        hi = mid - 1;
     }
-    __syncthreads();
-    const uint32_t b = s_item[0], lc = s_item[1], rc = s_item[2];
-    const uint32_t lbeg = L.off[b] + lc * cap;
-    const uint32_t lend = (uint32_t)min((uint64_t)lbeg + cap, (uint64_t)L.off[b + 1]);
-    const uint32_t nl = lend - lbeg;
-    const uint32_t rbeg = R.off[b] + rc * kRightChunk;
-    const uint32_t rend = (uint32_t)min((uint64_t)rbeg + kRightChunk, (uint64_t)R.off[b + 1]);
-    uint32_t logt = 5;
-    while ((1u << logt) < 2 * nl) logt++;
-    const uint32_t tsz = 1u << logt, mask = tsz - 1;
+    const uint32_t local = (uint32_t)(it - item_off[lo]);
+    const uint32_t nl = offL[lo + 1] - offL[lo], nr = offR[lo + 1] - offR[lo];
+    const uint32_t nrc = (nr + rch - 1) / rch;
+    const uint32_t lc = local / nrc, rc = local % nrc;
+    Item d;
+    d.lbeg = offL[lo] + lc * cap;
+    d.nl = min(cap, nl - lc * cap);
+    d.rbeg = offR[lo] + rc * rch;
+    d.nr = min(rch, nr - rc * rch);
+    desc[it] = d;
+  }
+}
 
-    // ---- build
-    for (uint32_t i = threadIdx.x; i < nl; i += blockDim.x) keys_s[i] = Lkey[lbeg + i];
-    for (uint32_t s = threadIdx.x; s < tsz; s += blockDim.x) {
-      slots[s] = 0;
-      cnt[s] = 0;
-      if (MODE == MODE_CHECKSUM) fsum[s] = 0;
+// ------------------------------------------------------------ table build
+
+template <typename KeyT>
+__device__ __forceinline__ uint32_t table_log(uint32_t nl) {
+  uint32_t logt = 5;
+  while ((1u << logt) < 2 * nl) logt++;
+  return logt;
+}
+
+// Loads the build keys into shared memory and clears 2^logt slots.
+template <typename KeyT, bool FSUM>
+__device__ __forceinline__ void load_and_clear(const KeyT *__restrict__ Lkey, uint32_t lbeg, uint32_t nl, uint32_t tsz,
+                                               KeyT *keys_s, uint32_t *slots, uint32_t *cnt, uint64_t *fsum) {
+  const uint32_t nthr = blockDim.x, tid = threadIdx.x;
+  for (uint32_t i0 = 0; i0 < nl; i0 += 4 * nthr) {
+    KeyT v[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const uint32_t i = i0 + u * nthr + tid;
+      v[u] = i < nl ? Lkey[lbeg + i] : KeyT(0);
     }
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < nl; i += blockDim.x) {
-      const KeyT k = keys_s[i];
-      const uint64_t h = fmix64(key_bits(k));
-      const uint32_t tag = (uint32_t)(h >> 32) & 0xFFFFu;
-      const uint32_t w = (tag << 16) | (i + 1);
-      uint32_t s = (uint32_t)h >> (32 - logt);
-      for (uint32_t probe = 0; probe < tsz; probe++) {
-        uint32_t cur = slots[s];
-        if (cur == 0) {
-          uint32_t prev = atomicCAS(&slots[s], 0u, w);
-          if (prev == 0) {
-            nxt[i] = 0;
-            break;
-          }
-          cur = prev;
-        }
-        if ((cur >> 16) == tag && keys_s[(cur & 0xFFFFu) - 1] == k) {
-          uint32_t prev = atomicExch(&slots[s], w);
-          nxt[i] = (uint16_t)(prev & 0xFFFFu);
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const uint32_t i = i0 + u * nthr + tid;
+      if (i < nl) keys_s[i] = v[u];
+    }
+  }
+  uint4 z = make_uint4(0, 0, 0, 0);
+  for (uint32_t s = tid * 4; s < tsz; s += nthr * 4) {
+    *(uint4 *)(slots + s) = z;
+    *(uint4 *)(cnt + s) = z;
+  }
+  if (FSUM)
+    for (uint32_t s = tid * 2; s < tsz; s += nthr * 2) *(uint4 *)(fsum + s) = z;
+}
+
+// One slot per distinct key; rows of a key are chained through nxt[] (head =
+// the slot word's index, most recent insert first) and counted in cnt[].
+template <typename KeyT, bool FSUM>
+__device__ __forceinline__ void build_table(const KeyT *keys_s, uint32_t nl, uint32_t logt, uint32_t *slots,
+                                            uint32_t *cnt, uint16_t *nxt, uint64_t *fsum, const JSide &L,
+                                            uint32_t lbeg) {
+  const uint32_t mask = (1u << logt) - 1;
+  for (uint32_t i = threadIdx.x; i < nl; i += blockDim.x) {
+    const KeyT k = keys_s[i];
+    uint32_t s, tag;
+    slot_tag(key_bits(k), logt, s, tag);
+    const uint32_t w = (tag << 16) | (i + 1);
+    for (uint32_t probe = 0; probe <= mask; probe++) {
+      uint32_t cur = slots[s];
+      if (cur == 0) {
+        const uint32_t prev = atomicCAS(&slots[s], 0u, w);
+        if (prev == 0) {
+          nxt[i] = 0;
           break;
         }
-        s = (s + 1) & mask;
+        cur = prev;
       }
-      atomicAdd(&cnt[s], 1u);
-      if (MODE == MODE_CHECKSUM) {
-        const uint32_t lr = L.rid ? L.rid[lbeg + i] : lbeg + i;
-        const uint64_t pb = L.ncols > 0 ? pay_bits(L.cols[0], L.width[0], lbeg + i) : 0ull;
-        atomicAdd((unsigned long long *)&fsum[s], (unsigned long long)term_f(key_bits(k), lr, pb));
+      if ((cur >> 16) == tag && keys_s[(cur & 0xFFFFu) - 1] == k) {
+        const uint32_t prev = atomicExch(&slots[s], w);
+        nxt[i] = (uint16_t)(prev & 0xFFFFu);
+        break;
       }
+      s = (s + 1) & mask;
     }
-    __syncthreads();
+    atomicAdd(&cnt[s], 1u);
+    if (FSUM) {
+      const uint32_t lr = L.rid ? L.rid[lbeg + i] : lbeg + i;
+      const uint64_t pb = L.ncols > 0 ? pay_bits(L.cols[0], L.width[0], lbeg + i) : 0ull;
+      atomicAdd((unsigned long long *)&fsum[s], (unsigned long long)term_f(key_bits(k), lr, pb));
+    }
+  }
+}
 
-    // ---- probe
-    if (MODE != MODE_WRITE) {
-      uint64_t acc = 0, csum = 0;
-      for (uint32_t r = rbeg + threadIdx.x; r < rend; r += blockDim.x) {
-        const KeyT k = Rkey[r];
-        const uint64_t h = fmix64(key_bits(k));
-        const uint32_t tag = (uint32_t)(h >> 32) & 0xFFFFu;
-        uint32_t s = (uint32_t)h >> (32 - logt);
-        for (uint32_t probe = 0; probe < tsz; probe++) {
-          const uint32_t w = slots[s];
-          if (w == 0) break;
-          if ((w >> 16) == tag && keys_s[(w & 0xFFFFu) - 1] == k) {
-            acc += cnt[s];
-            if (MODE == MODE_CHECKSUM) {
+// Probe: slot of key k (or where the search ended) and the chain head (0: absent).
+template <typename KeyT>
+__device__ __forceinline__ uint32_t probe_table(const KeyT k, const KeyT *keys_s, const uint32_t *slots, uint32_t logt,
+                                                uint32_t &slot_out) {
+  const uint32_t mask = (1u << logt) - 1;
+  uint32_t s, tag;
+  slot_tag(key_bits(k), logt, s, tag);
+  uint32_t head = 0;
+  for (uint32_t probe = 0; probe <= mask; probe++) {
+    const uint32_t w = slots[s];
+    if (w == 0) break;
+    if ((w >> 16) == tag && keys_s[(w & 0xFFFFu) - 1] == k) {
+      head = w & 0xFFFFu;
+      break;
+    }
+    s = (s + 1) & mask;
+  }
+  slot_out = s;
+  return head;
+}
+
+__device__ __forceinline__ uint32_t next_ticket(uint32_t *ticket, uint32_t *s_it) {
+  if (threadIdx.x == 0) *s_it = atomicAdd(ticket, 1u);
+  __syncthreads();
+  const uint32_t it = *s_it;
+  __syncthreads();
+  return it;
+}
+
+// ---------------------------------------------------- count (+ checksum)
+
+// Pair count (and pair checksum) of every item, summed into totals[0..1].
+template <typename KeyT, bool CHECKSUM>
+__global__ void __launch_bounds__(kJoinThreads, 2)
+    k_join_count(JSide L, JSide R, const Item *__restrict__ desc, uint32_t nitems, uint32_t *ticket,
+                 unsigned long long *totals) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t s_it;
+  const KeyT *__restrict__ Lkey = (const KeyT *)L.key;
+  const KeyT *__restrict__ Rkey = (const KeyT *)R.key;
+  const uint32_t nthr = blockDim.x, tid = threadIdx.x;
+  for (;;) {
+    const uint32_t it = next_ticket(ticket, &s_it);
+    if (it >= nitems) break;
+    const Item d = desc[it];
+    const uint32_t logt = table_log<KeyT>(d.nl), tsz = 1u << logt;
+    KeyT *keys_s = (KeyT *)smem;
+    uint16_t *nxt = (uint16_t *)(smem + (size_t)d.nl * sizeof(KeyT));
+    uint32_t *slots = (uint32_t *)(smem + align16((size_t)d.nl * (sizeof(KeyT) + 2)));
+    uint32_t *cnt = slots + tsz;
+    uint64_t *fsum = (uint64_t *)(cnt + tsz);
+    load_and_clear<KeyT, CHECKSUM>(Lkey, d.lbeg, d.nl, tsz, keys_s, slots, cnt, fsum);
+    __syncthreads();
+    build_table<KeyT, CHECKSUM>(keys_s, d.nl, logt, slots, cnt, nxt, fsum, L, d.lbeg);
+    __syncthreads();
+    uint64_t acc = 0, csum = 0;
+    for (uint32_t r0 = d.rbeg; r0 < d.rbeg + d.nr; r0 += kPF * nthr) {
+      KeyT rk[kPF];
+#pragma unroll
+      for (int j = 0; j < kPF; j++) {
+        const uint32_t r = r0 + j * nthr + tid;
+        rk[j] = r < d.rbeg + d.nr ? Rkey[r] : KeyT(0);
+      }
+#pragma unroll
+      for (int j = 0; j < kPF; j++) {
+        const uint32_t r = r0 + j * nthr + tid;
+        if (r < d.rbeg + d.nr) {
+          uint32_t slot;
+          if (probe_table<KeyT>(rk[j], keys_s, slots, logt, slot)) {
+            acc += cnt[slot];
+            if (CHECKSUM) {
               const uint32_t rr = R.rid ? R.rid[r] : r;
               const uint64_t pb = R.ncols > 0 ? pay_bits(R.cols[0], R.width[0], r) : 0ull;
-              csum += term_g(rr, pb) * fsum[s];
+              csum += term_g(rr, pb) * fsum[slot];
             }
-            break;
-          }
-          s = (s + 1) & mask;
-        }
-      }
-      acc = warp_sum(acc);
-      if (MODE == MODE_CHECKSUM) csum = warp_sum(csum);
-      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-      if (lane == 0) {
-        scratch64[warp] = acc;
-        if (MODE == MODE_CHECKSUM) scratch64[16 + warp] = csum;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        uint64_t a = 0, c = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
-          a += scratch64[w];
-          if (MODE == MODE_CHECKSUM) c += scratch64[16 + w];
-        }
-        item_cnt[it] = a;
-        if (MODE == MODE_CHECKSUM) atomicAdd(chk, (unsigned long long)c);
-      }
-    } else {
-      uint64_t base = out_off[it];
-      KeyT *okey = (KeyT *)out.key;
-      for (uint32_t r0 = rbeg; r0 < rend; r0 += blockDim.x) {
-        const uint32_t r = r0 + threadIdx.x;
-        uint32_t c = 0, head = 0;
-        KeyT k = KeyT(0);
-        if (r < rend) {
-          k = Rkey[r];
-          const uint64_t h = fmix64(key_bits(k));
-          const uint32_t tag = (uint32_t)(h >> 32) & 0xFFFFu;
-          uint32_t s = (uint32_t)h >> (32 - logt);
-          for (uint32_t probe = 0; probe < tsz; probe++) {
-            const uint32_t w = slots[s];
-            if (w == 0) break;
-            if ((w >> 16) == tag && keys_s[(w & 0xFFFFu) - 1] == k) {
-              c = cnt[s];
-              head = w & 0xFFFFu;
-              break;
-            }
-            s = (s + 1) & mask;
           }
         }
-        uint32_t tot;
-        const uint32_t ex = block_exclusive_scan<uint32_t>(c, scratch32, &tot);
-        if (c) {
-          const uint64_t pos0 = base + ex;
-          const uint32_t rr = R.rid ? R.rid[r] : r;
-          uint32_t li = head - 1;
-          for (uint32_t q = 0; q < c; q++) {
-            const uint64_t pos = pos0 + q;
-            const uint32_t lrow = lbeg + li;
-            okey[pos] = k;
-            out.lrow[pos] = L.rid ? L.rid[lrow] : lrow;
-            out.rrow[pos] = rr;
-            for (int j = 0; j < L.ncols; j++) {
-              if (L.width[j] == 8)
-                ((uint64_t *)out.lcols[j])[pos] = ((const uint64_t *)L.cols[j])[lrow];
-              else
-                ((uint32_t *)out.lcols[j])[pos] = ((const uint32_t *)L.cols[j])[lrow];
-            }
-            for (int j = 0; j < R.ncols; j++) {
-              if (R.width[j] == 8)
-                ((uint64_t *)out.rcols[j])[pos] = ((const uint64_t *)R.cols[j])[r];
-              else
-                ((uint32_t *)out.rcols[j])[pos] = ((const uint32_t *)R.cols[j])[r];
-            }
-            li = (uint32_t)nxt[li] - 1;
-          }
+      }
+    }
+    acc = warp_sum(acc);
+    if (CHECKSUM) csum = warp_sum(csum);
+    if ((tid & 31) == 0) {
+      if (acc) atomicAdd(&totals[0], (unsigned long long)acc);
+      if (CHECKSUM && csum) atomicAdd(&totals[1], (unsigned long long)csum);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ fused write
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Exclusive output offset of item `it` whose own count is `total`: publish the
+// count, then walk back over predecessors until one whose inclusive prefix is
+// known.  Bounded: after kWaitLimitNs (or kPollLimit polls) the wait is
+// abandoned, FLAG_TIMEOUT and FLAG_ABORT are set (other waiters then stop
+// too) and ~0 is returned.  `withhold_first` (test hook) keeps item 0 from
+// publishing, so that every later wait runs out.
+__device__ uint64_t look_back(unsigned long long *state, uint32_t it, uint64_t total, int *flags,
+                              int withhold_first) {
+  volatile unsigned long long *vs = state;
+  if (it == 0) {
+    if (withhold_first) return ~0ull;
+    __threadfence();
+    atomicExch(&state[0], kFlagInc | total);
+    return 0;
+  }
+  __threadfence();
+  atomicExch(&state[it], kFlagAgg | total);
+  uint64_t excl = 0;
+  uint32_t j = it - 1;
+  uint32_t polls = 0;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    const unsigned long long v = vs[j];
+    const uint64_t flag = v & ~kValMask;
+    if (flag == 0) {
+      if (++polls > kPollLimit || global_ns() - t0 > kWaitLimitNs || ((volatile int *)flags)[FLAG_ABORT]) {
+        atomicExch(&flags[FLAG_TIMEOUT], 1);
+        atomicExch(&flags[FLAG_ABORT], 1);
+        return ~0ull;
+      }
+      __nanosleep(64);
+      continue;
+    }
+    excl += v & kValMask;
+    if (flag == kFlagInc || j == 0) break;
+    j--;
+  }
+  __threadfence();
+  atomicExch(&state[it], kFlagInc | (excl + total));
+  return excl;
+}
+
+// Build + probe + write of every item.  HAVE_OFFSETS = false: the fused pass
+// (offsets by look-back, rows written only while they fit `capacity`);
+// HAVE_OFFSETS = true: the exact pass at offsets recorded by the fused pass.
+template <typename KeyT, bool HAVE_OFFSETS>
+__global__ void __launch_bounds__(kJoinThreads, 2)
+    k_join_write(JSide L, JSide R, const Item *__restrict__ desc, uint32_t nitems, uint32_t *ticket,
+                 unsigned long long *state, uint64_t *__restrict__ item_off, unsigned long long *total,
+                 uint64_t capacity, int *flags, int withhold_first, JOut out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t s_it;
+  __shared__ uint32_t scratch32[33];
+  __shared__ uint64_t s_base;
+  const KeyT *__restrict__ Lkey = (const KeyT *)L.key;
+  const KeyT *__restrict__ Rkey = (const KeyT *)R.key;
+  KeyT *okey = (KeyT *)out.key;
+  const uint32_t nthr = blockDim.x, tid = threadIdx.x;
+  for (;;) {
+    const uint32_t it = next_ticket(ticket, &s_it);
+    if (it >= nitems) break;
+    const Item d = desc[it];
+    const uint32_t logt = table_log<KeyT>(d.nl), tsz = 1u << logt;
+    KeyT *keys_s = (KeyT *)smem;
+    uint16_t *nxt = (uint16_t *)(smem + (size_t)d.nl * sizeof(KeyT));
+    uint32_t *slots = (uint32_t *)(smem + align16((size_t)d.nl * (sizeof(KeyT) + 2)));
+    uint32_t *cnt = slots + tsz;
+
+    // probe keys first (one round: d.nr <= kPF * nthr), then the build chunk
+    KeyT rk[kPF];
+#pragma unroll
+    for (int j = 0; j < kPF; j++) {
+      const uint32_t r = j * nthr + tid;
+      rk[j] = r < d.nr ? Rkey[d.rbeg + r] : KeyT(0);
+    }
+    load_and_clear<KeyT, false>(Lkey, d.lbeg, d.nl, tsz, keys_s, slots, cnt, nullptr);
+    __syncthreads();
+    build_table<KeyT, false>(keys_s, d.nl, logt, slots, cnt, nxt, nullptr, L, d.lbeg);
+    __syncthreads();
+
+    uint32_t c[kPF], hd[kPF], mine = 0;
+#pragma unroll
+    for (int j = 0; j < kPF; j++) {
+      const uint32_t r = j * nthr + tid;
+      c[j] = 0;
+      hd[j] = 0;
+      if (r < d.nr) {
+        uint32_t slot;
+        hd[j] = probe_table<KeyT>(rk[j], keys_s, slots, logt, slot);
+        if (hd[j]) c[j] = cnt[slot];
+      }
+      mine += c[j];
+    }
+    uint32_t tot;
+    const uint32_t ex = block_exclusive_scan<uint32_t>(mine, scratch32, &tot);
+    if (tid == 0) {
+      uint64_t base;
+      if (HAVE_OFFSETS) {
+        base = item_off[it];
+      } else {
+        base = look_back(state, it, tot, flags, withhold_first);
+        if (base != ~0ull) {
+          item_off[it] = base;
+          if (tot) atomicAdd(total, (unsigned long long)tot);
+          if (base + tot > capacity) atomicExch(&flags[FLAG_OVERFLOW], 1);
         }
-        base += tot;
+      }
+      s_base = base;
+    }
+    __syncthreads();
+    const uint64_t base = s_base;
+    if (base != ~0ull && base + tot <= capacity && mine) {
+      uint64_t pos = base + ex;
+#pragma unroll
+      for (int j = 0; j < kPF; j++) {
+        if (!c[j]) continue;
+        const uint32_t r = d.rbeg + j * nthr + tid;
+        const uint32_t rr = R.rid ? R.rid[r] : r;
+        uint32_t li = hd[j] - 1;
+        for (uint32_t q = 0; q < c[j]; q++, pos++) {
+          const uint32_t lrow = d.lbeg + li;
+          okey[pos] = rk[j];
+          out.lrow[pos] = L.rid ? L.rid[lrow] : lrow;
+          out.rrow[pos] = rr;
+          for (int cc = 0; cc < L.ncols; cc++) {
+            if (L.width[cc] == 8)
+              ((uint64_t *)out.lcols[cc])[pos] = ((const uint64_t *)L.cols[cc])[lrow];
+            else
+              ((uint32_t *)out.lcols[cc])[pos] = ((const uint32_t *)L.cols[cc])[lrow];
+          }
+          for (int cc = 0; cc < R.ncols; cc++) {
+            if (R.width[cc] == 8)
+              ((uint64_t *)out.rcols[cc])[pos] = ((const uint64_t *)R.cols[cc])[r];
+            else
+              ((uint32_t *)out.rcols[cc])[pos] = ((const uint32_t *)R.cols[cc])[r];
+          }
+          li = (uint32_t)nxt[li] - 1;
+        }
       }
     }
     __syncthreads();
   }
 }
+
+// ------------------------------------------------------------------- host
 
 JSide to_jside(const Side &s) {
   JSide j;
@@ -279,43 +467,27 @@ JSide to_jside(const Side &s) {
   return j;
 }
 
-template <typename KeyT>
-int set_join_attrs(uint32_t cap) {
-  static uint32_t done_cap = 0;
-  if (done_cap >= cap) return MDJ_OK;
-  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_join<KeyT, MODE_COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)join_smem_bytes<KeyT>(cap, MODE_COUNT)));
-  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_join<KeyT, MODE_WRITE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)join_smem_bytes<KeyT>(cap, MODE_WRITE)));
-  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_join<KeyT, MODE_CHECKSUM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)join_smem_bytes<KeyT>(cap, MODE_CHECKSUM)));
-  done_cap = cap;
+template <typename KernelT>
+int resident_grid(KernelT kernel, size_t smem, uint64_t nitems, int *grid) {
+  int per_sm = 0;
+  MDJ_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  MDJ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kJoinThreads, smem));
+  if (per_sm < 1) return MDJ_ERR_INTERNAL;
+  uint64_t g = (uint64_t)num_sms() * per_sm;
+  if (g > nitems) g = nitems;
+  *grid = (int)(g ? g : 1);
   return MDJ_OK;
 }
 
-int join_grid(size_t smem, uint32_t max_items) {
-  int per_sm = (int)((227 * 1024) / (smem + 1024));
-  if (per_sm < 1) per_sm = 1;
-  if (per_sm > 4) per_sm = 4;
-  uint64_t g = (uint64_t)num_sms() * per_sm;
-  if (g > max_items) g = max_items;
-  return (int)(g ? g : 1);
-}
-
-// count (or checksum) pass + scan + readback; then the write pass.
-template <typename KeyT>
-int run_join(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, bool checksum_mode,
-             mdj_result *res, uint64_t *count, uint64_t *checksum) {
+// Work items of the whole join, with `rch` probe rows per item at most.
+int make_items(Workspace &ws, const Side &Ls, const Side &Rs, uint32_t nb, uint32_t cap, uint32_t rch, Item **desc,
+               uint32_t *nitems_out) {
   cudaStream_t s = ws.stream();
-  const uint32_t nb = plan.nbuckets, cap = plan.cap;
-  MDJ_TRY(set_join_attrs<KeyT>(cap));
-  const JSide L = to_jside(Ls), R = to_jside(Rs);
-
   uint64_t *item_off = (uint64_t *)ws.get((size_t)(nb + 1) * 8);
   if (!item_off) return MDJ_ERR_OOM;
   {
     TraceScope tr("join_items", s);
-    k_items<<<(nb + 1 + 255) / 256, 256, 0, s>>>(Ls.off, Rs.off, nb, cap, item_off);
+    k_items<<<(nb + 1 + 255) / 256, 256, 0, s>>>(Ls.off, Rs.off, nb, cap, rch, item_off);
   }
   MDJ_LAUNCH_CHECK();
   MDJ_TRY(exclusive_scan_u64(ws, item_off, item_off, nb + 1));
@@ -323,82 +495,159 @@ int run_join(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, bo
   MDJ_CUDA_TRY(cudaMemcpyAsync(&nitems, item_off + nb, 8, cudaMemcpyDeviceToHost, s));
   MDJ_CUDA_TRY(cudaStreamSynchronize(s));
   if (nitems >= (1ull << 31)) return MDJ_ERR_TOO_LARGE;
-  const uint64_t max_items = nitems;
-
-  uint64_t *item_cnt = (uint64_t *)ws.get((size_t)(max_items + 1) * 8);
-  unsigned long long *chk = (unsigned long long *)ws.get(16);
-  if (!item_cnt || !chk) return MDJ_ERR_OOM;
-  MDJ_CUDA_TRY(cudaMemsetAsync(item_cnt, 0, (size_t)(max_items + 1) * 8, s));
-  MDJ_CUDA_TRY(cudaMemsetAsync(chk, 0, 16, s));
-
-  JOut none;
-  memset(&none, 0, sizeof none);
-  if (checksum_mode) {
-    const size_t sm = join_smem_bytes<KeyT>(cap, MODE_CHECKSUM);
-    TraceScope tr("join_checksum", s);
-    k_join<KeyT, MODE_CHECKSUM><<<join_grid(sm, (uint32_t)max_items), kJoinThreads, sm, s>>>(
-        L, R, item_off, nb, (uint32_t)nitems, cap, item_cnt, chk, nullptr, none);
-  } else {
-    const size_t sm = join_smem_bytes<KeyT>(cap, MODE_COUNT);
-    TraceScope tr("join_count", s);
-    k_join<KeyT, MODE_COUNT><<<join_grid(sm, (uint32_t)max_items), kJoinThreads, sm, s>>>(
-        L, R, item_off, nb, (uint32_t)nitems, cap, item_cnt, nullptr, nullptr, none);
+  *nitems_out = (uint32_t)nitems;
+  *desc = (Item *)ws.get((size_t)(nitems ? nitems : 1) * sizeof(Item));
+  if (!*desc) return MDJ_ERR_OOM;
+  if (nitems) {
+    TraceScope tr("join_expand", s);
+    const uint64_t want = (nitems + 255) / 256, most = (uint64_t)num_sms() * 8;
+    const unsigned g = (unsigned)(want < most ? want : most);
+    k_expand<<<g, 256, 0, s>>>(Ls.off, Rs.off, nb, cap, rch, item_off, (uint32_t)nitems, *desc);
   }
   MDJ_LAUNCH_CHECK();
-  MDJ_TRY(exclusive_scan_u64(ws, item_cnt, item_cnt, max_items + 1));
+  ws.give_back(item_off);
+  return MDJ_OK;
+}
 
-  uint64_t host[2] = {0, 0};
-  MDJ_CUDA_TRY(cudaMemcpyAsync(&host[0], item_cnt + max_items, 8, cudaMemcpyDeviceToHost, s));
-  if (checksum_mode) MDJ_CUDA_TRY(cudaMemcpyAsync(&host[1], chk, 8, cudaMemcpyDeviceToHost, s));
+template <typename KeyT>
+int run_count(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, uint64_t *count, uint64_t *checksum) {
+  cudaStream_t s = ws.stream();
+  Item *desc;
+  uint32_t nitems;
+  MDJ_TRY(make_items(ws, Ls, Rs, plan.nbuckets, plan.cap, kCountChunk, &desc, &nitems));
+  unsigned long long *tot = (unsigned long long *)ws.get(32);
+  if (!tot) return MDJ_ERR_OOM;
+  MDJ_CUDA_TRY(cudaMemsetAsync(tot, 0, 32, s));
+  uint32_t *ticket = (uint32_t *)(tot + 2);
+  if (nitems) {
+    const size_t sm = join_smem_bytes<KeyT>(plan.cap, true);
+    int grid;
+    MDJ_TRY(resident_grid(k_join_count<KeyT, true>, sm, nitems, &grid));
+    TraceScope tr("join_checksum", s);
+    k_join_count<KeyT, true><<<grid, kJoinThreads, sm, s>>>(to_jside(Ls), to_jside(Rs), desc, nitems, ticket, tot);
+  }
+  MDJ_LAUNCH_CHECK();
+  unsigned long long host[2] = {0, 0};
+  MDJ_CUDA_TRY(cudaMemcpyAsync(host, tot, 16, cudaMemcpyDeviceToHost, s));
   MDJ_CUDA_TRY(cudaStreamSynchronize(s));
-  const uint64_t m = host[0];
-  if (checksum_mode) {
-    *count = m;
-    *checksum = host[1];
-    return MDJ_OK;
-  }
-  if (count) *count = m;
+  *count = host[0];
+  *checksum = host[1];
+  return MDJ_OK;
+}
 
-  // ---- outputs (owned by the caller)
+int alloc_result(Workspace &ws, const Side &Ls, const Side &Rs, size_t key_width, uint64_t rows, mdj_result *r,
+                 JOut *o) {
+  memset(r, 0, sizeof *r);
+  r->key_dtype = Ls.key_dtype;
+  r->n_left_cols = Ls.ncols;
+  r->n_right_cols = Rs.ncols;
+  for (int j = 0; j < Ls.ncols; j++) r->left_dtypes[j] = Ls.dtypes[j];
+  for (int j = 0; j < Rs.ncols; j++) r->right_dtypes[j] = Rs.dtypes[j];
+  memset(o, 0, sizeof *o);
+  if (rows == 0) return MDJ_OK;
+  bool ok = (r->key = ws.get_owned_by_caller(rows * key_width)) != nullptr;
+  ok = ok && (r->left_row = (uint32_t *)ws.get_owned_by_caller(rows * 4)) != nullptr;
+  ok = ok && (r->right_row = (uint32_t *)ws.get_owned_by_caller(rows * 4)) != nullptr;
+  for (int j = 0; ok && j < Ls.ncols; j++) ok = (r->left_cols[j] = ws.get_owned_by_caller(rows * Ls.widths[j])) != nullptr;
+  for (int j = 0; ok && j < Rs.ncols; j++) ok = (r->right_cols[j] = ws.get_owned_by_caller(rows * Rs.widths[j])) != nullptr;
+  if (!ok) {
+    mdj_result_release(r, ws.allocator(), (void *)ws.stream());
+    return MDJ_ERR_OOM;
+  }
+  o->key = r->key;
+  o->lrow = r->left_row;
+  o->rrow = r->right_row;
+  for (int j = 0; j < Ls.ncols; j++) o->lcols[j] = r->left_cols[j];
+  for (int j = 0; j < Rs.ncols; j++) o->rcols[j] = r->right_cols[j];
+  return MDJ_OK;
+}
+
+// Test hook: MDJ_TEST_WITHHOLD_FIRST_ITEM=1 makes item 0 of the fused write
+// pass never publish its count, so every look-back wait must run out and the
+// call must report MDJ_ERR_DEVICE_TIMEOUT with the context still usable.
+int test_withhold_first() {
+  const char *e = getenv("MDJ_TEST_WITHHOLD_FIRST_ITEM");
+  return e && e[0] == '1';
+}
+
+// Rows of the optimistic output buffer of the fused pass: max(n_L, n_R), the
+// exact bound when build keys are unique (MDJ_OUTPUT_ROWS overrides).
+uint64_t output_capacity_hint(uint64_t nl, uint64_t nr) {
+  uint64_t c = nl > nr ? nl : nr;
+  const char *e = getenv("MDJ_OUTPUT_ROWS");
+  if (e) {
+    long long v = atoll(e);
+    if (v >= 0) c = (uint64_t)v;
+  }
+  return c;
+}
+
+template <typename KeyT>
+int run_join(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, mdj_result *res) {
+  cudaStream_t s = ws.stream();
+  Item *desc;
+  uint32_t nitems;
+  MDJ_TRY(make_items(ws, Ls, Rs, plan.nbuckets, plan.cap, kWriteChunk, &desc, &nitems));
+  // state[nitems] | item_off[nitems] | total | ticket | flags
+  const size_t words = 2 * (size_t)nitems + 4;
+  unsigned long long *state = (unsigned long long *)ws.get(words * 8);
+  if (!state) return MDJ_ERR_OOM;
+  MDJ_CUDA_TRY(cudaMemsetAsync(state, 0, words * 8, s));
+  uint64_t *item_off = (uint64_t *)(state + nitems);
+  unsigned long long *total = state + 2 * (size_t)nitems;
+  uint32_t *ticket = (uint32_t *)(total + 1);
+  int *flags = (int *)(total + 2);
+
+  const uint64_t cap_rows = output_capacity_hint(Ls.nrows, Rs.nrows);
   mdj_result r;
-  memset(&r, 0, sizeof r);
-  r.nrows = m;
-  r.key_dtype = Ls.key_dtype;
-  r.n_left_cols = Ls.ncols;
-  r.n_right_cols = Rs.ncols;
-  for (int j = 0; j < Ls.ncols; j++) r.left_dtypes[j] = Ls.dtypes[j];
-  for (int j = 0; j < Rs.ncols; j++) r.right_dtypes[j] = Rs.dtypes[j];
-  if (m > 0) {
-    bool ok = true;
-    r.key = ws.get_owned_by_caller(m * sizeof(KeyT));
-    r.left_row = (uint32_t *)ws.get_owned_by_caller(m * 4);
-    r.right_row = (uint32_t *)ws.get_owned_by_caller(m * 4);
-    ok = r.key && r.left_row && r.right_row;
-    for (int j = 0; ok && j < Ls.ncols; j++) ok = (r.left_cols[j] = ws.get_owned_by_caller(m * Ls.widths[j])) != nullptr;
-    for (int j = 0; ok && j < Rs.ncols; j++) ok = (r.right_cols[j] = ws.get_owned_by_caller(m * Rs.widths[j])) != nullptr;
-    if (!ok) {
-      mdj_result_release(&r, ws.allocator(), (void *)s);
-      return MDJ_ERR_OOM;
-    }
-    JOut o;
-    memset(&o, 0, sizeof o);
-    o.key = r.key;
-    o.lrow = r.left_row;
-    o.rrow = r.right_row;
-    for (int j = 0; j < Ls.ncols; j++) o.lcols[j] = r.left_cols[j];
-    for (int j = 0; j < Rs.ncols; j++) o.rcols[j] = r.right_cols[j];
-    const size_t sm = join_smem_bytes<KeyT>(cap, MODE_WRITE);
-    {
-      TraceScope tr("join_write", s);
-      k_join<KeyT, MODE_WRITE><<<join_grid(sm, (uint32_t)max_items), kJoinThreads, sm, s>>>(
-          L, R, item_off, nb, (uint32_t)nitems, cap, nullptr, nullptr, item_cnt, o);
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
-      mdj_result_release(&r, ws.allocator(), (void *)s);
-      return cuda_status(e);
+  JOut o;
+  MDJ_TRY(alloc_result(ws, Ls, Rs, sizeof(KeyT), cap_rows, &r, &o));
+  const size_t sm = join_smem_bytes<KeyT>(plan.cap, false);
+  if (nitems) {
+    int grid;
+    MDJ_TRY(resident_grid(k_join_write<KeyT, false>, sm, nitems, &grid));
+    TraceScope tr("join_write", s);
+    k_join_write<KeyT, false><<<grid, kJoinThreads, sm, s>>>(to_jside(Ls), to_jside(Rs), desc, nitems, ticket,
+                                                             state, item_off, total, cap_rows, flags,
+                                                             test_withhold_first(), o);
+  }
+  cudaError_t e = cudaGetLastError();
+  unsigned long long host_total = 0;
+  int host_flags[FLAG_WORDS] = {0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&host_total, total, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host_flags, flags, sizeof host_flags, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    mdj_result_release(&r, ws.allocator(), (void *)s);
+    return cuda_status(e);
+  }
+  if (host_flags[FLAG_TIMEOUT]) {
+    mdj_result_release(&r, ws.allocator(), (void *)s);
+    return MDJ_ERR_DEVICE_TIMEOUT;
+  }
+  const uint64_t m = host_total;
+  if (m > cap_rows || m == 0) {
+    // the join outgrew the optimistic buffer (or is empty): exact buffers,
+    // then one write pass at the offsets the fused pass recorded
+    mdj_result_release(&r, ws.allocator(), (void *)s);
+    MDJ_TRY(alloc_result(ws, Ls, Rs, sizeof(KeyT), m, &r, &o));
+    if (m > 0) {
+      int grid;
+      MDJ_TRY(resident_grid(k_join_write<KeyT, true>, sm, nitems, &grid));
+      MDJ_CUDA_TRY(cudaMemsetAsync(ticket, 0, 4, s));
+      {
+        TraceScope tr("join_write_exact", s);
+        k_join_write<KeyT, true><<<grid, kJoinThreads, sm, s>>>(to_jside(Ls), to_jside(Rs), desc, nitems, ticket,
+                                                                state, item_off, total, m, flags, 0, o);
+      }
+      e = cudaGetLastError();
+      if (e != cudaSuccess) {
+        mdj_result_release(&r, ws.allocator(), (void *)s);
+        return cuda_status(e);
+      }
     }
   }
+  r.nrows = m;
   *res = r;
   return MDJ_OK;
 }
@@ -447,8 +696,10 @@ int merge_impl(const mdj_table *left, int32_t lk, const mdj_table *right, int32_
   Side L, R;
   MDJ_TRY(partition_side(ws, left, lk, plan, &L));
   MDJ_TRY(partition_side(ws, right, rk, plan, &R));
-  if (left->cols[lk].dtype == MDJ_I64) return run_join<int64_t>(ws, L, R, plan, checksum_mode, out, count, checksum);
-  return run_join<int32_t>(ws, L, R, plan, checksum_mode, out, count, checksum);
+  const bool k64 = left->cols[lk].dtype == MDJ_I64;
+  if (checksum_mode)
+    return k64 ? run_count<int64_t>(ws, L, R, plan, count, checksum) : run_count<int32_t>(ws, L, R, plan, count, checksum);
+  return k64 ? run_join<int64_t>(ws, L, R, plan, out) : run_join<int32_t>(ws, L, R, plan, out);
 }
 
 }  // namespace

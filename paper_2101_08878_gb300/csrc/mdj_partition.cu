@@ -24,8 +24,8 @@ namespace mdj {
 namespace {
 
 constexpr int kNW = 16;                     // warps per scatter block
-constexpr int kRPL = 16;                    // rows per lane per tile
-constexpr uint32_t kTile = kNW * 32 * kRPL; // 8192 rows per tile
+constexpr int kRPL = 8;                     // rows per lane per tile
+constexpr uint32_t kTile = kNW * 32 * kRPL; // 4096 rows per tile
 constexpr int kHistThreads = 512;
 
 struct ColMove {
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(const KeyT *__restrict__ 
   uint32_t *cnt2 = sh + F;
   if (total2)
     for (uint32_t i = threadIdx.x; i < nsub; i += blockDim.x) cnt2[i] = 0;
-  constexpr int U = 4;
+  constexpr int U = 8;
   for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     for (uint32_t b = threadIdx.x; b < F; b += blockDim.x) cnt[b] = 0;
     __syncthreads();
@@ -69,20 +69,16 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(const KeyT *__restrict__ 
 #pragma unroll
       for (int u = 0; u < U; u++) {
         uint32_t r = base + u * blockDim.x + threadIdx.x;
-        bool valid = r < end;
-        uint32_t b = 0xFFFFFFFFu;
-        if (valid) {
-          uint64_t h = fmix64(key_bits(kv[u]));
+        if (r < end) {
+          const uint64_t h = fmix64(key_bits(kv[u]));
           if (total2) {
-            uint32_t sb = sub_bucket_of(h, bs);
-            b = bs.div == 1 ? sb : sb / bs.div;
-            atomicAdd(&cnt2[sb], 1u);
+            const uint32_t p = mod_p(h, bs), x = (uint32_t)(h >> 32);
+            atomicAdd(&cnt[p * bs.S1 + __umulhi(x, bs.S1)], 1u);
+            atomicAdd(&cnt2[p * bs.S + __umulhi(x, bs.S)], 1u);
           } else {
-            b = bucket_of(h, bs);
+            atomicAdd(&cnt[bucket_of(h, bs)], 1u);
           }
         }
-        uint32_t peers = __match_any_sync(0xffffffffu, b);
-        if (valid && (peers & lanemask_lt()) == 0) atomicAdd(&cnt[b], (uint32_t)__popc(peers));
       }
     }
     __syncthreads();
@@ -132,7 +128,7 @@ __device__ void scatter_direct(const KeyT (&kv)[kRPL], uint32_t wrow0, uint32_t 
 }
 
 template <typename KeyT, bool RESERVE>
-__global__ void __launch_bounds__(kNW * 32, 1)
+__global__ void __launch_bounds__(kNW * 32, 2)
     k_scatter(const KeyT *__restrict__ keys, uint32_t n, BucketSpec bs, uint32_t F, uint32_t ntiles,
               const uint32_t *__restrict__ tile_base, uint32_t *__restrict__ cursors, uint32_t F2, ColMove cm,
               const uint32_t *__restrict__ rid_in, uint32_t *__restrict__ rid_out) {
@@ -608,7 +604,8 @@ Plan make_plan(uint64_t n_build, uint32_t P, uint32_t cap, bool force_partition)
     pl.nbuckets = pl.F1;
     return pl;
   }
-  uint32_t S1 = kMaxFanout / P;
+  uint32_t S1 = kMergeFanout / P;
+  if (S1 < 1) S1 = 1;
   uint64_t F2 = (S + S1 - 1) / S1;
   uint64_t max_f2 = kMaxSubBuckets / ((uint64_t)P * S1);
   if (F2 > max_f2) F2 = max_f2;  // larger inputs: sub-buckets split into several tables

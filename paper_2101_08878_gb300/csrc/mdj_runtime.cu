@@ -84,9 +84,11 @@ BucketSpec make_spec(uint32_t P, uint32_t S, uint32_t div) {
   b.P = P;
   b.M = UINT64_MAX / P;
   b.S = S;
+  b.S1 = S / div;
   b.div = div;
   b.dmul = 1;
   b.dmod = 1;
+  b.pow2 = (P & (P - 1)) == 0;
   b.digit_mode = 0;
   return b;
 }

@@ -172,3 +172,24 @@ def test_invalid_arguments():
     with pytest.raises(mdj.MdjError) as e:
         mdj.mdj_join([k64.float()], [k64.float()])
     assert e.value.status == -2
+
+
+def test_output_buffer_overflow_takes_exact_pass(monkeypatch):
+    # an optimistic buffer smaller than the join forces the exact second pass
+    (lk, lp), (rk, rp) = datagen.match_fraction_tables(50_000, 70_000, 0.5, seed=21)
+    monkeypatch.setenv("MDJ_OUTPUT_ROWS", "1000")
+    got = _check([lk, lp], [rk, rp], 8)
+    assert got["key"].size == 35_000
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(monkeypatch):
+    # item 0 withholds its count (test hook): every look-back wait must give up
+    # after its bound, the call must say so, and the next call must work
+    (lk, lp), (rk, rp) = datagen.match_fraction_tables(100_000, 100_000, 0.3, seed=22)
+    mdj = _mdj()
+    monkeypatch.setenv("MDJ_TEST_WITHHOLD_FIRST_ITEM", "1")
+    with pytest.raises(mdj.MdjError) as e:
+        mdj.mdj_merge(_dev([lk, lp]), _dev([rk, rp]), 8)
+    assert e.value.status == -6
+    monkeypatch.delenv("MDJ_TEST_WITHHOLD_FIRST_ITEM")
+    _check([lk, lp], [rk, rp], 8)
