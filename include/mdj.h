@@ -139,6 +139,36 @@ MDJ_API int mdj_partition(const mdj_table *in, int32_t key_col, uint32_t P,
                   const mdj_allocator *alloc, void *stream);
 
 /*
+ * mdj_partition_noalloc - mdj_partition for callers that cannot allocate.
+ * The paper has no counterpart to this call; it exists for users of the
+ * library.  Some callers may not call cudaMalloc or any other device
+ * allocator where they need a partition: code that runs inside another
+ * framework's memory pool which owns the device budget, loops where an
+ * allocation could stall the device or fail half-way, or plugins that their
+ * host process keeps away from the allocator.  They own their inputs and
+ * outputs but cannot supply working memory, so this call takes its working
+ * memory from a fixed array inside the library and allocates nothing
+ * (no cudaMalloc / cudaMallocAsync / cudaFree, no allocator callback).
+ *   Arguments and results are those of mdj_partition (same stable layout, same
+ *   out_offsets), without the allocator.
+ *   Limits: 1 <= P <= 1024, and the working set must fit the 16 MiB array:
+ *   P * T + ceil(P * T / 4096) + P + 1 <= 4194304 words, T = ceil(nrows / 4096)
+ *   (e.g. up to 16.7M rows at P = 1024, any nrows < 2^32 at P = 8).  Larger
+ *   inputs return MDJ_ERR_TOO_LARGE before any work; P > 1024 returns
+ *   MDJ_ERR_INVALID_ARG.
+ *   The array (16 MiB of device memory) is held on every GPU that loads the
+ *   library until the process exits.  The first call on a device looks up the
+ *   array's device address (a one-time set-up for that device, done with it
+ *   current); make that first call before any stream capture.  All calls on a
+ *   device share the one array and leave their data in it: calls whose GPU work
+ *   can overlap (other streams, other threads) race and must be ordered by the
+ *   caller.
+ */
+MDJ_API int mdj_partition_noalloc(const mdj_table *in, int32_t key_col, uint32_t P,
+                                  void *const *out_cols, uint32_t *out_row_ids,
+                                  int64_t *out_offsets, void *stream);
+
+/*
  * mdj_join - the per-partition merge (Sec. V-B: "a merge operation is carried
  * out" on the co-located partitions).  Inner equi-join of `left` (build side)
  * and `right` (probe side) on left column `left_key` = right column

@@ -241,6 +241,15 @@ int partition_side(Workspace &ws, const mdj_table *t, int32_t key_col, const Pla
 int stable_partition(Workspace &ws, const mdj_table *t, int32_t key_col, uint32_t P,
                      void *const *out_cols, uint32_t *out_rid, int64_t *out_offsets);
 
+// Allocation-free variants (caller-provided device scratch), used only by
+// mdj_partition_noalloc: words of scratch needed, and the calls themselves.
+size_t scan_scratch_words(size_t n);
+int exclusive_scan_u32_scratch(const uint32_t *in, uint32_t *out, size_t n, uint32_t *sums, cudaStream_t s);
+size_t stable_partition_scratch_words(uint64_t n, uint32_t P);
+int stable_partition_scratch(const mdj_table *t, int32_t key_col, uint32_t P, void *const *out_cols,
+                             uint32_t *out_rid, int64_t *out_offsets, uint32_t *scratch, size_t scratch_words,
+                             cudaStream_t s);
+
 // Exclusive scans (out may equal in).  n may be 0.
 int exclusive_scan_u32(Workspace &ws, const uint32_t *in, uint32_t *out, size_t n);
 int exclusive_scan_u64(Workspace &ws, const uint64_t *in, uint64_t *out, size_t n);

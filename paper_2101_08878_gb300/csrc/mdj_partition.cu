@@ -631,3 +631,61 @@ int stable_partition(Workspace &ws, const mdj_table *t, int32_t key_col, uint32_
 }
 
 }  // namespace mdj
+
+namespace mdj {
+namespace {
+
+template <typename KeyT>
+int stable_partition_scratch_t(const mdj_table *t, int32_t key_col, uint32_t P, void *const *out_cols,
+                               uint32_t *out_rid, int64_t *out_offsets, uint32_t *scratch, size_t scratch_words,
+                               cudaStream_t s) {
+  const uint32_t n = (uint32_t)t->nrows, F = P;
+  const uint32_t ntiles = (n + kTile - 1) / kTile;
+  const size_t nhist = (size_t)F * ntiles;
+  if (stable_partition_scratch_words(n, P) > scratch_words) return MDJ_ERR_TOO_LARGE;
+  MDJ_TRY(set_smem_attrs<KeyT>());
+  uint32_t *hist = scratch;
+  uint32_t *sums = hist + nhist;
+  uint32_t *start = sums + scan_scratch_words(nhist);
+  if (ntiles == 0) {
+    MDJ_CUDA_TRY(cudaMemsetAsync(start, 0, (size_t)(F + 1) * 4, s));
+  } else {
+    const BucketSpec bs = make_spec(P, 1, 1);
+    const size_t hsmem = (size_t)F * 4;
+    const unsigned hgrid = (unsigned)(ntiles < (uint32_t)hist_grid(hsmem) ? ntiles : (uint32_t)hist_grid(hsmem));
+    k_hist<KeyT><<<hgrid, kHistThreads, hsmem, s>>>((const KeyT *)t->cols[key_col].data, n, bs, F, ntiles, hist,
+                                                   nullptr, 0);
+    MDJ_LAUNCH_CHECK();
+    MDJ_TRY(exclusive_scan_u32_scratch(hist, hist, nhist, sums, s));
+    k_bucket_starts<<<(F + 1 + 255) / 256, 256, 0, s>>>(hist, F, ntiles, n, start);
+    MDJ_LAUNCH_CHECK();
+    const void *src[MDJ_MAX_COLS];
+    for (int j = 0; j < t->ncols; j++) src[j] = t->cols[j].data;
+    ColMove cm = make_move(t, key_col, src, out_cols);
+    k_scatter<KeyT, false><<<ntiles, kNW * 32, scatter_smem_bytes(F), s>>>(
+        (const KeyT *)src[key_col], n, bs, F, ntiles, hist, nullptr, 1, cm, nullptr, out_rid);
+    MDJ_LAUNCH_CHECK();
+  }
+  k_u32_to_i64<<<(P + 1 + 255) / 256, 256, 0, s>>>(start, out_offsets, P + 1);
+  MDJ_LAUNCH_CHECK();
+  return MDJ_OK;
+}
+
+}  // namespace
+
+size_t stable_partition_scratch_words(uint64_t n, uint32_t P) {
+  const uint64_t nhist = (uint64_t)P * ((n + kTile - 1) / kTile);
+  return (size_t)(nhist + scan_scratch_words(nhist) + P + 1);
+}
+
+int stable_partition_scratch(const mdj_table *t, int32_t key_col, uint32_t P, void *const *out_cols,
+                             uint32_t *out_rid, int64_t *out_offsets, uint32_t *scratch, size_t scratch_words,
+                             cudaStream_t s) {
+  if (t->cols[key_col].dtype == MDJ_I64)
+    return stable_partition_scratch_t<int64_t>(t, key_col, P, out_cols, out_rid, out_offsets, scratch,
+                                               scratch_words, s);
+  return stable_partition_scratch_t<int32_t>(t, key_col, P, out_cols, out_rid, out_offsets, scratch, scratch_words,
+                                             s);
+}
+
+}  // namespace mdj

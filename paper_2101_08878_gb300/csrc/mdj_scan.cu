@@ -99,3 +99,22 @@ int exclusive_scan_u64(Workspace &ws, const uint64_t *in, uint64_t *out, size_t 
 }
 
 }  // namespace mdj
+
+namespace mdj {
+
+// Scan with caller-provided scratch for the chunk sums (no allocation):
+// scan_scratch_words(n) words at `sums`.  Used by the allocation-free
+// partition entry point.
+size_t scan_scratch_words(size_t n) { return n ? (n + kScanChunk - 1) / kScanChunk : 0; }
+
+int exclusive_scan_u32_scratch(const uint32_t *in, uint32_t *out, size_t n, uint32_t *sums, cudaStream_t s) {
+  if (n == 0) return MDJ_OK;
+  const size_t nb = (n + kScanChunk - 1) / kScanChunk;
+  k_scan_reduce<uint32_t><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums);
+  k_scan_sums<uint32_t><<<1, kScanThreads, 0, s>>>(sums, nb);
+  k_scan_down<uint32_t><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, sums);
+  MDJ_LAUNCH_CHECK();
+  return MDJ_OK;
+}
+
+}  // namespace mdj

@@ -34,7 +34,7 @@ _TORCH_TO_MDJ = {
 _MDJ_TO_TORCH = {v: k for k, v in _TORCH_TO_MDJ.items()}
 
 EXPORTED = [
-    "mdj_partition", "mdj_join", "mdj_merge", "mdj_count_checksum", "mdj_result_release",
+    "mdj_partition", "mdj_partition_noalloc", "mdj_join", "mdj_merge", "mdj_count_checksum", "mdj_result_release",
     "mdj_status_string", "mdj_version", "mdj_profile_enable", "mdj_profile_reset",
     "mdj_profile_collect", "mdj_profile_count", "mdj_profile_get",
 ]
@@ -92,6 +92,8 @@ def load(path: str = LIB_PATH):
         P = ctypes.POINTER
         lib.mdj_partition.restype = ctypes.c_int
         lib.mdj_partition.argtypes = [P(MdjTable), i32, u32, P(vp), vp, vp, P(MdjAllocator), vp]
+        lib.mdj_partition_noalloc.restype = ctypes.c_int
+        lib.mdj_partition_noalloc.argtypes = [P(MdjTable), i32, u32, P(vp), vp, vp, vp]
         for name in ("mdj_join",):
             f = getattr(lib, name)
             f.restype = ctypes.c_int
