@@ -26,6 +26,7 @@
 #include <string.h>
 
 #include "mdj_internal.cuh"
+#include "mdj_tma.cuh"
 
 namespace mdj {
 namespace {
@@ -301,12 +302,6 @@ __global__ void __launch_bounds__(kJoinThreads, 2)
 
 // ------------------------------------------------------------ fused write
 
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
 // Exclusive output offset of item `it` whose own count is `total`: publish the
 // count, then walk back over predecessors until one whose inclusive prefix is
 // known.  Bounded: after kWaitLimitNs (or kPollLimit polls) the wait is
@@ -327,12 +322,12 @@ __device__ uint64_t look_back(unsigned long long *state, uint32_t it, uint64_t t
   uint64_t excl = 0;
   uint32_t j = it - 1;
   uint32_t polls = 0;
-  const uint64_t t0 = global_ns();
+  const uint64_t t0 = globaltimer_ns();
   for (;;) {
     const unsigned long long v = vs[j];
     const uint64_t flag = v & ~kValMask;
     if (flag == 0) {
-      if (++polls > kPollLimit || global_ns() - t0 > kWaitLimitNs || ((volatile int *)flags)[FLAG_ABORT]) {
+      if (++polls > kPollLimit || globaltimer_ns() - t0 > kWaitLimitNs || ((volatile int *)flags)[FLAG_ABORT]) {
         atomicExch(&flags[FLAG_TIMEOUT], 1);
         atomicExch(&flags[FLAG_ABORT], 1);
         return ~0ull;
@@ -349,103 +344,251 @@ __device__ uint64_t look_back(unsigned long long *state, uint32_t it, uint64_t t
   return excl;
 }
 
-// Build + probe + write of every item.  HAVE_OFFSETS = false: the fused pass
-// (offsets by look-back, rows written only while they fit `capacity`);
-// HAVE_OFFSETS = true: the exact pass at offsets recorded by the fused pass.
+// ------------------------------------------------------------ fused write
+//
+// Two 512-thread blocks per SM, so one block's global-memory phases overlap
+// the other's shared-memory phases.  Per item: load its build keys into
+// shared memory and its probe keys into registers, build, probe, block-scan
+// the match counts, reserve the item's output range, write.  Probe rows with
+// exactly one match (the common case) are written cooperatively from a
+// shared-memory match list, so consecutive threads store consecutive output
+// rows; rows with several matches are expanded by their own thread.  The
+// next item's ticket and descriptor are fetched while the current one runs.
+
+constexpr int kWT = 512;                        // threads of the write block
+constexpr int kWPF = 8;                         // probe rows per thread
+static_assert(kWPF * kWT == (int)kWriteChunk, "probe chunk = one round");
+
+template <typename KeyT>
+struct WriteLayout {
+  size_t keys, slots, nxt, list, total;
+  uint32_t tsz;  // slots of the largest table
+  __host__ __device__ WriteLayout(uint32_t cap) {
+    tsz = 32;
+    while (tsz < 2 * cap) tsz *= 2;
+    keys = 0;
+    slots = align16((size_t)cap * sizeof(KeyT));
+    nxt = slots + (size_t)tsz * 4;
+    list = align16(nxt + (size_t)cap * 2);
+    total = list + (size_t)kWriteChunk * 4;
+  }
+};
+
+// Write-pass table: 32-bit fold of the key, one multiply for the slot and
+// one for the tag.  (The count pass keeps the 64-bit hash and counters.)
+__device__ __forceinline__ void slot_tag32(uint64_t kb, uint32_t logt, uint32_t &slot, uint32_t &tag) {
+  const uint32_t f = (uint32_t)kb ^ (uint32_t)(kb >> 32);
+  slot = (f * 0x9E3779B1u) >> (32 - logt);
+  tag = (f * 0x85EBCA6Bu) >> 16;
+}
+
+// Slots hold (tag16 << 16 | head + 1); one slot per distinct key; rows of a
+// key are chained through nxt[] (0 ends the chain).
+template <typename KeyT>
+__device__ __forceinline__ void build_chain_table(const KeyT *keys, uint32_t nl, uint32_t logt, uint32_t *slots,
+                                                  uint16_t *nxt) {
+  const uint32_t mask = (1u << logt) - 1;
+  for (uint32_t i = threadIdx.x; i < nl; i += blockDim.x) {
+    const KeyT k = keys[i];
+    uint32_t s, tag;
+    slot_tag32(key_bits(k), logt, s, tag);
+    const uint32_t w = (tag << 16) | (i + 1);
+    for (uint32_t probe = 0; probe <= mask; probe++) {
+      uint32_t cur = slots[s];
+      if (cur == 0) {
+        const uint32_t prev = atomicCAS(&slots[s], 0u, w);
+        if (prev == 0) {
+          nxt[i] = 0;
+          break;
+        }
+        cur = prev;
+      }
+      if ((cur >> 16) == tag && keys[(cur & 0xFFFFu) - 1] == k) {
+        const uint32_t prev = atomicExch(&slots[s], w);
+        nxt[i] = (uint16_t)(prev & 0xFFFFu);
+        break;
+      }
+      s = (s + 1) & mask;
+    }
+  }
+}
+
+// Chain head (row index + 1) of key k, 0 if absent.
+template <typename KeyT>
+__device__ __forceinline__ uint32_t find_head(const KeyT k, const KeyT *keys, const uint32_t *slots, uint32_t logt) {
+  const uint32_t mask = (1u << logt) - 1;
+  uint32_t s, tag;
+  slot_tag32(key_bits(k), logt, s, tag);
+  for (uint32_t probe = 0; probe <= mask; probe++) {
+    const uint32_t w = slots[s];
+    if (w == 0) return 0;
+    if ((w >> 16) == tag && keys[(w & 0xFFFFu) - 1] == k) return w & 0xFFFFu;
+    s = (s + 1) & mask;
+  }
+  return 0;
+}
+
+__device__ __forceinline__ void copy_cols_row(const JSide &L, const JSide &R, const JOut &out, uint64_t pos,
+                                              uint32_t lrow, uint32_t r) {
+  out.lrow[pos] = L.rid ? L.rid[lrow] : lrow;
+  out.rrow[pos] = R.rid ? R.rid[r] : r;
+  for (int cc = 0; cc < L.ncols; cc++) {
+    if (L.width[cc] == 8)
+      ((uint64_t *)out.lcols[cc])[pos] = ((const uint64_t *)L.cols[cc])[lrow];
+    else
+      ((uint32_t *)out.lcols[cc])[pos] = ((const uint32_t *)L.cols[cc])[lrow];
+  }
+  for (int cc = 0; cc < R.ncols; cc++) {
+    if (R.width[cc] == 8)
+      ((uint64_t *)out.rcols[cc])[pos] = ((const uint64_t *)R.cols[cc])[r];
+    else
+      ((uint32_t *)out.rcols[cc])[pos] = ((const uint32_t *)R.cols[cc])[r];
+  }
+}
+
 template <typename KeyT, bool HAVE_OFFSETS>
-__global__ void __launch_bounds__(kJoinThreads, 2)
-    k_join_write(JSide L, JSide R, const Item *__restrict__ desc, uint32_t nitems, uint32_t *ticket,
+__global__ void __launch_bounds__(kWT, 2)
+    k_join_write(JSide L, JSide R, const Item *__restrict__ desc, uint32_t nitems, uint32_t cap, uint32_t *ticket,
                  unsigned long long *state, uint64_t *__restrict__ item_off, unsigned long long *total,
-                 uint64_t capacity, int *flags, int withhold_first, JOut out) {
+                 uint64_t capacity, int *flags, int withhold_first, int ordered, JOut out) {
   extern __shared__ __align__(16) unsigned char smem[];
+  const WriteLayout<KeyT> lay(cap);
+  KeyT *keys = (KeyT *)(smem + lay.keys);
+  uint32_t *slots = (uint32_t *)(smem + lay.slots);
+  uint16_t *nxt = (uint16_t *)(smem + lay.nxt);
+  uint32_t *list = (uint32_t *)(smem + lay.list);
+  __shared__ Item s_item;
   __shared__ uint32_t s_it;
-  __shared__ uint32_t scratch32[33];
   __shared__ uint64_t s_base;
+  __shared__ uint64_t scratch64[33];
+
   const KeyT *__restrict__ Lkey = (const KeyT *)L.key;
   const KeyT *__restrict__ Rkey = (const KeyT *)R.key;
   KeyT *okey = (KeyT *)out.key;
-  const uint32_t nthr = blockDim.x, tid = threadIdx.x;
+  const uint32_t tid = threadIdx.x;
+
+  if (tid == 0) {
+    s_it = atomicAdd(ticket, 1u);
+    if (s_it < nitems) s_item = desc[s_it];
+  }
+  __syncthreads();
   for (;;) {
-    const uint32_t it = next_ticket(ticket, &s_it);
+    const uint32_t it = s_it;
     if (it >= nitems) break;
-    const Item d = desc[it];
-    const uint32_t logt = table_log<KeyT>(d.nl), tsz = 1u << logt;
-    KeyT *keys_s = (KeyT *)smem;
-    uint16_t *nxt = (uint16_t *)(smem + (size_t)d.nl * sizeof(KeyT));
-    uint32_t *slots = (uint32_t *)(smem + align16((size_t)d.nl * (sizeof(KeyT) + 2)));
-    uint32_t *cnt = slots + tsz;
-
-    // probe keys first (one round: d.nr <= kPF * nthr), then the build chunk
-    KeyT rk[kPF];
-#pragma unroll
-    for (int j = 0; j < kPF; j++) {
-      const uint32_t r = j * nthr + tid;
-      rk[j] = r < d.nr ? Rkey[d.rbeg + r] : KeyT(0);
+    const Item d = s_item;
+    // next ticket: fetched now, published at the end of this item
+    uint32_t nx = 0;
+    Item dn = {0, 0, 0, 0};
+    if (tid == 0) {
+      nx = atomicAdd(ticket, 1u);
+      if (nx < nitems) dn = desc[nx];
     }
-    load_and_clear<KeyT, false>(Lkey, d.lbeg, d.nl, tsz, keys_s, slots, cnt, nullptr);
-    __syncthreads();
-    build_table<KeyT, false>(keys_s, d.nl, logt, slots, cnt, nxt, nullptr, L, d.lbeg);
-    __syncthreads();
-
-    uint32_t c[kPF], hd[kPF], mine = 0;
+    KeyT rk[kWPF];
 #pragma unroll
-    for (int j = 0; j < kPF; j++) {
-      const uint32_t r = j * nthr + tid;
-      c[j] = 0;
-      hd[j] = 0;
-      if (r < d.nr) {
-        uint32_t slot;
-        hd[j] = probe_table<KeyT>(rk[j], keys_s, slots, logt, slot);
-        if (hd[j]) c[j] = cnt[slot];
+    for (int j = 0; j < kWPF; j++) {
+      const uint32_t rl = j * kWT + tid;
+      rk[j] = rl < d.nr ? Rkey[d.rbeg + rl] : KeyT(0);
+    }
+    for (uint32_t i0 = 0; i0 < d.nl; i0 += 4 * kWT) {
+      KeyT v[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const uint32_t i = i0 + u * kWT + tid;
+        v[u] = i < d.nl ? Lkey[d.lbeg + i] : KeyT(0);
       }
-      mine += c[j];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const uint32_t i = i0 + u * kWT + tid;
+        if (i < d.nl) keys[i] = v[u];
+      }
     }
-    uint32_t tot;
-    const uint32_t ex = block_exclusive_scan<uint32_t>(mine, scratch32, &tot);
+    const uint32_t logt = table_log<KeyT>(d.nl), tsz = 1u << logt;
+    {
+      const uint4 z = make_uint4(0, 0, 0, 0);
+      for (uint32_t s = tid * 4; s < tsz; s += kWT * 4) *(uint4 *)(slots + s) = z;
+    }
+    __syncthreads();
+    build_chain_table<KeyT>(keys, d.nl, logt, slots, nxt);
+    __syncthreads();
+
+    // probe: head of each row's key; c = chain length (1 in the common case)
+    uint32_t c[kWPF], hd[kWPF];
+    uint32_t n1 = 0, nm = 0;
+#pragma unroll
+    for (int j = 0; j < kWPF; j++) {
+      const uint32_t rl = j * kWT + tid;
+      hd[j] = rl < d.nr ? find_head<KeyT>(rk[j], keys, slots, logt) : 0u;
+      c[j] = 0;
+      if (hd[j]) {
+        uint32_t n = 1, li = nxt[hd[j] - 1];
+        while (li) {
+          n++;
+          li = nxt[li - 1];
+        }
+        c[j] = n;
+      }
+      if (c[j] == 1) n1++;
+      else nm += c[j];
+    }
+    uint64_t tot64;
+    const uint64_t ex64 = block_exclusive_scan<uint64_t>(((uint64_t)n1 << 32) | nm, scratch64, &tot64);
+    const uint32_t S = (uint32_t)(tot64 >> 32);
+    const uint64_t item_total = S + (tot64 & 0xFFFFFFFFull);
     if (tid == 0) {
       uint64_t base;
       if (HAVE_OFFSETS) {
         base = item_off[it];
       } else {
-        base = look_back(state, it, tot, flags, withhold_first);
+        if (ordered) {
+          base = look_back(state, it, item_total, flags, withhold_first);
+          if (base != ~0ull && item_total) atomicAdd(total, (unsigned long long)item_total);
+        } else {
+          base = item_total ? atomicAdd(total, (unsigned long long)item_total) : 0ull;
+        }
         if (base != ~0ull) {
           item_off[it] = base;
-          if (tot) atomicAdd(total, (unsigned long long)tot);
-          if (base + tot > capacity) atomicExch(&flags[FLAG_OVERFLOW], 1);
+          if (base + item_total > capacity) atomicExch(&flags[FLAG_OVERFLOW], 1);
         }
       }
       s_base = base;
     }
+    {
+      uint32_t e = (uint32_t)(ex64 >> 32);
+#pragma unroll
+      for (int j = 0; j < kWPF; j++)
+        if (c[j] == 1) list[e++] = ((j * kWT + tid) << 16) | (hd[j] - 1);
+    }
     __syncthreads();
     const uint64_t base = s_base;
-    if (base != ~0ull && base + tot <= capacity && mine) {
-      uint64_t pos = base + ex;
+    if (base != ~0ull && base + item_total <= capacity) {
+      // single-match rows: consecutive threads write consecutive rows
+      for (uint32_t e = tid; e < S; e += kWT) {
+        const uint32_t w = list[e];
+        const uint32_t li = w & 0xFFFFu;
+        const uint64_t pos = base + e;
+        okey[pos] = keys[li];
+        copy_cols_row(L, R, out, pos, d.lbeg + li, d.rbeg + (w >> 16));
+      }
+      // rows with several matches: each thread expands its own
+      if (nm) {
+        uint64_t pos = base + S + (ex64 & 0xFFFFFFFFull);
 #pragma unroll
-      for (int j = 0; j < kPF; j++) {
-        if (!c[j]) continue;
-        const uint32_t r = d.rbeg + j * nthr + tid;
-        const uint32_t rr = R.rid ? R.rid[r] : r;
-        uint32_t li = hd[j] - 1;
-        for (uint32_t q = 0; q < c[j]; q++, pos++) {
-          const uint32_t lrow = d.lbeg + li;
-          okey[pos] = rk[j];
-          out.lrow[pos] = L.rid ? L.rid[lrow] : lrow;
-          out.rrow[pos] = rr;
-          for (int cc = 0; cc < L.ncols; cc++) {
-            if (L.width[cc] == 8)
-              ((uint64_t *)out.lcols[cc])[pos] = ((const uint64_t *)L.cols[cc])[lrow];
-            else
-              ((uint32_t *)out.lcols[cc])[pos] = ((const uint32_t *)L.cols[cc])[lrow];
+        for (int j = 0; j < kWPF; j++) {
+          if (c[j] < 2) continue;
+          const uint32_t r = d.rbeg + j * kWT + tid;
+          uint32_t li = hd[j];
+          while (li) {
+            okey[pos] = keys[li - 1];
+            copy_cols_row(L, R, out, pos, d.lbeg + li - 1, r);
+            pos++;
+            li = nxt[li - 1];
           }
-          for (int cc = 0; cc < R.ncols; cc++) {
-            if (R.width[cc] == 8)
-              ((uint64_t *)out.rcols[cc])[pos] = ((const uint64_t *)R.cols[cc])[r];
-            else
-              ((uint32_t *)out.rcols[cc])[pos] = ((const uint32_t *)R.cols[cc])[r];
-          }
-          li = (uint32_t)nxt[li] - 1;
         }
       }
+    }
+    if (tid == 0) {
+      s_it = nx;
+      if (nx < nitems) s_item = dn;
     }
     __syncthreads();
   }
@@ -468,10 +611,10 @@ JSide to_jside(const Side &s) {
 }
 
 template <typename KernelT>
-int resident_grid(KernelT kernel, size_t smem, uint64_t nitems, int *grid) {
+int resident_grid(KernelT kernel, size_t smem, uint64_t nitems, int *grid, int threads = kJoinThreads) {
   int per_sm = 0;
   MDJ_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  MDJ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kJoinThreads, smem));
+  MDJ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem));
   if (per_sm < 1) return MDJ_ERR_INTERNAL;
   uint64_t g = (uint64_t)num_sms() * per_sm;
   if (g > nitems) g = nitems;
@@ -570,6 +713,16 @@ int test_withhold_first() {
   return e && e[0] == '1';
 }
 
+
+// MDJ_ORDERED_OUTPUT=1: item output ranges follow item order (decoupled
+// look-back), so the same inputs give byte-identical outputs.  Default: each
+// item reserves its range with one atomicAdd (same rows, item order not
+// reproducible), which never waits on other items.
+int ordered_output() {
+  const char *e = getenv("MDJ_ORDERED_OUTPUT");
+  return e && e[0] == '1';
+}
+
 // Rows of the optimistic output buffer of the fused pass: max(n_L, n_R), the
 // exact bound when build keys are unique (MDJ_OUTPUT_ROWS overrides).
 uint64_t output_capacity_hint(uint64_t nl, uint64_t nr) {
@@ -602,14 +755,14 @@ int run_join(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, md
   mdj_result r;
   JOut o;
   MDJ_TRY(alloc_result(ws, Ls, Rs, sizeof(KeyT), cap_rows, &r, &o));
-  const size_t sm = join_smem_bytes<KeyT>(plan.cap, false);
+  const size_t sm = WriteLayout<KeyT>(plan.cap).total;  // ~88 KB at cap 4096: two blocks per SM
   if (nitems) {
     int grid;
-    MDJ_TRY(resident_grid(k_join_write<KeyT, false>, sm, nitems, &grid));
+    MDJ_TRY(resident_grid(k_join_write<KeyT, false>, sm, nitems, &grid, kWT));
     TraceScope tr("join_write", s);
-    k_join_write<KeyT, false><<<grid, kJoinThreads, sm, s>>>(to_jside(Ls), to_jside(Rs), desc, nitems, ticket,
-                                                             state, item_off, total, cap_rows, flags,
-                                                             test_withhold_first(), o);
+    k_join_write<KeyT, false><<<grid, kWT, sm, s>>>(to_jside(Ls), to_jside(Rs), desc, nitems, plan.cap, ticket,
+                                                    state, item_off, total, cap_rows, flags, test_withhold_first(),
+                                                    ordered_output(), o);
   }
   cudaError_t e = cudaGetLastError();
   unsigned long long host_total = 0;
@@ -633,12 +786,12 @@ int run_join(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, md
     MDJ_TRY(alloc_result(ws, Ls, Rs, sizeof(KeyT), m, &r, &o));
     if (m > 0) {
       int grid;
-      MDJ_TRY(resident_grid(k_join_write<KeyT, true>, sm, nitems, &grid));
+      MDJ_TRY(resident_grid(k_join_write<KeyT, true>, sm, nitems, &grid, kWT));
       MDJ_CUDA_TRY(cudaMemsetAsync(ticket, 0, 4, s));
       {
         TraceScope tr("join_write_exact", s);
-        k_join_write<KeyT, true><<<grid, kJoinThreads, sm, s>>>(to_jside(Ls), to_jside(Rs), desc, nitems, ticket,
-                                                                state, item_off, total, m, flags, 0, o);
+        k_join_write<KeyT, true><<<grid, kWT, sm, s>>>(to_jside(Ls), to_jside(Rs), desc, nitems, plan.cap, ticket,
+                                                       state, item_off, total, m, flags, 0, 0, o);
       }
       e = cudaGetLastError();
       if (e != cudaSuccess) {

@@ -125,7 +125,9 @@ def test_config0_plain_merge_P1():
     assert got["key"].size == 300_000
 
 
-def test_deterministic_for_unique_left():
+def test_deterministic_for_unique_left(monkeypatch):
+    # ordered output mode: item ranges follow item order (decoupled look-back)
+    monkeypatch.setenv("MDJ_ORDERED_OUTPUT", "1")
     (lk, lp), (rk, rp) = datagen.match_fraction_tables(100_000, 100_000, 0.5, seed=9)
     mdj = _mdj()
     a = mdj.mdj_merge(_dev([lk, lp]), _dev([rk, rp]), 8)
@@ -187,9 +189,17 @@ def test_bounded_wait_reports_timeout_and_context_survives(monkeypatch):
     # after its bound, the call must say so, and the next call must work
     (lk, lp), (rk, rp) = datagen.match_fraction_tables(100_000, 100_000, 0.3, seed=22)
     mdj = _mdj()
+    monkeypatch.setenv("MDJ_ORDERED_OUTPUT", "1")
     monkeypatch.setenv("MDJ_TEST_WITHHOLD_FIRST_ITEM", "1")
     with pytest.raises(mdj.MdjError) as e:
         mdj.mdj_merge(_dev([lk, lp]), _dev([rk, rp]), 8)
     assert e.value.status == -6
     monkeypatch.delenv("MDJ_TEST_WITHHOLD_FIRST_ITEM")
+    _check([lk, lp], [rk, rp], 8)
+
+
+@pytest.mark.parametrize("ordered", ["0", "1"])
+def test_both_output_modes_match_oracle(monkeypatch, ordered):
+    monkeypatch.setenv("MDJ_ORDERED_OUTPUT", ordered)
+    (lk, lp), (rk, rp) = datagen.zipf_tables(60_000, 90_000, 20_000, 1.1, seed=23)
     _check([lk, lp], [rk, rp], 8)
