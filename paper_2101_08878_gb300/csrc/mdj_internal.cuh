@@ -178,6 +178,10 @@ class Workspace {
   void release_all();
   cudaStream_t stream() const { return stream_; }
   const mdj_allocator *allocator() const { return alloc_; }
+  // A zeroed device int owned by this workspace (kernels set it to report a
+  // bounded wait that ran out); NULL if it cannot be allocated.
+  int *flag_word();
+  int *flag_word_if_any() const { return flag_; }
 
  private:
   void *raw_alloc(size_t bytes);
@@ -185,6 +189,7 @@ class Workspace {
   const mdj_allocator *alloc_;
   cudaStream_t stream_;
   std::vector<void *> owned_;
+  int *flag_ = nullptr;
 };
 
 // Launch tracing (mdj_profile_*): events around each launch when enabled.

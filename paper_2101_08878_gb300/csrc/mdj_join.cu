@@ -635,8 +635,11 @@ int make_items(Workspace &ws, const Side &Ls, const Side &Rs, uint32_t nb, uint3
   MDJ_LAUNCH_CHECK();
   MDJ_TRY(exclusive_scan_u64(ws, item_off, item_off, nb + 1));
   uint64_t nitems = 0;
+  int part_flag = 0;
   MDJ_CUDA_TRY(cudaMemcpyAsync(&nitems, item_off + nb, 8, cudaMemcpyDeviceToHost, s));
+  if (ws.flag_word_if_any()) MDJ_CUDA_TRY(cudaMemcpyAsync(&part_flag, ws.flag_word_if_any(), 4, cudaMemcpyDeviceToHost, s));
   MDJ_CUDA_TRY(cudaStreamSynchronize(s));
+  if (part_flag) return MDJ_ERR_DEVICE_TIMEOUT;  // a partition pass gave up on a copy wait
   if (nitems >= (1ull << 31)) return MDJ_ERR_TOO_LARGE;
   *nitems_out = (uint32_t)nitems;
   *desc = (Item *)ws.get((size_t)(nitems ? nitems : 1) * sizeof(Item));

@@ -104,7 +104,7 @@ def test_heavy_key_exceeding_one_table():
 
 
 def test_P_invariance():
-    (lk, lp), (rk, rp) = datagen.zipf_tables(30_000, 50_000, 5_000, 1.1, seed=6)
+    (lk, lp), (rk, rp) = datagen.zipf_tables(12_000, 20_000, 20_000, 1.1, seed=6)
     base = _run([lk, lp], [rk, rp], None)
     for P in (1, 3, 8, 64, 1025):
         got = _run([lk, lp], [rk, rp], P)
@@ -201,5 +201,12 @@ def test_bounded_wait_reports_timeout_and_context_survives(monkeypatch):
 @pytest.mark.parametrize("ordered", ["0", "1"])
 def test_both_output_modes_match_oracle(monkeypatch, ordered):
     monkeypatch.setenv("MDJ_ORDERED_OUTPUT", ordered)
-    (lk, lp), (rk, rp) = datagen.zipf_tables(60_000, 90_000, 20_000, 1.1, seed=23)
+    (lk, lp), (rk, rp) = datagen.zipf_tables(20_000, 30_000, 50_000, 1.1, seed=23)
     _check([lk, lp], [rk, rp], 8)
+
+
+def test_merge_with_pipelined_scatter(monkeypatch):
+    monkeypatch.setenv("MDJ_PIPE_SCATTER", "1")
+    (lk, lp), (rk, rp) = datagen.match_fraction_tables(4_000_000, 1_000_000, 0.3, seed=31)
+    got = _check([lk, lp], [rk, rp], 8)
+    assert got["key"].size == 300_000
