@@ -50,6 +50,9 @@ def _load():
         lib.oracle_count_checksum.restype = i32
         lib.oracle_count_checksum.argtypes = [vp, vp, i32, u64, vp, vp, i32, u64, i32,
                                               ctypes.POINTER(u64), ctypes.POINTER(u64)]
+        lib.oracle_count_checksum_dense.restype = i32
+        lib.oracle_count_checksum_dense.argtypes = [vp, vp, i32, u64, vp, vp, i32, u64, i32, u64,
+                                                    ctypes.POINTER(u64), ctypes.POINTER(u64)]
         lib.oracle_fmix64_array.restype = None
         lib.oracle_fmix64_array.argtypes = [vp, u64, vp]
         lib.oracle_partition_ids.restype = None
@@ -202,4 +205,20 @@ def count_checksum(lkeys, lpay, rkeys, rpay):
                                        lkeys.dtype.itemsize, ctypes.byref(cnt), ctypes.byref(chk))
     if rc != 0:
         raise ValueError("oracle_count_checksum failed")
+    return cnt.value, chk.value
+
+
+def count_checksum_dense(lkeys, lpay, rkeys, rpay, key_range: int):
+    """count_checksum for keys in [0, key_range), by per-key arrays (no sort)."""
+    lkeys, rkeys = _key_array(lkeys), _key_array(rkeys)
+    if lkeys.dtype != rkeys.dtype:
+        raise TypeError("left and right key columns must have the same dtype")
+    lb, rb = _bits(lpay), _bits(rpay)
+    cnt, chk = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    rc = _load().oracle_count_checksum_dense(_ptr(lkeys), _ptr(lb), lb.dtype.itemsize, lkeys.size,
+                                             _ptr(rkeys), _ptr(rb), rb.dtype.itemsize, rkeys.size,
+                                             lkeys.dtype.itemsize, key_range, ctypes.byref(cnt),
+                                             ctypes.byref(chk))
+    if rc != 0:
+        raise ValueError("oracle_count_checksum_dense failed (key outside [0, key_range)?)")
     return cnt.value, chk.value

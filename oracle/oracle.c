@@ -285,3 +285,60 @@ void oracle_checksum_terms(const void *lkeys, int key_bytes, const void *lpay, i
     for (uint64_t i = 0; i < nr; i++)
         g[i] = oracle_checksum_g((uint32_t)i, pay_bits(rpay, rpay_bytes, i));
 }
+
+/*
+ * count + checksum for keys known to lie in [0, K): per-key sums in arrays
+ * (lc, rc, F = sum of f, G = sum of g), then count = sum_k lc*rc and
+ * checksum = sum_k F*G (mod 2^64).  Same definitions as
+ * oracle_count_checksum, computed without sorting, for large skewed inputs.
+ * Returns 0, or -1 on a key outside [0, K) or allocation failure.
+ */
+int oracle_count_checksum_dense(const void *lkeys, const void *lpay, int lpay_bytes, uint64_t nl,
+                                const void *rkeys, const void *rpay, int rpay_bytes, uint64_t nr,
+                                int key_bytes, uint64_t K, uint64_t *count, uint64_t *checksum)
+{
+    if ((key_bytes != 4 && key_bytes != 8) || K == 0)
+        return -1;
+    uint64_t *lc = (uint64_t *)calloc(K, sizeof(uint64_t));
+    uint64_t *rc = (uint64_t *)calloc(K, sizeof(uint64_t));
+    uint64_t *F = (uint64_t *)calloc(K, sizeof(uint64_t));
+    uint64_t *G = (uint64_t *)calloc(K, sizeof(uint64_t));
+    int rcode = 0;
+    if (!lc || !rc || !F || !G) {
+        rcode = -1;
+        goto done;
+    }
+    for (uint64_t i = 0; i < nl; i++) {
+        int64_t k = key_at(lkeys, key_bytes, i);
+        if (k < 0 || (uint64_t)k >= K) {
+            rcode = -1;
+            goto done;
+        }
+        lc[k] += 1;
+        F[k] += oracle_checksum_f(k, (uint32_t)i, pay_bits(lpay, lpay_bytes, i));
+    }
+    for (uint64_t i = 0; i < nr; i++) {
+        int64_t k = key_at(rkeys, key_bytes, i);
+        if (k < 0 || (uint64_t)k >= K) {
+            rcode = -1;
+            goto done;
+        }
+        rc[k] += 1;
+        G[k] += oracle_checksum_g((uint32_t)i, pay_bits(rpay, rpay_bytes, i));
+    }
+    {
+        uint64_t cnt = 0, sum = 0;
+        for (uint64_t k = 0; k < K; k++) {
+            cnt += lc[k] * rc[k];
+            sum += F[k] * G[k];
+        }
+        *count = cnt;
+        *checksum = sum;
+    }
+done:
+    free(lc);
+    free(rc);
+    free(F);
+    free(G);
+    return rcode;
+}

@@ -226,3 +226,30 @@ def test_data_volume_matches_paper():
     assert 5e7 * per_row * 2 == 1.6e9
     assert 32 * 5e7 * per_row * 2 == 51.2e9
     assert [k * 3.2 for k in range(1, 7)] == pytest.approx([3.2, 6.4, 9.6, 12.8, 16.0, 19.2])
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_dense_count_checksum_equals_sort_merge(seed):
+    # the per-key-array form used for the full-size skewed config agrees with
+    # the sort-merge form on the same Zipf tables
+    (lk, lp), (rk, rp) = datagen.zipf_tables(30_000, 60_000, 2_000, 1.1, seed=seed)
+    assert oracle.count_checksum_dense(lk, lp, rk, rp, 2_000) == oracle.count_checksum(lk, lp, rk, rp)
+
+
+def test_dense_count_checksum_rejects_out_of_range_keys():
+    with pytest.raises(ValueError):
+        oracle.count_checksum_dense(np.array([5], np.int64), np.zeros(1), np.array([1], np.int64),
+                                    np.zeros(1), 3)
+
+
+def test_zipf_skew_matches_closed_form():
+    # the Zipf(1.1) generator over 1e7 values: P(key = 0) = 1 / H(1e7, 1.1);
+    # expected pair count of the skewed config, n_L n_R sum_k p_k^2, ~2.0e14
+    k = np.arange(1, 10_000_001, dtype=np.float64)
+    w = k ** -1.1
+    p = w / w.sum()
+    assert abs(1 / w.sum() - 0.1164) < 5e-4
+    assert 1.9e14 < 5e7 * 2e8 * float(np.sum(p * p)) < 2.1e14
+    rng = np.random.default_rng(5)
+    keys = datagen.zipf_keys(rng, 2_000_000, 10_000_000, 1.1)
+    assert abs(np.mean(keys == 0) - p[0]) < 5 * np.sqrt(p[0] * (1 - p[0]) / 2_000_000)
