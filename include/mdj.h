@@ -205,11 +205,41 @@ MDJ_API int mdj_count_checksum(const mdj_table *left, int32_t left_key, const md
                        int32_t right_key, uint32_t P, const mdj_allocator *alloc, void *stream,
                        uint64_t *count, uint64_t *checksum);
 
+/* Tuning of the join tables (0 in a field = default). */
+typedef struct {
+    uint32_t table_rows;  /* build rows per shared-memory hash table, 256..8192 (default 4096) */
+    uint32_t fill_pct;    /* target mean build rows per bucket, percent of table_rows, 10..100 (default 85) */
+    uint32_t reserved[6];
+} mdj_tuning;
+
+/*
+ * mdj_join_batch - many independent partition-pair merges (the per-partition
+ * merge of Sec. V-B for every worker's pair at once) in a fixed number of
+ * launches, however many pairs there are.  Pair i joins rows
+ * [left_offsets[i], left_offsets[i+1]) of `left` with rows
+ * [right_offsets[i], right_offsets[i+1]) of `right` (host arrays of npairs+1
+ * nondecreasing offsets, first 0, last nrows).  Each pair is split into its
+ * own hash buckets, all pairs' buckets are joined by one persistent kernel,
+ * and the output holds pair 0's rows, then pair 1's, ...: pair i's rows are
+ * [pair_offsets[i], pair_offsets[i+1]) (host array of npairs+1, filled by the
+ * call).  left_row / right_row index the whole `left` / `right` tables.
+ * Within a pair the rows are those of mdj_join on the pair's two slices.
+ * `tuning` may be NULL.  Synchronises `stream` before returning.
+ */
+MDJ_API int mdj_join_batch(const mdj_table *left, int32_t left_key, const uint64_t *left_offsets,
+                           const mdj_table *right, int32_t right_key, const uint64_t *right_offsets,
+                           int32_t npairs, const mdj_tuning *tuning, const mdj_allocator *alloc,
+                           void *stream, mdj_result *out, uint64_t *pair_offsets);
+
 /* Releases every array of *res with `alloc` (stream order) and zeroes *res. */
 MDJ_API void mdj_result_release(mdj_result *res, const mdj_allocator *alloc, void *stream);
 
 /* Static, human-readable text for a status code. */
 MDJ_API const char *mdj_status_string(int status);
+
+/* Text of the CUDA error behind the calling thread's last MDJ_ERR_CUDA ("" if
+ * none); valid until that thread's next call. */
+MDJ_API const char *mdj_last_error(void);
 
 /* MDJ_VERSION of the loaded library. */
 MDJ_API int mdj_version(void);

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "mdj.h"
@@ -81,6 +82,11 @@ __device__ __forceinline__ uint32_t bucket_of(uint64_t h, const BucketSpec &bs) 
   if (bs.digit_mode) return (p / bs.dmul) % bs.dmod;
   return p * bs.S1 + __umulhi((uint32_t)(h >> 32), bs.S1);
 }
+
+// A tile of a segmented (batched) partition: rows [row0, row0 + rows) of one segment.
+struct SegTile {
+  uint32_t row0, rows, seg;
+};
 
 BucketSpec make_spec(uint32_t P, uint32_t S, uint32_t div);
 BucketSpec make_digit_spec(uint32_t P, uint32_t dmul, uint32_t dmod);
@@ -241,6 +247,13 @@ Plan make_plan(uint64_t n_build, uint32_t P, uint32_t cap, bool force_partition)
 // freshly allocated workspace buffers; fills `out` (offsets per final bucket).
 int partition_side(Workspace &ws, const mdj_table *t, int32_t key_col, const Plan &plan,
                    Side *out);
+
+// Segmented partition of a batch: segment i = rows [seg_off[i], seg_off[i+1])
+// (host array) is split into seg_nb[i] buckets numbered from seg_base[i] by
+// floor(hi32(fmix64(key)) * seg_nb[i] / 2^32).  nbuckets = sum of seg_nb.
+int partition_side_segmented(Workspace &ws, const mdj_table *t, int32_t key_col, const uint64_t *seg_off,
+                             uint32_t nseg, const uint32_t *seg_base, const uint32_t *seg_nb, uint32_t nbuckets,
+                             Side *out);
 
 // Stable partition into caller buffers (the mdj_partition body).
 int stable_partition(Workspace &ws, const mdj_table *t, int32_t key_col, uint32_t P,

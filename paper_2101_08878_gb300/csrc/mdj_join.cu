@@ -36,7 +36,8 @@ constexpr int kPF = 8;                                   // probe rows per threa
 constexpr uint32_t kWriteChunk = kPF * kJoinThreads;     // probe rows per write item (one round)
 constexpr uint32_t kCountChunk = 65536;                  // probe rows per count item
 constexpr uint32_t kDefaultCap = 4096;
-constexpr uint32_t kMaxCap = 16384;
+constexpr uint32_t kMaxCap = 8192;      // write-pass table: 8-byte keys fit 227 KB of shared memory
+constexpr uint32_t kCountCapMax = 4096;  // count/checksum table (per-slot counts and sums)
 constexpr uint64_t kWaitLimitNs = 1000000000ull;         // look-back wait bound: 1 s of device time
 constexpr uint32_t kPollLimit = 1u << 26;                // and a poll-count bound as a backstop
 constexpr uint64_t kFlagAgg = 1ull << 62, kFlagInc = 2ull << 62, kValMask = (1ull << 62) - 1;
@@ -624,7 +625,7 @@ int resident_grid(KernelT kernel, size_t smem, uint64_t nitems, int *grid, int t
 
 // Work items of the whole join, with `rch` probe rows per item at most.
 int make_items(Workspace &ws, const Side &Ls, const Side &Rs, uint32_t nb, uint32_t cap, uint32_t rch, Item **desc,
-               uint32_t *nitems_out) {
+               uint32_t *nitems_out, uint64_t **bucket_items = nullptr) {
   cudaStream_t s = ws.stream();
   uint64_t *item_off = (uint64_t *)ws.get((size_t)(nb + 1) * 8);
   if (!item_off) return MDJ_ERR_OOM;
@@ -651,7 +652,10 @@ int make_items(Workspace &ws, const Side &Ls, const Side &Rs, uint32_t nb, uint3
     k_expand<<<g, 256, 0, s>>>(Ls.off, Rs.off, nb, cap, rch, item_off, (uint32_t)nitems, *desc);
   }
   MDJ_LAUNCH_CHECK();
-  ws.give_back(item_off);
+  if (bucket_items)
+    *bucket_items = item_off;
+  else
+    ws.give_back(item_off);
   return MDJ_OK;
 }
 
@@ -660,13 +664,14 @@ int run_count(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, u
   cudaStream_t s = ws.stream();
   Item *desc;
   uint32_t nitems;
-  MDJ_TRY(make_items(ws, Ls, Rs, plan.nbuckets, plan.cap, kCountChunk, &desc, &nitems));
+  const uint32_t cap = plan.cap < kCountCapMax ? plan.cap : kCountCapMax;
+  MDJ_TRY(make_items(ws, Ls, Rs, plan.nbuckets, cap, kCountChunk, &desc, &nitems));
   unsigned long long *tot = (unsigned long long *)ws.get(32);
   if (!tot) return MDJ_ERR_OOM;
   MDJ_CUDA_TRY(cudaMemsetAsync(tot, 0, 32, s));
   uint32_t *ticket = (uint32_t *)(tot + 2);
   if (nitems) {
-    const size_t sm = join_smem_bytes<KeyT>(plan.cap, true);
+    const size_t sm = join_smem_bytes<KeyT>(cap, true);
     int grid;
     MDJ_TRY(resident_grid(k_join_count<KeyT, true>, sm, nitems, &grid));
     TraceScope tr("join_checksum", s);
@@ -738,12 +743,22 @@ uint64_t output_capacity_hint(uint64_t nl, uint64_t nr) {
   return c;
 }
 
+// Batch bookkeeping returned by run_join: per-bucket item prefix, per-item
+// output offsets (valid in ordered mode) and the item count.
+struct ItemMap {
+  uint64_t *bucket_items = nullptr;
+  uint64_t *item_out = nullptr;
+  uint32_t nitems = 0;
+};
+
 template <typename KeyT>
-int run_join(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, mdj_result *res) {
+int run_join(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, mdj_result *res,
+             bool force_ordered = false, ItemMap *map = nullptr) {
   cudaStream_t s = ws.stream();
   Item *desc;
   uint32_t nitems;
-  MDJ_TRY(make_items(ws, Ls, Rs, plan.nbuckets, plan.cap, kWriteChunk, &desc, &nitems));
+  MDJ_TRY(make_items(ws, Ls, Rs, plan.nbuckets, plan.cap, kWriteChunk, &desc, &nitems,
+                     map ? &map->bucket_items : nullptr));
   // state[nitems] | item_off[nitems] | total | ticket | flags
   const size_t words = 2 * (size_t)nitems + 4;
   unsigned long long *state = (unsigned long long *)ws.get(words * 8);
@@ -765,7 +780,7 @@ int run_join(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, md
     TraceScope tr("join_write", s);
     k_join_write<KeyT, false><<<grid, kWT, sm, s>>>(to_jside(Ls), to_jside(Rs), desc, nitems, plan.cap, ticket,
                                                     state, item_off, total, cap_rows, flags, test_withhold_first(),
-                                                    ordered_output(), o);
+                                                    force_ordered ? 1 : ordered_output(), o);
   }
   cudaError_t e = cudaGetLastError();
   unsigned long long host_total = 0;
@@ -805,7 +820,23 @@ int run_join(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, md
   }
   r.nrows = m;
   *res = r;
+  if (map) {
+    map->item_out = item_off;
+    map->nitems = nitems;
+  }
   return MDJ_OK;
+}
+
+// pair_off[i] = output offset of pair i's first item (or of the next pair's,
+// for a pair without items); pair_off[npairs] = total rows.
+__global__ void k_pair_offsets(const uint32_t *__restrict__ seg_base, uint32_t npairs, uint32_t nb,
+                               const uint64_t *__restrict__ bucket_items, const uint64_t *__restrict__ item_out,
+                               uint32_t nitems, uint64_t total, uint64_t *__restrict__ pair_off) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > npairs) return;
+  const uint32_t b = i < npairs ? seg_base[i] : nb;
+  const uint64_t idx = bucket_items[b];
+  pair_off[i] = (i < npairs && idx < nitems) ? item_out[idx] : total;
 }
 
 // ------------------------------------------------------------- validation
@@ -889,6 +920,80 @@ int mdj_merge(const mdj_table *left, int32_t left_key, const mdj_table *right, i
 int mdj_count_checksum(const mdj_table *left, int32_t left_key, const mdj_table *right, int32_t right_key,
                        uint32_t P, const mdj_allocator *alloc, void *stream, uint64_t *count, uint64_t *checksum) {
   return merge_impl(left, left_key, right, right_key, P, alloc, stream, nullptr, true, count, checksum);
+}
+
+int mdj_join_batch(const mdj_table *left, int32_t left_key, const uint64_t *left_offsets, const mdj_table *right,
+                   int32_t right_key, const uint64_t *right_offsets, int32_t npairs, const mdj_tuning *tuning,
+                   const mdj_allocator *alloc, void *stream, mdj_result *out, uint64_t *pair_offsets) {
+  MDJ_TRY(check_table(left, left_key));
+  MDJ_TRY(check_table(right, right_key));
+  if (left->cols[left_key].dtype != right->cols[right_key].dtype) return MDJ_ERR_INVALID_ARG;
+  if (npairs < 1 || !left_offsets || !right_offsets || !out || !pair_offsets) return MDJ_ERR_INVALID_ARG;
+  if (left_offsets[0] != 0 || right_offsets[0] != 0 || left_offsets[npairs] != left->nrows ||
+      right_offsets[npairs] != right->nrows)
+    return MDJ_ERR_INVALID_ARG;
+  for (int32_t i = 0; i < npairs; i++)
+    if (left_offsets[i + 1] < left_offsets[i] || right_offsets[i + 1] < right_offsets[i]) return MDJ_ERR_INVALID_ARG;
+  memset(out, 0, sizeof *out);
+  uint32_t cap = cap_from_env();
+  uint32_t fill = 85;
+  if (tuning) {
+    if (tuning->table_rows) {
+      if (tuning->table_rows < 256 || tuning->table_rows > kMaxCap) return MDJ_ERR_INVALID_ARG;
+      cap = tuning->table_rows;
+    }
+    if (tuning->fill_pct) {
+      if (tuning->fill_pct < 10 || tuning->fill_pct > 100) return MDJ_ERR_INVALID_ARG;
+      fill = tuning->fill_pct;
+    }
+  }
+  const uint64_t target = std::max<uint64_t>(1, (uint64_t)cap * fill / 100);
+  std::vector<uint32_t> seg_nb(npairs), seg_base(npairs);
+  uint64_t nb = 0;
+  for (int32_t i = 0; i < npairs; i++) {
+    const uint64_t nl = left_offsets[i + 1] - left_offsets[i], nr = right_offsets[i + 1] - right_offsets[i];
+    uint64_t S = (nl && nr) ? (nl + target - 1) / target : 1;
+    S = std::min<uint64_t>(std::max<uint64_t>(S, 1), kPass2SpanMax);
+    seg_nb[i] = (uint32_t)S;
+    seg_base[i] = (uint32_t)nb;
+    nb += S;
+  }
+  if (nb >= (1ull << 31)) return MDJ_ERR_TOO_LARGE;
+  Workspace ws(alloc, (cudaStream_t)stream);
+  cudaStream_t s = (cudaStream_t)stream;
+  Side L, R;
+  MDJ_TRY(partition_side_segmented(ws, left, left_key, left_offsets, npairs, seg_base.data(), seg_nb.data(),
+                                   (uint32_t)nb, &L));
+  MDJ_TRY(partition_side_segmented(ws, right, right_key, right_offsets, npairs, seg_base.data(), seg_nb.data(),
+                                   (uint32_t)nb, &R));
+  Plan plan;
+  plan.P = 1;
+  plan.nbuckets = (uint32_t)nb;
+  plan.cap = cap;
+  ItemMap map;
+  const bool k64 = left->cols[left_key].dtype == MDJ_I64;
+  MDJ_TRY(k64 ? run_join<int64_t>(ws, L, R, plan, out, true, &map) : run_join<int32_t>(ws, L, R, plan, out, true, &map));
+  // pair boundaries in the (pair-major) output
+  uint32_t *dbase = (uint32_t *)ws.get((size_t)npairs * 4);
+  uint64_t *doff = (uint64_t *)ws.get((size_t)(npairs + 1) * 8);
+  int rc = MDJ_OK;
+  if (!dbase || !doff) rc = MDJ_ERR_OOM;
+  if (rc == MDJ_OK)
+    rc = cuda_status(cudaMemcpyAsync(dbase, seg_base.data(), (size_t)npairs * 4, cudaMemcpyHostToDevice, s));
+  if (rc == MDJ_OK) {
+    {
+      TraceScope tr("pair_offsets", s);
+      k_pair_offsets<<<(npairs + 1 + 255) / 256, 256, 0, s>>>(dbase, (uint32_t)npairs, (uint32_t)nb,
+                                                              map.bucket_items, map.item_out, map.nitems, out->nrows,
+                                                              doff);
+    }
+    rc = cuda_status(cudaGetLastError());
+  }
+  if (rc == MDJ_OK) rc = cuda_status(cudaMemcpyAsync(pair_offsets, doff, (size_t)(npairs + 1) * 8,
+                                                     cudaMemcpyDeviceToHost, s));
+  if (rc == MDJ_OK) rc = cuda_status(cudaStreamSynchronize(s));
+  if (rc != MDJ_OK) mdj_result_release(out, alloc, stream);
+  return rc;
 }
 
 }  // extern "C"

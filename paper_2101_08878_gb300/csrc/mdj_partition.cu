@@ -129,11 +129,15 @@ __device__ void scatter_direct(const KeyT (&kv)[kRPL], uint32_t wrow0, uint32_t 
   }
 }
 
-template <typename KeyT, bool RESERVE>
+// SEG (with RESERVE): tiles come from `seg_tiles` and never cross a segment;
+// a row's local bucket is floor(hi32(h) * S_seg / 2^32) among the segment's
+// S_seg buckets starting at seg_base[seg] (a batch of independent joins).
+template <typename KeyT, bool RESERVE, bool SEG>
 __global__ void __launch_bounds__(kNW * 32, 2)
     k_scatter(const KeyT *__restrict__ keys, uint32_t n, BucketSpec bs, uint32_t F, uint32_t ntiles,
               const uint32_t *__restrict__ tile_base, uint32_t *__restrict__ cursors, uint32_t F2, ColMove cm,
-              const uint32_t *__restrict__ rid_in, uint32_t *__restrict__ rid_out) {
+              const uint32_t *__restrict__ rid_in, uint32_t *__restrict__ rid_out, const SegTile *__restrict__ seg_tiles,
+              const uint32_t *__restrict__ seg_base, const uint32_t *__restrict__ seg_nb) {
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t FL = RESERVE ? kPass2SpanMax : F;
   uint64_t *stage64 = (uint64_t *)smem;
@@ -145,8 +149,10 @@ __global__ void __launch_bounds__(kNW * 32, 2)
   uint32_t *scratch = gbase + FL;
 
   const uint32_t t = blockIdx.x;
-  const uint32_t row0 = t * kTile;
-  const uint32_t rows = min(kTile, n - row0);
+  SegTile td = {0, 0, 0};
+  if (SEG) td = seg_tiles[t];
+  const uint32_t row0 = SEG ? td.row0 : t * kTile;
+  const uint32_t rows = SEG ? td.rows : min(kTile, n - row0);
   const uint32_t rend = row0 + rows;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t wrow0 = row0 + warp * 32 * kRPL;
@@ -158,8 +164,12 @@ __global__ void __launch_bounds__(kNW * 32, 2)
     kv[c] = r < rend ? keys[r] : KeyT(0);
   }
 
-  uint32_t Floc = F, lb0 = 0;
-  if (RESERVE) {
+  uint32_t Floc = F, lb0 = 0, Sseg = 0;
+  if (SEG) {
+    lb0 = seg_base[td.seg];
+    Sseg = seg_nb[td.seg];
+    Floc = Sseg;
+  } else if (RESERVE) {
     uint32_t b1f = sub_bucket_of(fmix64(key_bits(keys[row0])), bs) / F2;
     uint32_t b1l = sub_bucket_of(fmix64(key_bits(keys[rend - 1])), bs) / F2;
     lb0 = b1f * F2;
@@ -180,7 +190,11 @@ __global__ void __launch_bounds__(kNW * 32, 2)
   for (int c = 0; c < kRPL; c++) {
     uint32_t r = wrow0 + c * 32 + lane;
     bool valid = r < rend;
-    uint32_t b = valid ? bucket_of(fmix64(key_bits(kv[c])), bs) - lb0 : 0xFFFFFFFFu;
+    uint32_t b = 0xFFFFFFFFu;
+    if (valid) {
+      const uint64_t h = fmix64(key_bits(kv[c]));
+      b = SEG ? __umulhi((uint32_t)(h >> 32), Sseg) : bucket_of(h, bs) - lb0;
+    }
     uint32_t peers = __match_any_sync(0xffffffffu, b);
     uint32_t rank = __popc(peers & lanemask_lt());
     uint32_t old = valid ? wh[b] : 0u;
@@ -590,9 +604,11 @@ template <typename KeyT>
 int set_smem_attrs() {
   static bool done = false;
   if (done) return MDJ_OK;
-  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_scatter<KeyT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_scatter<KeyT, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)scatter_smem_bytes(kMaxFanout)));
-  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_scatter<KeyT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_scatter<KeyT, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)scatter_smem_bytes(kPass2SpanMax)));
+  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_scatter<KeyT, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)scatter_smem_bytes(kPass2SpanMax)));
   MDJ_CUDA_TRY(cudaFuncSetAttribute(k_hist<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)((kMaxFanout + kMaxSubBuckets) * 4)));
@@ -696,8 +712,8 @@ int stable_pass(Workspace &ws, const KeyT *keys, uint32_t n, const BucketSpec &b
     MDJ_TRY((launch_pipe<KeyT, false>(ws, n, bs, F, ntiles, hist, nullptr, 1, F, pc)));
   } else {
     TraceScope tr("scatter_stable", s);
-    k_scatter<KeyT, false><<<ntiles, kNW * 32, scatter_smem_bytes(F), s>>>(keys, n, bs, F, ntiles, hist, nullptr, 1,
-                                                                          cm, rid_in, rid_out);
+    k_scatter<KeyT, false, false><<<ntiles, kNW * 32, scatter_smem_bytes(F), s>>>(
+        keys, n, bs, F, ntiles, hist, nullptr, 1, cm, rid_in, rid_out, nullptr, nullptr, nullptr);
   }
   MDJ_LAUNCH_CHECK();
   ws.give_back(hist);
@@ -721,8 +737,8 @@ int reserve_pass(Workspace &ws, const KeyT *keys, uint32_t n, const BucketSpec &
   if (ntiles == 0) return MDJ_OK;
   {
     TraceScope tr("scatter_reserve", s);
-    k_scatter<KeyT, true><<<ntiles, kNW * 32, scatter_smem_bytes(kPass2SpanMax), s>>>(
-        keys, n, bs_sub, 0, ntiles, nullptr, cursors, F2, cm, rid_in, rid_out);
+    k_scatter<KeyT, true, false><<<ntiles, kNW * 32, scatter_smem_bytes(kPass2SpanMax), s>>>(
+        keys, n, bs_sub, 0, ntiles, nullptr, cursors, F2, cm, rid_in, rid_out, nullptr, nullptr, nullptr);
   }
   MDJ_LAUNCH_CHECK();
   return MDJ_OK;
@@ -995,8 +1011,9 @@ int stable_partition_scratch_t(const mdj_table *t, int32_t key_col, uint32_t P, 
     const void *src[MDJ_MAX_COLS];
     for (int j = 0; j < t->ncols; j++) src[j] = t->cols[j].data;
     ColMove cm = make_move(t, key_col, src, out_cols);
-    k_scatter<KeyT, false><<<ntiles, kNW * 32, scatter_smem_bytes(F), s>>>(
-        (const KeyT *)src[key_col], n, bs, F, ntiles, hist, nullptr, 1, cm, nullptr, out_rid);
+    k_scatter<KeyT, false, false><<<ntiles, kNW * 32, scatter_smem_bytes(F), s>>>(
+        (const KeyT *)src[key_col], n, bs, F, ntiles, hist, nullptr, 1, cm, nullptr, out_rid, nullptr, nullptr,
+        nullptr);
     MDJ_LAUNCH_CHECK();
   }
   k_u32_to_i64<<<(P + 1 + 255) / 256, 256, 0, s>>>(start, out_offsets, P + 1);
@@ -1019,6 +1036,126 @@ int stable_partition_scratch(const mdj_table *t, int32_t key_col, uint32_t P, vo
                                                scratch_words, s);
   return stable_partition_scratch_t<int32_t>(t, key_col, P, out_cols, out_rid, out_offsets, scratch, scratch_words,
                                              s);
+}
+
+}  // namespace mdj
+
+// ------------------------------------------------- segmented (batched) form
+namespace mdj {
+namespace {
+
+// Per tile: counts of its segment's buckets, added into totals[seg_base + b].
+template <typename KeyT>
+__global__ void __launch_bounds__(kHistThreads) k_seg_hist(const KeyT *__restrict__ keys,
+                                                           const SegTile *__restrict__ tiles,
+                                                           const uint32_t *__restrict__ seg_base,
+                                                           const uint32_t *__restrict__ seg_nb,
+                                                           uint32_t *__restrict__ totals) {
+  extern __shared__ uint32_t cnt[];
+  const SegTile td = tiles[blockIdx.x];
+  const uint32_t S = seg_nb[td.seg], B = seg_base[td.seg];
+  for (uint32_t b = threadIdx.x; b < S; b += blockDim.x) cnt[b] = 0;
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < td.rows; i += blockDim.x) {
+    const uint64_t h = fmix64(key_bits(keys[td.row0 + i]));
+    atomicAdd(&cnt[__umulhi((uint32_t)(h >> 32), S)], 1u);
+  }
+  __syncthreads();
+  for (uint32_t b = threadIdx.x; b < S; b += blockDim.x)
+    if (cnt[b]) atomicAdd(&totals[B + b], cnt[b]);
+}
+
+template <typename T>
+T *upload(Workspace &ws, const std::vector<T> &v) {
+  T *d = (T *)ws.get(v.size() * sizeof(T) + 16);
+  if (!d) return nullptr;
+  if (!v.empty() && cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, ws.stream()) !=
+                        cudaSuccess)
+    return nullptr;
+  return d;
+}
+
+template <typename KeyT>
+int seg_partition_t(Workspace &ws, const mdj_table *t, int32_t key_col, const uint64_t *seg_off, uint32_t nseg,
+                    const uint32_t *seg_base, const uint32_t *seg_nb, uint32_t nb, Side *out) {
+  cudaStream_t s = ws.stream();
+  const uint32_t n = (uint32_t)t->nrows;
+  const void *src[MDJ_MAX_COLS];
+  for (int j = 0; j < t->ncols; j++) src[j] = t->cols[j].data;
+  bool all_single = true;
+  for (uint32_t i = 0; i < nseg; i++) all_single = all_single && seg_nb[i] == 1;
+
+  const void *key = src[key_col];
+  const void *const *cols = src;
+  const uint32_t *rid = nullptr;
+  uint32_t *off = nullptr;
+  TableBufs fin;
+  fin.rid = nullptr;
+  if (all_single) {
+    // every segment is one bucket: bucket offsets are the segment offsets
+    std::vector<uint32_t> h(nseg + 1);
+    for (uint32_t i = 0; i <= nseg; i++) h[i] = (uint32_t)seg_off[i];
+    off = upload(ws, h);
+    if (!off) return MDJ_ERR_OOM;
+  } else {
+    MDJ_TRY(set_smem_attrs<KeyT>());
+    std::vector<SegTile> tiles;
+    for (uint32_t i = 0; i < nseg; i++)
+      for (uint64_t r = seg_off[i]; r < seg_off[i + 1]; r += kTile)
+        tiles.push_back(SegTile{(uint32_t)r, (uint32_t)std::min<uint64_t>(kTile, seg_off[i + 1] - r), i});
+    std::vector<uint32_t> hb(seg_base, seg_base + nseg), hs(seg_nb, seg_nb + nseg);
+    SegTile *dt = upload(ws, tiles);
+    uint32_t *db = upload(ws, hb), *ds = upload(ws, hs);
+    off = (uint32_t *)ws.get((size_t)(nb + 1) * 4);
+    uint32_t *cur = (uint32_t *)ws.get((size_t)(nb + 1) * 4);
+    if (!dt || !db || !ds || !off || !cur) return MDJ_ERR_OOM;
+    MDJ_CUDA_TRY(cudaMemsetAsync(off, 0, (size_t)(nb + 1) * 4, s));
+    uint32_t smax = 1;
+    for (uint32_t i = 0; i < nseg; i++) smax = std::max(smax, seg_nb[i]);
+    if (!tiles.empty()) {
+      TraceScope tr("seg_hist", s);
+      k_seg_hist<KeyT><<<(unsigned)tiles.size(), kHistThreads, smax * 4, s>>>((const KeyT *)key, dt, db, ds, off);
+    }
+    MDJ_LAUNCH_CHECK();
+    MDJ_TRY(exclusive_scan_u32(ws, off, off, nb + 1));
+    MDJ_CUDA_TRY(cudaMemcpyAsync(cur, off, (size_t)nb * 4, cudaMemcpyDeviceToDevice, s));
+    MDJ_TRY(alloc_table_bufs(ws, t, &fin, true));
+    ColMove cm = make_move(t, key_col, src, fin.cols);
+    if (!tiles.empty()) {
+      TraceScope tr("seg_scatter", s);
+      k_scatter<KeyT, true, true><<<(unsigned)tiles.size(), kNW * 32, scatter_smem_bytes(kPass2SpanMax), s>>>(
+          (const KeyT *)key, n, make_spec(1, 1, 1), 0, (uint32_t)tiles.size(), nullptr, cur, 1, cm, nullptr,
+          fin.rid, dt, db, ds);
+    }
+    MDJ_LAUNCH_CHECK();
+    key = fin.cols[key_col];
+    cols = fin.cols;
+    rid = fin.rid;
+  }
+  out->key = key;
+  out->key_dtype = t->cols[key_col].dtype;
+  out->ncols = 0;
+  for (int j = 0; j < t->ncols; j++) {
+    if (j == key_col) continue;
+    out->cols[out->ncols] = cols[j];
+    out->widths[out->ncols] = dtype_width(t->cols[j].dtype);
+    out->dtypes[out->ncols] = t->cols[j].dtype;
+    out->ncols++;
+  }
+  out->rid = rid;
+  out->off = off;
+  out->nrows = n;
+  return MDJ_OK;
+}
+
+}  // namespace
+
+int partition_side_segmented(Workspace &ws, const mdj_table *t, int32_t key_col, const uint64_t *seg_off,
+                             uint32_t nseg, const uint32_t *seg_base, const uint32_t *seg_nb, uint32_t nbuckets,
+                             Side *out) {
+  if (t->cols[key_col].dtype == MDJ_I64)
+    return seg_partition_t<int64_t>(ws, t, key_col, seg_off, nseg, seg_base, seg_nb, nbuckets, out);
+  return seg_partition_t<int32_t>(ws, t, key_col, seg_off, nseg, seg_base, seg_nb, nbuckets, out);
 }
 
 }  // namespace mdj

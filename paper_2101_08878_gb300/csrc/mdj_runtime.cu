@@ -11,6 +11,8 @@
 
 namespace mdj {
 
+extern thread_local char g_last_cuda_error[256];
+
 // ----------------------------------------------------------------- workspace
 
 void *Workspace::raw_alloc(size_t bytes) {
@@ -80,7 +82,7 @@ int num_sms() {
   return cached[dev];
 }
 
-static thread_local char g_last_cuda_error[256];
+thread_local char g_last_cuda_error[256];
 
 int cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return MDJ_OK;
@@ -236,6 +238,8 @@ const char *mdj_status_string(int status) {
 }
 
 int mdj_version(void) { return MDJ_VERSION; }
+
+const char *mdj_last_error(void) { return g_last_cuda_error[0] ? g_last_cuda_error : ""; }
 
 void mdj_result_release(mdj_result *res, const mdj_allocator *alloc, void *stream) {
   if (!res) return;

@@ -34,8 +34,9 @@ _TORCH_TO_MDJ = {
 _MDJ_TO_TORCH = {v: k for k, v in _TORCH_TO_MDJ.items()}
 
 EXPORTED = [
-    "mdj_partition", "mdj_partition_noalloc", "mdj_join", "mdj_merge", "mdj_count_checksum", "mdj_result_release",
-    "mdj_status_string", "mdj_version", "mdj_profile_enable", "mdj_profile_reset",
+    "mdj_partition", "mdj_partition_noalloc", "mdj_join", "mdj_merge", "mdj_count_checksum", "mdj_join_batch",
+    "mdj_result_release",
+    "mdj_status_string", "mdj_last_error", "mdj_version", "mdj_profile_enable", "mdj_profile_reset",
     "mdj_profile_collect", "mdj_profile_count", "mdj_profile_get",
 ]
 
@@ -74,6 +75,10 @@ class MdjResult(ctypes.Structure):
     ]
 
 
+class MdjTuning(ctypes.Structure):
+    _fields_ = [("table_rows", ctypes.c_uint32), ("fill_pct", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 6)]
+
+
 _lib = None
 _lib_lock = threading.Lock()
 
@@ -103,11 +108,15 @@ def load(path: str = LIB_PATH):
         lib.mdj_count_checksum.restype = ctypes.c_int
         lib.mdj_count_checksum.argtypes = [P(MdjTable), i32, P(MdjTable), i32, u32, P(MdjAllocator), vp,
                                            P(u64), P(u64)]
+        lib.mdj_join_batch.restype = ctypes.c_int
+        lib.mdj_join_batch.argtypes = [P(MdjTable), i32, P(u64), P(MdjTable), i32, P(u64), i32, P(MdjTuning),
+                                       P(MdjAllocator), vp, P(MdjResult), P(u64)]
         lib.mdj_result_release.restype = None
         lib.mdj_result_release.argtypes = [P(MdjResult), P(MdjAllocator), vp]
         lib.mdj_status_string.restype = ctypes.c_char_p
         lib.mdj_status_string.argtypes = [ctypes.c_int]
         lib.mdj_version.restype = ctypes.c_int
+        lib.mdj_last_error.restype = ctypes.c_char_p
         lib.mdj_profile_enable.argtypes = [ctypes.c_int]
         lib.mdj_profile_enable.restype = None
         lib.mdj_profile_reset.restype = None
@@ -181,7 +190,10 @@ def _stream_handle(device) -> int:
 
 def _check(rc: int, what: str):
     if rc != MDJ_OK:
-        raise MdjError(rc, what)
+        detail = ""
+        if rc == -5 and _lib is not None:
+            detail = _lib.mdj_last_error().decode(errors="replace")
+        raise MdjError(rc, what + (f" [{detail}]" if detail else ""))
 
 
 @dataclass
@@ -274,6 +286,36 @@ def mdj_count_checksum(left_cols: Sequence[torch.Tensor], right_cols: Sequence[t
                                 ctypes.byref(chk))
     _check(rc, "mdj_count_checksum")
     return cnt.value, chk.value
+
+
+def mdj_join_batch(left_cols: Sequence[torch.Tensor], right_cols: Sequence[torch.Tensor], left_offsets,
+                   right_offsets, left_key: int = 0, right_key: int = 0, table_rows: int = 0,
+                   fill_pct: int = 0):
+    """Independent joins of pair i = left rows [left_offsets[i], left_offsets[i+1])
+    with right rows [right_offsets[i], right_offsets[i+1]) (see mdj.h).
+
+    Returns (JoinResult of all pairs, pair_offsets) where pair i's output rows
+    are [pair_offsets[i], pair_offsets[i+1]); row ids index the whole tables."""
+    lib = load()
+    dev = left_cols[0].device
+    lt, lk = _table(left_cols)
+    rt, rk = _table(right_cols)
+    lo = [int(x) for x in left_offsets]
+    ro = [int(x) for x in right_offsets]
+    if len(lo) != len(ro) or len(lo) < 2:
+        raise ValueError("left_offsets and right_offsets need npairs + 1 entries each")
+    npairs = len(lo) - 1
+    lo_c = (ctypes.c_uint64 * len(lo))(*lo)
+    ro_c = (ctypes.c_uint64 * len(ro))(*ro)
+    po_c = (ctypes.c_uint64 * len(lo))()
+    tun = MdjTuning(table_rows, fill_pct)
+    alloc = TorchAllocator(dev)
+    res = MdjResult()
+    rc = lib.mdj_join_batch(ctypes.byref(lt), left_key, lo_c, ctypes.byref(rt), right_key, ro_c, npairs,
+                            ctypes.byref(tun), ctypes.byref(alloc.struct), _stream_handle(dev), ctypes.byref(res),
+                            po_c)
+    _check(rc, "mdj_join_batch")
+    return _adopt_result(res, alloc), [int(x) for x in po_c]
 
 
 def mdj_status_string(status: int) -> str:

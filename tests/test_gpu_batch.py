@@ -1,0 +1,128 @@
+"""mdj_join_batch: many independent partition-pair joins in one call.
+
+Each pair's slice of the output is compared with the oracle's merge of that
+pair's two slices (row ids shifted by the slice starts); the config-3 shape
+(256 pairs, sizes log-uniform in [1K, 4M] per side, match fraction U[0.1,0.9])
+is checked at full size by the per-pair closed-form row count plus the oracle
+on a sample of pairs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from joinhelp import bits
+from paper_2101_08878_gb300 import datagen
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda", 0)
+
+
+def _mdj():
+    from paper_2101_08878_gb300 import mdj
+    return mdj
+
+
+def _concat(pairs):
+    lk = np.concatenate([p[0][0] for p in pairs])
+    lp = np.concatenate([p[0][1] for p in pairs])
+    rk = np.concatenate([p[1][0] for p in pairs])
+    rp = np.concatenate([p[1][1] for p in pairs])
+    lo = np.concatenate([[0], np.cumsum([p[0][0].size for p in pairs])]).astype(np.uint64)
+    ro = np.concatenate([[0], np.cumsum([p[1][0].size for p in pairs])]).astype(np.uint64)
+    return (lk, lp), (rk, rp), lo, ro
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _check_pair(res_np, po, i, pair, lo, ro):
+    (lk, lp), (rk, rp) = pair
+    a, b = po[i], po[i + 1]
+    key = res_np["key"][a:b]
+    lrow = res_np["left_row"][a:b].astype(np.int64) - int(lo[i])
+    rrow = res_np["right_row"][a:b].astype(np.int64) - int(ro[i])
+    assert np.all((lrow >= 0) & (lrow < lk.size)) and np.all((rrow >= 0) & (rrow < rk.size))
+    order = np.lexsort((rrow, lrow, key))
+    want = oracle.merge_table([lk, lp], [rk, rp])
+    assert np.array_equal(key[order], want["key"])
+    assert np.array_equal(lrow[order].astype(np.uint32), want["left_row"])
+    assert np.array_equal(rrow[order].astype(np.uint32), want["right_row"])
+    assert np.array_equal(bits(res_np["lpay"][a:b][order]), bits(want["left_cols"][0]))
+    assert np.array_equal(bits(res_np["rpay"][a:b][order]), bits(want["right_cols"][0]))
+
+
+def _run_batch(pairs, **kw):
+    (lk, lp), (rk, rp), lo, ro = _concat(pairs)
+    mdj = _mdj()
+    res, po = mdj.mdj_join_batch([torch.from_numpy(lk).to(DEV), torch.from_numpy(lp).to(DEV)],
+                                 [torch.from_numpy(rk).to(DEV), torch.from_numpy(rp).to(DEV)], lo, ro, **kw)
+    torch.cuda.synchronize()
+    res_np = {"key": _np(res.key), "left_row": _np(res.left_row).view(np.uint32),
+              "right_row": _np(res.right_row).view(np.uint32), "lpay": _np(res.left_cols[0]),
+              "rpay": _np(res.right_cols[0])}
+    return res, res_np, po, lo, ro
+
+
+def _ragged_pairs(seed):
+    rng = np.random.default_rng(seed)
+    pairs = []
+    for i in range(40):
+        nl, nr = int(rng.integers(0, 30_000)), int(rng.integers(0, 30_000))
+        if i % 7 == 0:
+            nl = 0
+        if i % 11 == 0:
+            nr = 0
+        kr = int(rng.choice([50, 5_000, 10**9]))
+        pairs.append(datagen.random_tables(nl, nr, kr, seed=seed * 100 + i))
+    return pairs
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_batch_ragged_pairs_match_oracle(seed):
+    pairs = _ragged_pairs(seed)
+    res, res_np, po, lo, ro = _run_batch(pairs)
+    assert po[0] == 0 and po[-1] == res.nrows and all(po[i] <= po[i + 1] for i in range(len(pairs)))
+    for i, pair in enumerate(pairs):
+        _check_pair(res_np, po, i, pair, lo, ro)
+
+
+@pytest.mark.parametrize("table_rows,fill_pct", [(1024, 50), (2048, 85), (8192, 95), (8192, 30)])
+def test_batch_tuning_does_not_change_rows(table_rows, fill_pct):
+    pairs = [datagen.match_fraction_tables(n, 2 * n, 0.5, seed=n) for n in (100, 5_000, 60_000, 150_000)]
+    res, res_np, po, lo, ro = _run_batch(pairs, table_rows=table_rows, fill_pct=fill_pct)
+    for i, pair in enumerate(pairs):
+        assert po[i + 1] - po[i] == math.floor(0.5 * 2 * pair[0][0].size)
+        _check_pair(res_np, po, i, pair, lo, ro)
+
+
+def test_batch_invalid_arguments():
+    mdj = _mdj()
+    k = torch.arange(10, device=DEV)
+    with pytest.raises(mdj.MdjError):
+        mdj.mdj_join_batch([k], [k], [0, 5, 9], [0, 5, 10])      # last offset != rows
+    with pytest.raises(mdj.MdjError):
+        mdj.mdj_join_batch([k], [k], [0, 6, 5, 10], [0, 5, 5, 10])  # decreasing
+    with pytest.raises(mdj.MdjError):
+        mdj.mdj_join_batch([k], [k], [0, 10], [0, 10], table_rows=100)
+    with pytest.raises(mdj.MdjError):
+        mdj.mdj_join_batch([k], [k], [0, 10], [0, 10], table_rows=16384)
+
+
+@pytest.mark.slow
+def test_batch_config3_full_size():
+    # 256 pairs, n_L, n_R log-uniform in [1K, 4M], match fraction U[0.1, 0.9]
+    pairs = datagen.batch_pairs(256, 1_000, 4_000_000, seed=3)
+    res, res_np, po, lo, ro = _run_batch(pairs)
+    rng = np.random.default_rng(0)
+    for i, ((lk, _), (rk, _)) in enumerate(pairs):
+        # unique left keys: each right row meets at most one left row, and the
+        # generator makes exactly floor(f * n_R) of them match
+        n_match = int(np.count_nonzero(rk < lk.size))
+        assert po[i + 1] - po[i] == n_match
+    for i in rng.choice(len(pairs), 6, replace=False):
+        _check_pair(res_np, po, int(i), pairs[int(i)], lo, ro)
