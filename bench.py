@@ -295,11 +295,68 @@ def run_gpu(args):
         "roofline": roofline, "step_roofline": step_roof, "kernels": kernels, "gpu_launches": launches,
         "e2e": e2e, "clocks": clk.summary(),
     }
+    if args.batch_pairs > 0:
+        line["batched"] = batched_section(args, dev)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def batched_section(args, dev):
+    """Config 3: 256 independent partition-pair joins (n_L, n_R log-uniform in
+    [1K, 4M], match fraction U[0.1, 0.9]) through mdj_join_batch (tuned) versus
+    the plain path, one mdj_join call per pair.  Input rows/s of each."""
+    import torch
+    from paper_2101_08878_gb300 import mdj
+    from paper_2101_08878_gb300.tuner import BatchTuner
+
+    pairs = datagen.batch_pairs(args.batch_pairs, 1_000, 4_000_000, seed=3)
+    lo = np.concatenate([[0], np.cumsum([p[0][0].size for p in pairs])]).astype(np.uint64)
+    ro = np.concatenate([[0], np.cumsum([p[1][0].size for p in pairs])]).astype(np.uint64)
+    L = [torch.from_numpy(np.concatenate([p[0][0] for p in pairs])).to(dev),
+         torch.from_numpy(np.concatenate([p[0][1] for p in pairs])).to(dev)]
+    R = [torch.from_numpy(np.concatenate([p[1][0] for p in pairs])).to(dev),
+         torch.from_numpy(np.concatenate([p[1][1] for p in pairs])).to(dev)]
+    rows = int(lo[-1] + ro[-1])
+    expect = sum(int(np.count_nonzero(p[1][0] < p[0][0].size)) for p in pairs)
+    del pairs
+    tuner = BatchTuner()
+    tr, fp = tuner.choose(L, R, lo, ro)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, steps):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    def batched():
+        res, po = mdj.mdj_join_batch(L, R, lo, ro, 0, 0, tr, fp)
+        assert res.nrows == expect
+
+    def plain():
+        m = 0
+        for i in range(len(lo) - 1):
+            a, b, c, d = int(lo[i]), int(lo[i + 1]), int(ro[i]), int(ro[i + 1])
+            m += mdj.mdj_join([L[0][a:b], L[1][a:b]], [R[0][c:d], R[1][c:d]]).nrows
+        assert m == expect
+
+    ms_b = timed(batched, 5)
+    ms_p = timed(plain, 2)
+    return {"workload": f"{len(lo) - 1} pairs, sizes log-uniform [1K, 4M] per side, match U[0.1, 0.9], "
+                        f"int64 key + float64 payload, {rows} input rows, {expect} output rows",
+            "batched": {"value": rows / (ms_b / 1e3), "unit": UNIT, "ms_per_batch": round(ms_b, 3),
+                        "tuning": {"table_rows": tr, "fill_pct": fp}},
+            "plain_per_pair": {"value": rows / (ms_p / 1e3), "unit": UNIT, "ms_per_batch": round(ms_p, 3)},
+            "speedup": round(ms_p / ms_b, 3)}
 
 
 def measured_traffic(kernel: str):
@@ -365,6 +422,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=10_000_000)
     ap.add_argument("--ref-sample", type=int, default=2_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-pairs", type=int, default=256,
+                    help="pairs of the batched-vs-plain section (0 skips it)")
     ap.add_argument("--rows", type=int, default=None,
                     help="rows per side (default 100M); smaller values are for profiling captures only")
     args = ap.parse_args()

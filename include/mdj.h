@@ -231,6 +231,25 @@ MDJ_API int mdj_join_batch(const mdj_table *left, int32_t left_key, const uint64
                            int32_t npairs, const mdj_tuning *tuning, const mdj_allocator *alloc,
                            void *stream, mdj_result *out, uint64_t *pair_offsets);
 
+/*
+ * mdj_merge_batch - many independent merge requests (the whole hot path of
+ * Sec. V-B per request: shuffle into P[i] partitions, then join every
+ * partition pair) in a fixed number of launches.  Request i's tables are rows
+ * [left_offsets[i], left_offsets[i+1]) of `left` and [right_offsets[i],
+ * right_offsets[i+1]) of `right`; its rows are hash partitioned into P[i]
+ * partitions (1 <= P[i] <= 1024) inside its own region of the shuffled copy,
+ * and the output holds request 0's rows, then request 1's, ...: request i's
+ * rows are [req_offsets[i], req_offsets[i+1]) (host array of nreq+1, filled).
+ * left_row / right_row index the whole `left` / `right` tables.  Within a
+ * request the rows are those of mdj_merge on its two slices with P[i].
+ * Synchronises `stream` before returning.
+ */
+MDJ_API int mdj_merge_batch(const mdj_table *left, int32_t left_key, const uint64_t *left_offsets,
+                            const mdj_table *right, int32_t right_key, const uint64_t *right_offsets,
+                            int32_t nreq, const uint32_t *P, const mdj_tuning *tuning,
+                            const mdj_allocator *alloc, void *stream, mdj_result *out,
+                            uint64_t *req_offsets);
+
 /* Releases every array of *res with `alloc` (stream order) and zeroes *res. */
 MDJ_API void mdj_result_release(mdj_result *res, const mdj_allocator *alloc, void *stream);
 

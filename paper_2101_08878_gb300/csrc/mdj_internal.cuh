@@ -91,6 +91,21 @@ struct SegTile {
 BucketSpec make_spec(uint32_t P, uint32_t S, uint32_t div);
 BucketSpec make_digit_spec(uint32_t P, uint32_t dmul, uint32_t dmod);
 
+// Partition-only spec built on the device (one per segment of a batch).
+__device__ __forceinline__ BucketSpec make_spec_dev(uint32_t P) {
+  BucketSpec b;
+  b.P = P;
+  b.M = 0xFFFFFFFFFFFFFFFFull / P;
+  b.S = 1;
+  b.S1 = 1;
+  b.div = 1;
+  b.dmul = 1;
+  b.dmod = 1;
+  b.pow2 = (P & (P - 1)) == 0;
+  b.digit_mode = 0;
+  return b;
+}
+
 // ------------------------------------------------------------ primitives
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -249,11 +264,12 @@ int partition_side(Workspace &ws, const mdj_table *t, int32_t key_col, const Pla
                    Side *out);
 
 // Segmented partition of a batch: segment i = rows [seg_off[i], seg_off[i+1])
-// (host array) is split into seg_nb[i] buckets numbered from seg_base[i] by
-// floor(hi32(fmix64(key)) * seg_nb[i] / 2^32).  nbuckets = sum of seg_nb.
+// (host array) is split into seg_nb[i] = P_i * S_i buckets numbered from
+// seg_base[i]: bucket p * S_i + floor(hi32(h) * S_i / 2^32), p = h mod P_i,
+// h = fmix64(key) (all host arrays).  nbuckets = sum of seg_nb.
 int partition_side_segmented(Workspace &ws, const mdj_table *t, int32_t key_col, const uint64_t *seg_off,
-                             uint32_t nseg, const uint32_t *seg_base, const uint32_t *seg_nb, uint32_t nbuckets,
-                             Side *out);
+                             uint32_t nseg, const uint32_t *seg_base, const uint32_t *seg_nb, const uint32_t *seg_P,
+                             uint32_t nbuckets, Side *out);
 
 // Stable partition into caller buffers (the mdj_partition body).
 int stable_partition(Workspace &ws, const mdj_table *t, int32_t key_col, uint32_t P,

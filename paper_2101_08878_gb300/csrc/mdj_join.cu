@@ -889,6 +889,91 @@ int merge_impl(const mdj_table *left, int32_t lk, const mdj_table *right, int32_
   return k64 ? run_join<int64_t>(ws, L, R, plan, out) : run_join<int32_t>(ws, L, R, plan, out);
 }
 
+
+// A batch of independent merges (P given) or joins (P NULL, i.e. all 1): segment
+// i = rows [lo[i], lo[i+1]) of `left` and [ro[i], ro[i+1]) of `right`, hash
+// split into P_i partitions of S_i sub-buckets each; all buckets joined by one
+// persistent kernel in ordered mode, so segment i's rows come out contiguous.
+int batch_impl(const mdj_table *left, int32_t left_key, const uint64_t *left_offsets, const mdj_table *right,
+               int32_t right_key, const uint64_t *right_offsets, int32_t npairs, const uint32_t *P,
+               const mdj_tuning *tuning, const mdj_allocator *alloc, void *stream, mdj_result *out,
+               uint64_t *pair_offsets) {
+  MDJ_TRY(check_table(left, left_key));
+  MDJ_TRY(check_table(right, right_key));
+  if (left->cols[left_key].dtype != right->cols[right_key].dtype) return MDJ_ERR_INVALID_ARG;
+  if (npairs < 1 || !left_offsets || !right_offsets || !out || !pair_offsets) return MDJ_ERR_INVALID_ARG;
+  if (left_offsets[0] != 0 || right_offsets[0] != 0 || left_offsets[npairs] != left->nrows ||
+      right_offsets[npairs] != right->nrows)
+    return MDJ_ERR_INVALID_ARG;
+  for (int32_t i = 0; i < npairs; i++) {
+    if (left_offsets[i + 1] < left_offsets[i] || right_offsets[i + 1] < right_offsets[i]) return MDJ_ERR_INVALID_ARG;
+    if (P && (P[i] < 1 || P[i] > kPass2SpanMax)) return MDJ_ERR_INVALID_ARG;
+  }
+  memset(out, 0, sizeof *out);
+  uint32_t cap = cap_from_env();
+  uint32_t fill = 85;
+  if (tuning) {
+    if (tuning->table_rows) {
+      if (tuning->table_rows < 256 || tuning->table_rows > kMaxCap) return MDJ_ERR_INVALID_ARG;
+      cap = tuning->table_rows;
+    }
+    if (tuning->fill_pct) {
+      if (tuning->fill_pct < 10 || tuning->fill_pct > 100) return MDJ_ERR_INVALID_ARG;
+      fill = tuning->fill_pct;
+    }
+  }
+  const uint64_t target = std::max<uint64_t>(1, (uint64_t)cap * fill / 100);
+  std::vector<uint32_t> seg_nb(npairs), seg_base(npairs), seg_P(npairs);
+  uint64_t nb = 0;
+  for (int32_t i = 0; i < npairs; i++) {
+    const uint64_t nl = left_offsets[i + 1] - left_offsets[i], nr = right_offsets[i + 1] - right_offsets[i];
+    const uint32_t Pi = P ? P[i] : 1u;
+    // the shuffle of a merge always runs; a join of an empty side needs no buckets
+    uint64_t S = (nl && nr) ? (nl + target * Pi - 1) / (target * Pi) : 1;
+    S = std::min<uint64_t>(std::max<uint64_t>(S, 1), kPass2SpanMax / Pi);
+    seg_P[i] = Pi;
+    seg_nb[i] = (uint32_t)(Pi * S);
+    seg_base[i] = (uint32_t)nb;
+    nb += seg_nb[i];
+  }
+  if (nb >= (1ull << 31)) return MDJ_ERR_TOO_LARGE;
+  Workspace ws(alloc, (cudaStream_t)stream);
+  cudaStream_t s = (cudaStream_t)stream;
+  Side L, R;
+  MDJ_TRY(partition_side_segmented(ws, left, left_key, left_offsets, npairs, seg_base.data(), seg_nb.data(),
+                                   seg_P.data(), (uint32_t)nb, &L));
+  MDJ_TRY(partition_side_segmented(ws, right, right_key, right_offsets, npairs, seg_base.data(), seg_nb.data(),
+                                   seg_P.data(), (uint32_t)nb, &R));
+  Plan plan;
+  plan.P = 1;
+  plan.nbuckets = (uint32_t)nb;
+  plan.cap = cap;
+  ItemMap map;
+  const bool k64 = left->cols[left_key].dtype == MDJ_I64;
+  MDJ_TRY(k64 ? run_join<int64_t>(ws, L, R, plan, out, true, &map) : run_join<int32_t>(ws, L, R, plan, out, true, &map));
+  // segment boundaries in the (segment-major) output
+  uint32_t *dbase = (uint32_t *)ws.get((size_t)npairs * 4);
+  uint64_t *doff = (uint64_t *)ws.get((size_t)(npairs + 1) * 8);
+  int rc = MDJ_OK;
+  if (!dbase || !doff) rc = MDJ_ERR_OOM;
+  if (rc == MDJ_OK)
+    rc = cuda_status(cudaMemcpyAsync(dbase, seg_base.data(), (size_t)npairs * 4, cudaMemcpyHostToDevice, s));
+  if (rc == MDJ_OK) {
+    {
+      TraceScope tr("pair_offsets", s);
+      k_pair_offsets<<<(npairs + 1 + 255) / 256, 256, 0, s>>>(dbase, (uint32_t)npairs, (uint32_t)nb,
+                                                              map.bucket_items, map.item_out, map.nitems, out->nrows,
+                                                              doff);
+    }
+    rc = cuda_status(cudaGetLastError());
+  }
+  if (rc == MDJ_OK)
+    rc = cuda_status(cudaMemcpyAsync(pair_offsets, doff, (size_t)(npairs + 1) * 8, cudaMemcpyDeviceToHost, s));
+  if (rc == MDJ_OK) rc = cuda_status(cudaStreamSynchronize(s));
+  if (rc != MDJ_OK) mdj_result_release(out, alloc, stream);
+  return rc;
+}
+
 }  // namespace
 }  // namespace mdj
 
@@ -925,75 +1010,17 @@ int mdj_count_checksum(const mdj_table *left, int32_t left_key, const mdj_table 
 int mdj_join_batch(const mdj_table *left, int32_t left_key, const uint64_t *left_offsets, const mdj_table *right,
                    int32_t right_key, const uint64_t *right_offsets, int32_t npairs, const mdj_tuning *tuning,
                    const mdj_allocator *alloc, void *stream, mdj_result *out, uint64_t *pair_offsets) {
-  MDJ_TRY(check_table(left, left_key));
-  MDJ_TRY(check_table(right, right_key));
-  if (left->cols[left_key].dtype != right->cols[right_key].dtype) return MDJ_ERR_INVALID_ARG;
-  if (npairs < 1 || !left_offsets || !right_offsets || !out || !pair_offsets) return MDJ_ERR_INVALID_ARG;
-  if (left_offsets[0] != 0 || right_offsets[0] != 0 || left_offsets[npairs] != left->nrows ||
-      right_offsets[npairs] != right->nrows)
-    return MDJ_ERR_INVALID_ARG;
-  for (int32_t i = 0; i < npairs; i++)
-    if (left_offsets[i + 1] < left_offsets[i] || right_offsets[i + 1] < right_offsets[i]) return MDJ_ERR_INVALID_ARG;
-  memset(out, 0, sizeof *out);
-  uint32_t cap = cap_from_env();
-  uint32_t fill = 85;
-  if (tuning) {
-    if (tuning->table_rows) {
-      if (tuning->table_rows < 256 || tuning->table_rows > kMaxCap) return MDJ_ERR_INVALID_ARG;
-      cap = tuning->table_rows;
-    }
-    if (tuning->fill_pct) {
-      if (tuning->fill_pct < 10 || tuning->fill_pct > 100) return MDJ_ERR_INVALID_ARG;
-      fill = tuning->fill_pct;
-    }
-  }
-  const uint64_t target = std::max<uint64_t>(1, (uint64_t)cap * fill / 100);
-  std::vector<uint32_t> seg_nb(npairs), seg_base(npairs);
-  uint64_t nb = 0;
-  for (int32_t i = 0; i < npairs; i++) {
-    const uint64_t nl = left_offsets[i + 1] - left_offsets[i], nr = right_offsets[i + 1] - right_offsets[i];
-    uint64_t S = (nl && nr) ? (nl + target - 1) / target : 1;
-    S = std::min<uint64_t>(std::max<uint64_t>(S, 1), kPass2SpanMax);
-    seg_nb[i] = (uint32_t)S;
-    seg_base[i] = (uint32_t)nb;
-    nb += S;
-  }
-  if (nb >= (1ull << 31)) return MDJ_ERR_TOO_LARGE;
-  Workspace ws(alloc, (cudaStream_t)stream);
-  cudaStream_t s = (cudaStream_t)stream;
-  Side L, R;
-  MDJ_TRY(partition_side_segmented(ws, left, left_key, left_offsets, npairs, seg_base.data(), seg_nb.data(),
-                                   (uint32_t)nb, &L));
-  MDJ_TRY(partition_side_segmented(ws, right, right_key, right_offsets, npairs, seg_base.data(), seg_nb.data(),
-                                   (uint32_t)nb, &R));
-  Plan plan;
-  plan.P = 1;
-  plan.nbuckets = (uint32_t)nb;
-  plan.cap = cap;
-  ItemMap map;
-  const bool k64 = left->cols[left_key].dtype == MDJ_I64;
-  MDJ_TRY(k64 ? run_join<int64_t>(ws, L, R, plan, out, true, &map) : run_join<int32_t>(ws, L, R, plan, out, true, &map));
-  // pair boundaries in the (pair-major) output
-  uint32_t *dbase = (uint32_t *)ws.get((size_t)npairs * 4);
-  uint64_t *doff = (uint64_t *)ws.get((size_t)(npairs + 1) * 8);
-  int rc = MDJ_OK;
-  if (!dbase || !doff) rc = MDJ_ERR_OOM;
-  if (rc == MDJ_OK)
-    rc = cuda_status(cudaMemcpyAsync(dbase, seg_base.data(), (size_t)npairs * 4, cudaMemcpyHostToDevice, s));
-  if (rc == MDJ_OK) {
-    {
-      TraceScope tr("pair_offsets", s);
-      k_pair_offsets<<<(npairs + 1 + 255) / 256, 256, 0, s>>>(dbase, (uint32_t)npairs, (uint32_t)nb,
-                                                              map.bucket_items, map.item_out, map.nitems, out->nrows,
-                                                              doff);
-    }
-    rc = cuda_status(cudaGetLastError());
-  }
-  if (rc == MDJ_OK) rc = cuda_status(cudaMemcpyAsync(pair_offsets, doff, (size_t)(npairs + 1) * 8,
-                                                     cudaMemcpyDeviceToHost, s));
-  if (rc == MDJ_OK) rc = cuda_status(cudaStreamSynchronize(s));
-  if (rc != MDJ_OK) mdj_result_release(out, alloc, stream);
-  return rc;
+  return batch_impl(left, left_key, left_offsets, right, right_key, right_offsets, npairs, nullptr, tuning, alloc,
+                    stream, out, pair_offsets);
+}
+
+int mdj_merge_batch(const mdj_table *left, int32_t left_key, const uint64_t *left_offsets, const mdj_table *right,
+                    int32_t right_key, const uint64_t *right_offsets, int32_t nreq, const uint32_t *P,
+                    const mdj_tuning *tuning, const mdj_allocator *alloc, void *stream, mdj_result *out,
+                    uint64_t *req_offsets) {
+  if (!P) return MDJ_ERR_INVALID_ARG;
+  return batch_impl(left, left_key, left_offsets, right, right_key, right_offsets, nreq, P, tuning, alloc, stream,
+                    out, req_offsets);
 }
 
 }  // extern "C"

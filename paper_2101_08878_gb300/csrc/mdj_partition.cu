@@ -130,14 +130,18 @@ __device__ void scatter_direct(const KeyT (&kv)[kRPL], uint32_t wrow0, uint32_t 
 }
 
 // SEG (with RESERVE): tiles come from `seg_tiles` and never cross a segment;
-// a row's local bucket is floor(hi32(h) * S_seg / 2^32) among the segment's
-// S_seg buckets starting at seg_base[seg] (a batch of independent joins).
+// a segment with P_seg partitions of S_seg sub-buckets each puts a row in its
+// local bucket p * S_seg + floor(hi32(h) * S_seg / 2^32), p = h mod P_seg,
+// among the segment's buckets starting at seg_base[seg] (a batch of
+// independent merges; P_seg = 1 for a batch of joins).  seg_nb holds
+// P_seg * S_seg, seg_P holds P_seg and seg_S holds S_seg.
 template <typename KeyT, bool RESERVE, bool SEG>
 __global__ void __launch_bounds__(kNW * 32, 2)
     k_scatter(const KeyT *__restrict__ keys, uint32_t n, BucketSpec bs, uint32_t F, uint32_t ntiles,
               const uint32_t *__restrict__ tile_base, uint32_t *__restrict__ cursors, uint32_t F2, ColMove cm,
               const uint32_t *__restrict__ rid_in, uint32_t *__restrict__ rid_out, const SegTile *__restrict__ seg_tiles,
-              const uint32_t *__restrict__ seg_base, const uint32_t *__restrict__ seg_nb) {
+              const uint32_t *__restrict__ seg_base, const uint32_t *__restrict__ seg_nb,
+              const uint32_t *__restrict__ seg_P, const uint32_t *__restrict__ seg_S) {
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t FL = RESERVE ? kPass2SpanMax : F;
   uint64_t *stage64 = (uint64_t *)smem;
@@ -165,10 +169,12 @@ __global__ void __launch_bounds__(kNW * 32, 2)
   }
 
   uint32_t Floc = F, lb0 = 0, Sseg = 0;
+  BucketSpec sp = bs;
   if (SEG) {
     lb0 = seg_base[td.seg];
-    Sseg = seg_nb[td.seg];
-    Floc = Sseg;
+    Floc = seg_nb[td.seg];
+    Sseg = seg_S[td.seg];
+    sp = make_spec_dev(seg_P[td.seg]);
   } else if (RESERVE) {
     uint32_t b1f = sub_bucket_of(fmix64(key_bits(keys[row0])), bs) / F2;
     uint32_t b1l = sub_bucket_of(fmix64(key_bits(keys[rend - 1])), bs) / F2;
@@ -193,7 +199,7 @@ __global__ void __launch_bounds__(kNW * 32, 2)
     uint32_t b = 0xFFFFFFFFu;
     if (valid) {
       const uint64_t h = fmix64(key_bits(kv[c]));
-      b = SEG ? __umulhi((uint32_t)(h >> 32), Sseg) : bucket_of(h, bs) - lb0;
+      b = SEG ? mod_p(h, sp) * Sseg + __umulhi((uint32_t)(h >> 32), Sseg) : bucket_of(h, bs) - lb0;
     }
     uint32_t peers = __match_any_sync(0xffffffffu, b);
     uint32_t rank = __popc(peers & lanemask_lt());
@@ -713,7 +719,7 @@ int stable_pass(Workspace &ws, const KeyT *keys, uint32_t n, const BucketSpec &b
   } else {
     TraceScope tr("scatter_stable", s);
     k_scatter<KeyT, false, false><<<ntiles, kNW * 32, scatter_smem_bytes(F), s>>>(
-        keys, n, bs, F, ntiles, hist, nullptr, 1, cm, rid_in, rid_out, nullptr, nullptr, nullptr);
+        keys, n, bs, F, ntiles, hist, nullptr, 1, cm, rid_in, rid_out, nullptr, nullptr, nullptr, nullptr, nullptr);
   }
   MDJ_LAUNCH_CHECK();
   ws.give_back(hist);
@@ -738,7 +744,8 @@ int reserve_pass(Workspace &ws, const KeyT *keys, uint32_t n, const BucketSpec &
   {
     TraceScope tr("scatter_reserve", s);
     k_scatter<KeyT, true, false><<<ntiles, kNW * 32, scatter_smem_bytes(kPass2SpanMax), s>>>(
-        keys, n, bs_sub, 0, ntiles, nullptr, cursors, F2, cm, rid_in, rid_out, nullptr, nullptr, nullptr);
+        keys, n, bs_sub, 0, ntiles, nullptr, cursors, F2, cm, rid_in, rid_out, nullptr, nullptr, nullptr, nullptr,
+        nullptr);
   }
   MDJ_LAUNCH_CHECK();
   return MDJ_OK;
@@ -1013,7 +1020,7 @@ int stable_partition_scratch_t(const mdj_table *t, int32_t key_col, uint32_t P, 
     ColMove cm = make_move(t, key_col, src, out_cols);
     k_scatter<KeyT, false, false><<<ntiles, kNW * 32, scatter_smem_bytes(F), s>>>(
         (const KeyT *)src[key_col], n, bs, F, ntiles, hist, nullptr, 1, cm, nullptr, out_rid, nullptr, nullptr,
-        nullptr);
+        nullptr, nullptr, nullptr);
     MDJ_LAUNCH_CHECK();
   }
   k_u32_to_i64<<<(P + 1 + 255) / 256, 256, 0, s>>>(start, out_offsets, P + 1);
@@ -1050,18 +1057,21 @@ __global__ void __launch_bounds__(kHistThreads) k_seg_hist(const KeyT *__restric
                                                            const SegTile *__restrict__ tiles,
                                                            const uint32_t *__restrict__ seg_base,
                                                            const uint32_t *__restrict__ seg_nb,
+                                                           const uint32_t *__restrict__ seg_P,
+                                                           const uint32_t *__restrict__ seg_S,
                                                            uint32_t *__restrict__ totals) {
   extern __shared__ uint32_t cnt[];
   const SegTile td = tiles[blockIdx.x];
-  const uint32_t S = seg_nb[td.seg], B = seg_base[td.seg];
-  for (uint32_t b = threadIdx.x; b < S; b += blockDim.x) cnt[b] = 0;
+  const uint32_t NB = seg_nb[td.seg], B = seg_base[td.seg], S = seg_S[td.seg];
+  const BucketSpec sp = make_spec_dev(seg_P[td.seg]);
+  for (uint32_t b = threadIdx.x; b < NB; b += blockDim.x) cnt[b] = 0;
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < td.rows; i += blockDim.x) {
     const uint64_t h = fmix64(key_bits(keys[td.row0 + i]));
-    atomicAdd(&cnt[__umulhi((uint32_t)(h >> 32), S)], 1u);
+    atomicAdd(&cnt[mod_p(h, sp) * S + __umulhi((uint32_t)(h >> 32), S)], 1u);
   }
   __syncthreads();
-  for (uint32_t b = threadIdx.x; b < S; b += blockDim.x)
+  for (uint32_t b = threadIdx.x; b < NB; b += blockDim.x)
     if (cnt[b]) atomicAdd(&totals[B + b], cnt[b]);
 }
 
@@ -1077,7 +1087,8 @@ T *upload(Workspace &ws, const std::vector<T> &v) {
 
 template <typename KeyT>
 int seg_partition_t(Workspace &ws, const mdj_table *t, int32_t key_col, const uint64_t *seg_off, uint32_t nseg,
-                    const uint32_t *seg_base, const uint32_t *seg_nb, uint32_t nb, Side *out) {
+                    const uint32_t *seg_base, const uint32_t *seg_nb, const uint32_t *seg_P, uint32_t nb,
+                    Side *out) {
   cudaStream_t s = ws.stream();
   const uint32_t n = (uint32_t)t->nrows;
   const void *src[MDJ_MAX_COLS];
@@ -1103,18 +1114,21 @@ int seg_partition_t(Workspace &ws, const mdj_table *t, int32_t key_col, const ui
     for (uint32_t i = 0; i < nseg; i++)
       for (uint64_t r = seg_off[i]; r < seg_off[i + 1]; r += kTile)
         tiles.push_back(SegTile{(uint32_t)r, (uint32_t)std::min<uint64_t>(kTile, seg_off[i + 1] - r), i});
-    std::vector<uint32_t> hb(seg_base, seg_base + nseg), hs(seg_nb, seg_nb + nseg);
+    std::vector<uint32_t> hb(seg_base, seg_base + nseg), hs(seg_nb, seg_nb + nseg), hp(seg_P, seg_P + nseg),
+        hS(nseg);
+    for (uint32_t i = 0; i < nseg; i++) hS[i] = seg_nb[i] / seg_P[i];
     SegTile *dt = upload(ws, tiles);
-    uint32_t *db = upload(ws, hb), *ds = upload(ws, hs);
+    uint32_t *db = upload(ws, hb), *ds = upload(ws, hs), *dp = upload(ws, hp), *dS = upload(ws, hS);
     off = (uint32_t *)ws.get((size_t)(nb + 1) * 4);
     uint32_t *cur = (uint32_t *)ws.get((size_t)(nb + 1) * 4);
-    if (!dt || !db || !ds || !off || !cur) return MDJ_ERR_OOM;
+    if (!dt || !db || !ds || !dp || !dS || !off || !cur) return MDJ_ERR_OOM;
     MDJ_CUDA_TRY(cudaMemsetAsync(off, 0, (size_t)(nb + 1) * 4, s));
     uint32_t smax = 1;
     for (uint32_t i = 0; i < nseg; i++) smax = std::max(smax, seg_nb[i]);
     if (!tiles.empty()) {
       TraceScope tr("seg_hist", s);
-      k_seg_hist<KeyT><<<(unsigned)tiles.size(), kHistThreads, smax * 4, s>>>((const KeyT *)key, dt, db, ds, off);
+      k_seg_hist<KeyT><<<(unsigned)tiles.size(), kHistThreads, smax * 4, s>>>((const KeyT *)key, dt, db, ds, dp, dS,
+                                                                            off);
     }
     MDJ_LAUNCH_CHECK();
     MDJ_TRY(exclusive_scan_u32(ws, off, off, nb + 1));
@@ -1125,7 +1139,7 @@ int seg_partition_t(Workspace &ws, const mdj_table *t, int32_t key_col, const ui
       TraceScope tr("seg_scatter", s);
       k_scatter<KeyT, true, true><<<(unsigned)tiles.size(), kNW * 32, scatter_smem_bytes(kPass2SpanMax), s>>>(
           (const KeyT *)key, n, make_spec(1, 1, 1), 0, (uint32_t)tiles.size(), nullptr, cur, 1, cm, nullptr,
-          fin.rid, dt, db, ds);
+          fin.rid, dt, db, ds, dp, dS);
     }
     MDJ_LAUNCH_CHECK();
     key = fin.cols[key_col];
@@ -1151,11 +1165,11 @@ int seg_partition_t(Workspace &ws, const mdj_table *t, int32_t key_col, const ui
 }  // namespace
 
 int partition_side_segmented(Workspace &ws, const mdj_table *t, int32_t key_col, const uint64_t *seg_off,
-                             uint32_t nseg, const uint32_t *seg_base, const uint32_t *seg_nb, uint32_t nbuckets,
-                             Side *out) {
+                             uint32_t nseg, const uint32_t *seg_base, const uint32_t *seg_nb, const uint32_t *seg_P,
+                             uint32_t nbuckets, Side *out) {
   if (t->cols[key_col].dtype == MDJ_I64)
-    return seg_partition_t<int64_t>(ws, t, key_col, seg_off, nseg, seg_base, seg_nb, nbuckets, out);
-  return seg_partition_t<int32_t>(ws, t, key_col, seg_off, nseg, seg_base, seg_nb, nbuckets, out);
+    return seg_partition_t<int64_t>(ws, t, key_col, seg_off, nseg, seg_base, seg_nb, seg_P, nbuckets, out);
+  return seg_partition_t<int32_t>(ws, t, key_col, seg_off, nseg, seg_base, seg_nb, seg_P, nbuckets, out);
 }
 
 }  // namespace mdj

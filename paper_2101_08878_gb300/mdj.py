@@ -35,6 +35,7 @@ _MDJ_TO_TORCH = {v: k for k, v in _TORCH_TO_MDJ.items()}
 
 EXPORTED = [
     "mdj_partition", "mdj_partition_noalloc", "mdj_join", "mdj_merge", "mdj_count_checksum", "mdj_join_batch",
+    "mdj_merge_batch",
     "mdj_result_release",
     "mdj_status_string", "mdj_last_error", "mdj_version", "mdj_profile_enable", "mdj_profile_reset",
     "mdj_profile_collect", "mdj_profile_count", "mdj_profile_get",
@@ -111,6 +112,9 @@ def load(path: str = LIB_PATH):
         lib.mdj_join_batch.restype = ctypes.c_int
         lib.mdj_join_batch.argtypes = [P(MdjTable), i32, P(u64), P(MdjTable), i32, P(u64), i32, P(MdjTuning),
                                        P(MdjAllocator), vp, P(MdjResult), P(u64)]
+        lib.mdj_merge_batch.restype = ctypes.c_int
+        lib.mdj_merge_batch.argtypes = [P(MdjTable), i32, P(u64), P(MdjTable), i32, P(u64), i32, P(u32),
+                                        P(MdjTuning), P(MdjAllocator), vp, P(MdjResult), P(u64)]
         lib.mdj_result_release.restype = None
         lib.mdj_result_release.argtypes = [P(MdjResult), P(MdjAllocator), vp]
         lib.mdj_status_string.restype = ctypes.c_char_p
@@ -316,6 +320,36 @@ def mdj_join_batch(left_cols: Sequence[torch.Tensor], right_cols: Sequence[torch
                             po_c)
     _check(rc, "mdj_join_batch")
     return _adopt_result(res, alloc), [int(x) for x in po_c]
+
+
+def mdj_merge_batch(left_cols: Sequence[torch.Tensor], right_cols: Sequence[torch.Tensor], left_offsets,
+                    right_offsets, P, left_key: int = 0, right_key: int = 0, table_rows: int = 0,
+                    fill_pct: int = 0):
+    """Independent merges: request i = left rows [left_offsets[i], left_offsets[i+1])
+    and right rows [right_offsets[i], right_offsets[i+1]), shuffled into P[i]
+    partitions and joined (see mdj.h).  Returns (JoinResult, req_offsets)."""
+    lib = load()
+    dev = left_cols[0].device
+    lt, lk = _table(left_cols)
+    rt, rk = _table(right_cols)
+    lo = [int(x) for x in left_offsets]
+    ro = [int(x) for x in right_offsets]
+    pp = [int(x) for x in P]
+    if len(lo) != len(ro) or len(lo) < 2 or len(pp) != len(lo) - 1:
+        raise ValueError("offsets need nreq + 1 entries and P nreq entries")
+    nreq = len(lo) - 1
+    lo_c = (ctypes.c_uint64 * len(lo))(*lo)
+    ro_c = (ctypes.c_uint64 * len(ro))(*ro)
+    p_c = (ctypes.c_uint32 * nreq)(*pp)
+    out_c = (ctypes.c_uint64 * len(lo))()
+    tun = MdjTuning(table_rows, fill_pct)
+    alloc = TorchAllocator(dev)
+    res = MdjResult()
+    rc = lib.mdj_merge_batch(ctypes.byref(lt), left_key, lo_c, ctypes.byref(rt), right_key, ro_c, nreq, p_c,
+                             ctypes.byref(tun), ctypes.byref(alloc.struct), _stream_handle(dev), ctypes.byref(res),
+                             out_c)
+    _check(rc, "mdj_merge_batch")
+    return _adopt_result(res, alloc), [int(x) for x in out_c]
 
 
 def mdj_status_string(status: int) -> str:

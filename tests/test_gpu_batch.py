@@ -126,3 +126,55 @@ def test_batch_config3_full_size():
         assert po[i + 1] - po[i] == n_match
     for i in rng.choice(len(pairs), 6, replace=False):
         _check_pair(res_np, po, int(i), pairs[int(i)], lo, ro)
+
+
+def _run_merge_batch(pairs, P, **kw):
+    (lk, lp), (rk, rp), lo, ro = _concat(pairs)
+    mdj = _mdj()
+    res, po = mdj.mdj_merge_batch([torch.from_numpy(lk).to(DEV), torch.from_numpy(lp).to(DEV)],
+                                  [torch.from_numpy(rk).to(DEV), torch.from_numpy(rp).to(DEV)], lo, ro, P, **kw)
+    torch.cuda.synchronize()
+    res_np = {"key": _np(res.key), "left_row": _np(res.left_row).view(np.uint32),
+              "right_row": _np(res.right_row).view(np.uint32), "lpay": _np(res.left_cols[0]),
+              "rpay": _np(res.right_cols[0])}
+    return res, res_np, po, lo, ro
+
+
+def test_merge_batch_mixed_partition_counts_match_oracle():
+    pairs = _ragged_pairs(3)
+    P = [(1, 8, 32, 3, 1024)[i % 5] for i in range(len(pairs))]
+    res, res_np, po, lo, ro = _run_merge_batch(pairs, P)
+    for i, pair in enumerate(pairs):
+        _check_pair(res_np, po, i, pair, lo, ro)
+
+
+def test_merge_batch_larger_requests():
+    pairs = [datagen.match_fraction_tables(n, n, 0.3, seed=n) for n in (300_000, 1_500_000, 40_000)]
+    res, res_np, po, lo, ro = _run_merge_batch(pairs, [8, 32, 1])
+    for i, pair in enumerate(pairs):
+        assert po[i + 1] - po[i] == math.floor(0.3 * pair[1][0].size)
+        _check_pair(res_np, po, i, pair, lo, ro)
+
+
+def test_merge_batch_rejects_bad_P():
+    mdj = _mdj()
+    k = torch.arange(10, device=DEV)
+    for bad in ([0], [1025]):
+        with pytest.raises(mdj.MdjError):
+            mdj.mdj_merge_batch([k], [k], [0, 10], [0, 10], bad)
+
+
+def test_tuner_picks_and_caches(tmp_path):
+    from paper_2101_08878_gb300.tuner import BatchTuner
+    pairs = [datagen.match_fraction_tables(n, n, 0.5, seed=n) for n in (20_000, 80_000)]
+    (lk, lp), (rk, rp), lo, ro = _concat(pairs)
+    L = [torch.from_numpy(lk).to(DEV), torch.from_numpy(lp).to(DEV)]
+    R = [torch.from_numpy(rk).to(DEV), torch.from_numpy(rp).to(DEV)]
+    path = str(tmp_path / "tuner.json")
+    t = BatchTuner(path)
+    assert t.lookup(L[0].dtype, int(lo[-1]), 2) is None
+    best = t.choose(L, R, lo, ro)
+    assert best[0] in (2048, 4096, 8192) and best[1] in (60, 75, 85, 95)
+    again = BatchTuner(path)  # reloaded from the cache file
+    assert again.lookup(L[0].dtype, int(lo[-1]), 2) == best
+    assert again.choose(L, R, lo, ro, search=False) == best
