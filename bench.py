@@ -297,6 +297,9 @@ def run_gpu(args):
     }
     if args.batch_pairs > 0:
         line["batched"] = batched_section(args, dev)
+    if args.serve_requests > 0:
+        torch.cuda.empty_cache()
+        line["served"] = served_section(args, dev)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample)
     print(json.dumps(line), flush=True)
@@ -357,6 +360,72 @@ def batched_section(args, dev):
                         "tuning": {"table_rows": tr, "fill_pct": fp}},
             "plain_per_pair": {"value": rows / (ms_p / 1e3), "unit": UNIT, "ms_per_batch": round(ms_p, 3)},
             "speedup": round(ms_p / ms_b, 3)}
+
+
+def served_section(args, dev):
+    """Config 4: Poisson arrivals of merge requests (P in {1, 8, 32}, n_L, n_R
+    log-uniform in [1e4, 2e7], int32/int64 keys and float32/float64 payloads
+    50/50, match fraction 0.3) over a device-resident pool of tables, served
+    by MergeServer with continuous batching versus the plain per-request path
+    (one slot, no batching), at 0.5x, 1x and 2x the plain path's capacity."""
+    import asyncio
+    import torch
+    from paper_2101_08878_gb300.server import MergeServer, latency_stats, run_poisson
+
+    rng = np.random.default_rng(4)
+    pool, pool_out = [], []
+    for i in range(args.serve_pool):
+        nl = int(datagen.log_uniform_sizes(rng, 1, 10_000, 20_000_000)[0])
+        nr = int(datagen.log_uniform_sizes(rng, 1, 10_000, 20_000_000)[0])
+        kd = np.int32 if rng.random() < 0.5 else np.int64
+        pd = np.float32 if rng.random() < 0.5 else np.float64
+        (lk, lp), (rk, rp) = datagen.match_fraction_tables(nl, nr, FRAC, seed=4000 + i, key_dtype=kd, pay_dtype=pd)
+        P = int(rng.choice([1, 8, 32]))
+        pool_out.append(int(np.floor(FRAC * nr)))
+        pool.append(([torch.from_numpy(lk).to(dev), torch.from_numpy(lp).to(dev)],
+                     [torch.from_numpy(rk).to(dev), torch.from_numpy(rp).to(dev)], P))
+    picks = rng.integers(0, len(pool), args.serve_requests)
+    work = [pool[int(i)] for i in picks]
+    rows = [int(w[0][0].numel() + w[1][0].numel()) for w in work]
+    # match fraction 0.3 of the smaller side: the closed-form output row count
+    expect_rows = sum(pool_out[int(i)] for i in picks)
+
+    out_rows = []
+
+    def consume(req):
+        # the client reads its result and lets it go, as a caller of a server
+        # would; keeping thousands of results would fill the device
+        if req.result is not None:
+            out_rows.append(req.result.nrows)
+            req.result = None
+
+    def run(rate, batching, slots):
+        server = MergeServer(dev, slots=slots, batching=batching)
+        arrivals = np.cumsum(np.random.default_rng(44).exponential(1.0 / rate, len(work)))
+        out_rows.clear()
+        reqs, wall = asyncio.run(asyncio.wait_for(run_poisson(server, work, arrivals, consume), 300))
+        bad = [r.error for r in reqs if r.error is not None]
+        if bad:
+            raise RuntimeError(f"served requests failed: {bad[0]}")
+        if sum(out_rows) != expect_rows:
+            raise RuntimeError(f"served output rows {sum(out_rows)} != {expect_rows}")
+        st = latency_stats(reqs)
+        st["rows_per_s"] = sum(rows) / wall
+        st["wall_s"] = round(wall, 3)
+        st["mean_batch"] = round(float(np.mean(server.group_sizes)), 2)
+        return st
+
+    # capacity of the plain per-request path: everything queued at once
+    cap = run(1e9, False, 1)
+    cap_rps = len(work) / cap["wall_s"]
+    out = {"workload": f"{len(work)} requests drawn from {len(pool)} device-resident table pairs; P in {{1,8,32}}, "
+                       f"n_L, n_R log-uniform [1e4, 2e7], int32/int64 keys, float32/float64 payloads, match 0.3",
+           "plain_capacity_requests_per_s": round(cap_rps, 2), "rates": []}
+    for mult in (0.5, 1.0, 2.0):
+        rate = mult * cap_rps
+        out["rates"].append({"x_plain_capacity": mult, "requests_per_s": round(rate, 2),
+                             "served": run(rate, True, 2), "plain": run(rate, False, 1)})
+    return out
 
 
 def measured_traffic(kernel: str):
@@ -424,6 +493,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-pairs", type=int, default=256,
                     help="pairs of the batched-vs-plain section (0 skips it)")
+    ap.add_argument("--serve-requests", type=int, default=600,
+                    help="requests of the served section (0 skips it)")
+    ap.add_argument("--serve-pool", type=int, default=32, help="distinct table pairs the requests draw from")
     ap.add_argument("--rows", type=int, default=None,
                     help="rows per side (default 100M); smaller values are for profiling captures only")
     args = ap.parse_args()

@@ -133,7 +133,10 @@ class MergeServer:
         if self.memory_budget is not None:
             return self.memory_budget
         free, _total = torch.cuda.mem_get_info(self.device)
-        return max(free - self.memory_reserve, 0)
+        # blocks torch has cached but not handed out are free to the merge too
+        # (its allocations go through torch's allocator)
+        cached = torch.cuda.memory_reserved(self.device) - torch.cuda.memory_allocated(self.device)
+        return max(free + max(cached, 0) - self.memory_reserve, 0)
 
     def _dispatch(self, loop, inflight):
         while self.free_slots > 0 and self.pending:
@@ -153,6 +156,13 @@ class MergeServer:
                 rows += req.rows
                 need += fp
             if not group:
+                if self.reserved == 0 and self.free_slots == self.slots:
+                    # nothing runs that could free memory: the oldest request
+                    # would wait forever, so it fails instead
+                    self._complete(self.pending.popleft(),
+                                   error=MemoryError("request does not fit the device memory left free"))
+                    self.rejected += 1
+                    continue
                 return  # memory frees up when running work completes
             for req in group:
                 self.pending.remove(req)
@@ -237,9 +247,11 @@ def latency_stats(reqs: List[Request]) -> dict:
             "n": len(lat)}
 
 
-async def run_poisson(server: MergeServer, workload, arrivals):
+async def run_poisson(server: MergeServer, workload, arrivals, consume=None):
     """Submit workload[i] (left, right, P) at time arrivals[i] (seconds from
-    start); returns (requests, wall seconds)."""
+    start); returns (requests, wall seconds).  `consume(req)`, if given, is
+    called as each request finishes (a client reading its result; it may drop
+    req.result so the device memory is released)."""
     stop = asyncio.Event()
     sched = asyncio.ensure_future(server.serve(stop))
     t0 = time.perf_counter()
@@ -249,7 +261,10 @@ async def run_poisson(server: MergeServer, workload, arrivals):
         if delay > 0:
             await asyncio.sleep(delay)
         left, right, P = workload[i]
-        return await server.submit(left, right, P)
+        req = await server.submit(left, right, P)
+        if consume is not None:
+            consume(req)
+        return req
 
     reqs = await asyncio.gather(*[one(i) for i in range(len(workload))])
     wall = time.perf_counter() - t0

@@ -19,7 +19,11 @@ def fake_gpu(monkeypatch):
     monkeypatch.setattr(torch.cuda, "Stream", lambda dev=None: types.SimpleNamespace(synchronize=lambda: None))
     monkeypatch.setattr(torch.cuda, "stream", lambda s: contextlib.nullcontext())
     monkeypatch.setattr(torch.cuda, "device", lambda d: contextlib.nullcontext())
-    monkeypatch.setattr(torch.cuda, "mem_get_info", lambda d=None: (64 << 30, 128 << 30))
+    calls["free"] = 64 << 30
+    monkeypatch.setattr(torch.cuda, "mem_get_info", lambda d=None: (calls["free"], 128 << 30))
+    calls["cached"] = 2 << 30
+    monkeypatch.setattr(torch.cuda, "memory_reserved", lambda d=None: (1 << 30) + calls["cached"])
+    monkeypatch.setattr(torch.cuda, "memory_allocated", lambda d=None: 1 << 30)
 
     def merge(l, r, P):
         time.sleep(0.002)
@@ -89,6 +93,45 @@ def test_oversized_request_is_rejected(fake_gpu):
     server = MergeServer(torch.device("cpu"), slots=1, memory_budget=1 << 10)
     reqs, _ = _serve(server, _work(2, 3), [0.0, 0.0])
     assert all(isinstance(r.error, MemoryError) for r in reqs) and server.rejected == 2
+
+
+def test_budget_counts_torch_cached_blocks(fake_gpu):
+    from paper_2101_08878_gb300.server import MergeServer
+    server = MergeServer(torch.device("cpu"), slots=1, memory_reserve=8 << 30)
+    assert server._budget() == (64 << 30) + (2 << 30) - (8 << 30)
+
+
+def test_no_wait_forever_when_memory_is_held_elsewhere(fake_gpu):
+    # free memory drops below every request's footprint while the queue still
+    # holds work and nothing runs (results kept by the client): the queued
+    # requests fail with MemoryError instead of waiting for memory that no
+    # running merge will release
+    from paper_2101_08878_gb300 import mdj
+    from paper_2101_08878_gb300.server import MergeServer
+    real = mdj.mdj_merge
+
+    def hog(l, r, P):
+        fake_gpu["free"] = fake_gpu["cached"] = 0
+        return real(l, r, P)
+    mdj.mdj_merge = hog
+    server = MergeServer(torch.device("cpu"), slots=1, batching=False, memory_reserve=0)
+    reqs, _ = _serve(server, _work(4, 5), [0.0] * 4)
+    assert reqs[0].error is None and reqs[0].result is not None
+    assert all(isinstance(r.error, MemoryError) for r in reqs[1:]) and server.rejected == 3
+
+
+def test_consumer_sees_every_request_once(fake_gpu):
+    from paper_2101_08878_gb300.server import MergeServer, run_poisson
+    seen = []
+
+    def consume(req):
+        seen.append(req.result.nrows)
+        req.result = None  # a client that drops its result after reading it
+    work = _work(12, 6)
+    server = MergeServer(torch.device("cpu"), slots=2)
+    reqs, _ = asyncio.run(asyncio.wait_for(run_poisson(server, work, np.zeros(len(work)), consume), 30))
+    assert sorted(seen) == sorted(min(l[0].numel(), r[0].numel()) for l, r, _ in work)
+    assert all(r.result is None and r.error is None for r in reqs)
 
 
 def test_failure_is_confined_to_its_group(fake_gpu):
