@@ -253,6 +253,7 @@ struct Plan {
   uint32_t nbuckets = 1; // final buckets (P * S)
   bool lsd = false;      // P > kMaxFanout: two stable digit passes on p
   bool partition = true; // false: no partitioning at all (P = 1, small build side)
+  bool stable = false;   // stable passes (rows keep input order in a bucket)
   uint32_t cap = 4096;   // build rows per shared-memory table
 };
 

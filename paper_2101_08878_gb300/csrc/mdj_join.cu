@@ -879,7 +879,9 @@ int merge_impl(const mdj_table *left, int32_t lk, const mdj_table *right, int32_
   if (out) memset(out, 0, sizeof *out);
 
   Workspace ws(alloc, (cudaStream_t)stream);
-  const Plan plan = make_plan(left->nrows, P, cap_from_env(), P > 1);
+  Plan plan = make_plan(left->nrows, P, cap_from_env(), P > 1);
+  // ordered output is deterministic only over stable partition passes
+  plan.stable = ordered_output() != 0;
   Side L, R;
   MDJ_TRY(partition_side(ws, left, lk, plan, &L));
   MDJ_TRY(partition_side(ws, right, rk, plan, &R));

@@ -545,6 +545,224 @@ __global__ void __launch_bounds__(kPT, 2)
   }
 }
 
+// ------------------------------------------------- unstable shuffle (merge)
+//
+// The merge needs every row in its sub-bucket, not the input order inside a
+// bucket, so its shuffle drops stability (the public partition keeps it):
+//
+//   k_tot      rows per final sub-bucket (shared counters, flushed with one
+//              global add per counter); the next chunk's keys load while the
+//              current chunk is counted
+//   k_shuffle  one tile of 4096 rows: every column of a row is loaded at the
+//              start, a row's rank in its bucket is a shared-memory atomic,
+//              each (tile, bucket) run is reserved with one global atomicAdd
+//              on the bucket's cursor, and the columns are staged in bucket
+//              order and leave as runs; three block barriers per tile.
+//              PASS2: rows already grouped by pass-1 bucket (sub-bucket / F2)
+//              are split into their sub-buckets, as in k_scatter's RESERVE.
+// A pass-1 bucket's cursor starts at the offset of its first sub-bucket
+// (pass-1 bucket b = sub-bucket / F2, see BucketSpec), so one count of the
+// final sub-buckets serves both passes.
+
+constexpr int kTotThreads = 1024;
+constexpr int kTotU = 8;                        // keys per thread per chunk
+constexpr int kFT = 512;                        // threads of k_shuffle
+constexpr uint32_t kFTile = (uint32_t)kFT * kRPL;  // 4096 rows
+constexpr uint32_t kFSpan = 1024;               // local buckets of one tile
+
+size_t shuffle_smem_bytes() { return (size_t)kFTile * (8 + 8 + 4 + 4) + (size_t)kFSpan * 8 + 40 * 4; }
+
+template <typename KeyT>
+__device__ __forceinline__ void tot_load(const KeyT *__restrict__ keys, uint64_t base, uint32_t n, KeyT (&v)[kTotU]) {
+#pragma unroll
+  for (int u = 0; u < kTotU; u++) {
+    const uint64_t r = base + (uint64_t)u * kTotThreads + threadIdx.x;
+    v[u] = r < n ? keys[r] : KeyT(0);
+  }
+}
+
+template <typename KeyT>
+__global__ void __launch_bounds__(kTotThreads) k_tot(const KeyT *__restrict__ keys, uint32_t n, BucketSpec bs,
+                                                     uint32_t nsub, uint32_t *__restrict__ tot) {
+  extern __shared__ uint32_t cnt[];
+  for (uint32_t i = threadIdx.x; i < nsub; i += kTotThreads) cnt[i] = 0;
+  __syncthreads();
+  const uint64_t chunk = (uint64_t)kTotThreads * kTotU, stride = chunk * gridDim.x;
+  uint64_t base = chunk * blockIdx.x;
+  KeyT cur[kTotU], nxt[kTotU];
+  tot_load<KeyT>(keys, base, n, cur);
+  for (; base < n; base += stride) {
+    tot_load<KeyT>(keys, base + stride, n, nxt);
+#pragma unroll
+    for (int u = 0; u < kTotU; u++) {
+      const uint64_t r = base + (uint64_t)u * kTotThreads + threadIdx.x;
+      if (r < n) atomicAdd(&cnt[sub_bucket_of(fmix64(key_bits(cur[u])), bs)], 1u);
+      cur[u] = nxt[u];
+    }
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < nsub; i += kTotThreads)
+    if (cnt[i]) atomicAdd(&tot[i], cnt[i]);
+}
+
+// cur[b] = off[b * F2]: the first row of pass-1 bucket b
+__global__ void k_pass1_cursors(const uint32_t *__restrict__ off, uint32_t F1, uint32_t F2,
+                                uint32_t *__restrict__ cur) {
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < F1) cur[b] = off[(size_t)b * F2];
+}
+
+// scatter_direct for k_shuffle, reading the keys again from memory so that
+// the caller's key registers need no addressable copy.
+template <typename KeyT>
+__device__ __noinline__ void shuffle_direct(const KeyT *__restrict__ keys, uint32_t wrow0, uint32_t rend,
+                                            const BucketSpec &bs, uint32_t *__restrict__ cursors, const ColMove &cm,
+                                            const uint32_t *__restrict__ rid_in, uint32_t *__restrict__ rid_out) {
+  KeyT kv[kRPL];
+#pragma unroll
+  for (int c = 0; c < kRPL; c++) {
+    const uint32_t r = wrow0 + c * 32 + (threadIdx.x & 31);
+    kv[c] = r < rend ? keys[r] : KeyT(0);
+  }
+  scatter_direct<KeyT>(kv, wrow0, rend, bs, cursors, cm, rid_in, rid_out);
+}
+
+// Rows of tile blockIdx.x: warp w holds rows row0 + w*256 + c*32 + lane
+// (c < kRPL), the layout scatter_direct uses.  `reg_col` is the non-key column
+// carried in registers from the start (-1: none); the other non-key columns
+// are loaded and staged one at a time after the first write-out.
+template <typename KeyT, bool PASS2>
+__global__ void __launch_bounds__(kFT, 2)
+    k_shuffle(const KeyT *__restrict__ keys, uint32_t n, BucketSpec bs, uint32_t F, uint32_t F2,
+              uint32_t *__restrict__ cursors, ColMove cm, int reg_col, const uint32_t *__restrict__ rid_in,
+              uint32_t *__restrict__ rid_out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  KeyT *sk = (KeyT *)smem;
+  uint64_t *sp = (uint64_t *)(smem + (size_t)kFTile * 8);
+  uint32_t *sr = (uint32_t *)(smem + (size_t)kFTile * 16);
+  uint32_t *dstmap = sr + kFTile;
+  uint32_t *lstart = dstmap + kFTile;
+  uint32_t *gbase = lstart + kFSpan;
+  uint32_t *scratch = gbase + kFSpan;
+
+  const uint32_t row0 = blockIdx.x * kFTile;
+  const uint32_t rows = min(kFTile, n - row0);
+  const uint32_t rend = row0 + rows;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t wrow0 = row0 + warp * 32 * kRPL;
+
+  KeyT kv[kRPL];
+  uint64_t pv[kRPL];
+  uint32_t rv[kRPL];
+  const int pw = reg_col >= 0 ? cm.width[reg_col] : 0;
+#pragma unroll
+  for (int c = 0; c < kRPL; c++) {
+    const uint32_t r = wrow0 + c * 32 + lane;
+    const bool ok = r < rend;
+    kv[c] = ok ? keys[r] : KeyT(0);
+    pv[c] = 0;
+    if (ok && pw == 8) pv[c] = ((const uint64_t *)cm.src[reg_col])[r];
+    if (ok && pw == 4) pv[c] = ((const uint32_t *)cm.src[reg_col])[r];
+    rv[c] = rid_in ? (ok ? rid_in[r] : 0u) : r;
+  }
+
+  uint32_t lb0 = 0, Floc = F;
+  if (PASS2) {
+    const uint32_t b1f = sub_bucket_of(fmix64(key_bits(keys[row0])), bs) / F2;
+    const uint32_t b1l = sub_bucket_of(fmix64(key_bits(keys[rend - 1])), bs) / F2;
+    lb0 = b1f * F2;
+    Floc = (b1l - b1f + 1) * F2;
+    if (Floc > kFSpan) {
+      shuffle_direct<KeyT>(keys, wrow0, rend, bs, cursors, cm, rid_in, rid_out);
+      return;
+    }
+  }
+
+  // 1. rank of each row in its bucket (order among equal buckets: arbitrary)
+  uint32_t *cnt = lstart;
+  for (uint32_t i = threadIdx.x; i < Floc; i += kFT) cnt[i] = 0;
+  __syncthreads();
+  uint32_t pk[kRPL];
+#pragma unroll
+  for (int c = 0; c < kRPL; c++) {
+    pk[c] = 0xFFFFFFFFu;
+    if (wrow0 + c * 32 + lane < rend) {
+      const uint64_t h = fmix64(key_bits(kv[c]));
+      const uint32_t b = (PASS2 ? sub_bucket_of(h, bs) : bucket_of(h, bs)) - lb0;
+      pk[c] = (b << 16) | atomicAdd(&cnt[b], 1u);
+    }
+  }
+  __syncthreads();
+
+  // 2. reserve every non-empty run (two buckets per thread) and scan the counts
+  const uint32_t b0 = 2 * threadIdx.x, b1 = b0 + 1;
+  const uint32_t c0 = b0 < Floc ? cnt[b0] : 0u, c1 = b1 < Floc ? cnt[b1] : 0u;
+  const uint32_t g0 = c0 ? atomicAdd(&cursors[lb0 + b0], c0) : 0u;
+  const uint32_t g1 = c1 ? atomicAdd(&cursors[lb0 + b1], c1) : 0u;
+  uint32_t total;
+  const uint32_t ex = block_exclusive_scan<uint32_t>(c0 + c1, scratch, &total);
+  if (b0 < Floc) {
+    lstart[b0] = ex;
+    gbase[b0] = g0;
+  }
+  if (b1 < Floc) {
+    lstart[b1] = ex + c0;
+    gbase[b1] = g1;
+  }
+  __syncthreads();
+
+  // 3. stage every carried column in bucket order, with each row's destination
+  uint32_t lp[kRPL];
+#pragma unroll
+  for (int c = 0; c < kRPL; c++) {
+    lp[c] = 0xFFFFFFFFu;
+    if (pk[c] != 0xFFFFFFFFu) {
+      const uint32_t b = pk[c] >> 16, rank = pk[c] & 0xFFFFu;
+      lp[c] = lstart[b] + rank;
+      dstmap[lp[c]] = gbase[b] + rank;
+      sk[lp[c]] = kv[c];
+      sp[lp[c]] = pv[c];
+      sr[lp[c]] = rv[c];
+    }
+  }
+  __syncthreads();
+
+  // 4. write-out: consecutive threads store consecutive rows of one run
+  KeyT *kdst = (KeyT *)cm.dst[cm.key_index];
+  for (uint32_t i = threadIdx.x; i < rows; i += kFT) {
+    const uint32_t d = dstmap[i];
+    kdst[d] = sk[i];
+    if (pw == 8) ((uint64_t *)cm.dst[reg_col])[d] = sp[i];
+    if (pw == 4) ((uint32_t *)cm.dst[reg_col])[d] = (uint32_t)sp[i];
+    if (rid_out) rid_out[d] = sr[i];
+  }
+
+  // 5. any further column, one at a time through the payload stage
+  for (int j = 0; j < cm.n; j++) {
+    if (j == cm.key_index || j == reg_col) continue;
+    const int w = cm.width[j];
+    uint64_t v[kRPL];
+#pragma unroll
+    for (int c = 0; c < kRPL; c++) {
+      const uint32_t r = wrow0 + c * 32 + lane;
+      v[c] = 0;
+      if (r < rend) v[c] = w == 8 ? ((const uint64_t *)cm.src[j])[r] : ((const uint32_t *)cm.src[j])[r];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < kRPL; c++)
+      if (lp[c] != 0xFFFFFFFFu) sp[lp[c]] = v[c];
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < rows; i += kFT) {
+      const uint32_t d = dstmap[i];
+      if (w == 8)
+        ((uint64_t *)cm.dst[j])[d] = sp[i];
+      else
+        ((uint32_t *)cm.dst[j])[d] = (uint32_t)sp[i];
+    }
+  }
+}
+
 // ------------------------------------------------------------ small kernels
 
 __global__ void k_bucket_starts(const uint32_t *__restrict__ hist, uint32_t F, uint32_t ntiles, uint32_t n,
@@ -789,6 +1007,111 @@ ColMove make_move(const mdj_table *t, int32_t key_col, const void *const *src, v
   return cm;
 }
 
+// ------------------------------------------------ unstable shuffle (host)
+
+// MDJ_STABLE_SHUFFLE=1 makes the merge use the stable passes (for comparison).
+bool fast_shuffle_enabled() {
+  const char *e = getenv("MDJ_STABLE_SHUFFLE");
+  return !(e && e[0] == '1');
+}
+
+template <typename KeyT>
+int set_shuffle_attrs() {
+  static bool done = false;
+  if (done) return MDJ_OK;
+  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_shuffle<KeyT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)shuffle_smem_bytes()));
+  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_shuffle<KeyT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)shuffle_smem_bytes()));
+  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_tot<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(kMaxSubBuckets * 4)));
+  done = true;
+  return MDJ_OK;
+}
+
+// Rows per sub-bucket of spec `bs` (nsub = P * S) into tot[0..nsub), which
+// the call zeroes first.
+template <typename KeyT>
+int count_sub_buckets(Workspace &ws, const KeyT *keys, uint32_t n, const BucketSpec &bs, uint32_t nsub,
+                      uint32_t *tot) {
+  cudaStream_t s = ws.stream();
+  MDJ_CUDA_TRY(cudaMemsetAsync(tot, 0, (size_t)nsub * 4, s));
+  if (n == 0) return MDJ_OK;
+  const size_t smem = (size_t)nsub * 4;
+  int per_sm = 0;
+  MDJ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tot<KeyT>, kTotThreads, smem));
+  if (per_sm < 1) per_sm = 1;
+  const uint64_t chunks = ((uint64_t)n + (uint64_t)kTotThreads * kTotU - 1) / ((uint64_t)kTotThreads * kTotU);
+  const uint64_t full = (uint64_t)num_sms() * per_sm;
+  const unsigned grid = (unsigned)(chunks < full ? chunks : full);
+  {
+    TraceScope tr("hist", s);
+    k_tot<KeyT><<<grid, kTotThreads, smem, s>>>(keys, n, bs, nsub, tot);
+  }
+  MDJ_LAUNCH_CHECK();
+  return MDJ_OK;
+}
+
+// One unstable shuffle pass (see k_shuffle) of n rows with run cursors `cur`.
+template <typename KeyT, bool PASS2>
+int shuffle_pass(Workspace &ws, const KeyT *keys, uint32_t n, const BucketSpec &bs, uint32_t F, uint32_t F2,
+                 uint32_t *cur, const ColMove &cm, const uint32_t *rid_in, uint32_t *rid_out) {
+  const uint32_t ntiles = (n + kFTile - 1) / kFTile;
+  if (ntiles == 0) return MDJ_OK;
+  int reg_col = -1;
+  for (int j = 0; j < cm.n && reg_col < 0; j++)
+    if (j != cm.key_index) reg_col = j;
+  TraceScope tr(PASS2 ? "scatter_reserve" : "scatter_stable", ws.stream());
+  k_shuffle<KeyT, PASS2><<<ntiles, kFT, shuffle_smem_bytes(), ws.stream()>>>(keys, n, bs, F, F2, cur, cm, reg_col,
+                                                                            rid_in, rid_out);
+  MDJ_LAUNCH_CHECK();
+  return MDJ_OK;
+}
+
+// The merge's partition of one side with the unstable passes: count the
+// final sub-buckets, scan them into `off`, then one pass (F2 == 1) or two.
+template <typename KeyT>
+int shuffle_side_t(Workspace &ws, const mdj_table *t, int32_t key_col, const Plan &plan, uint32_t *off,
+                   TableBufs *fin) {
+  cudaStream_t s = ws.stream();
+  MDJ_TRY(set_shuffle_attrs<KeyT>());
+  const uint32_t n = (uint32_t)t->nrows;
+  const uint32_t nsub = plan.nbuckets;
+  const void *src[MDJ_MAX_COLS];
+  for (int j = 0; j < t->ncols; j++) src[j] = t->cols[j].data;
+  const KeyT *keys = (const KeyT *)src[key_col];
+  const BucketSpec sub = make_spec(plan.P, plan.S, 1);
+
+  MDJ_TRY(count_sub_buckets<KeyT>(ws, keys, n, sub, nsub, off));
+  MDJ_TRY(exclusive_scan_u32(ws, off, off, (size_t)nsub + 1));
+  uint32_t *cur = (uint32_t *)ws.get((size_t)(nsub + 1) * 4);
+  if (!cur) return MDJ_ERR_OOM;
+  MDJ_TRY(alloc_table_bufs(ws, t, fin, true));
+  if (plan.F2 == 1) {
+    MDJ_CUDA_TRY(cudaMemcpyAsync(cur, off, (size_t)nsub * 4, cudaMemcpyDeviceToDevice, s));
+    ColMove cm = make_move(t, key_col, src, fin->cols);
+    MDJ_TRY((shuffle_pass<KeyT, false>(ws, keys, n, sub, nsub, 1, cur, cm, nullptr, fin->rid)));
+  } else {
+    TableBufs p1;
+    MDJ_TRY(alloc_table_bufs(ws, t, &p1, true));
+    {
+      TraceScope tr("pass1_cursors", s);
+      k_pass1_cursors<<<(plan.F1 + 255) / 256, 256, 0, s>>>(off, plan.F1, plan.F2, cur);
+    }
+    MDJ_LAUNCH_CHECK();
+    ColMove cm1 = make_move(t, key_col, src, p1.cols);
+    MDJ_TRY((shuffle_pass<KeyT, false>(ws, keys, n, make_spec(plan.P, plan.S, plan.F2), plan.F1, plan.F2, cur, cm1,
+                                       nullptr, p1.rid)));
+    MDJ_CUDA_TRY(cudaMemcpyAsync(cur, off, (size_t)nsub * 4, cudaMemcpyDeviceToDevice, s));
+    ColMove cm2 = make_move(t, key_col, p1.cols, fin->cols);
+    MDJ_TRY((shuffle_pass<KeyT, true>(ws, (const KeyT *)p1.cols[key_col], n, sub, 0, plan.F2, cur, cm2, p1.rid,
+                                      fin->rid)));
+    release_table_bufs(ws, t, &p1);
+  }
+  ws.give_back(cur);
+  return MDJ_OK;
+}
+
 // Stable partition by p with P > kMaxFanout: two stable LSD digit passes
 // (p mod 1024, then p / 1024), which sort stably by p.  Writes into `dst`
 // buffers; `off` (device u32[P+1]) receives the partition offsets.
@@ -872,6 +1195,11 @@ int partition_side_t(Workspace &ws, const mdj_table *t, int32_t key_col, const P
     TraceScope tr("offsets_whole", s);
     k_two<<<1, 1, 0, s>>>(off, 0u, n);
     MDJ_LAUNCH_CHECK();
+  } else if (!plan.lsd && !plan.stable && fast_shuffle_enabled()) {
+    MDJ_TRY(shuffle_side_t<KeyT>(ws, t, key_col, plan, off, &fin));
+    key = fin.cols[key_col];
+    cols = fin.cols;
+    rid = fin.rid;
   } else if (plan.lsd) {
     MDJ_TRY(alloc_table_bufs(ws, t, &fin, true));
     MDJ_TRY(lsd_partition<KeyT>(ws, t, key_col, plan.P, fin.cols, fin.rid, off));

@@ -118,6 +118,14 @@ def test_two_level_plan():
     assert got["key"].size == math.floor(0.3 * 2_000_000)
 
 
+def test_two_level_plan_stable_passes(monkeypatch):
+    # the stable partition passes (MDJ_STABLE_SHUFFLE=1) give the same result
+    monkeypatch.setenv("MDJ_STABLE_SHUFFLE", "1")
+    (lk, lp), (rk, rp) = datagen.match_fraction_tables(4_000_000, 2_000_000, 0.3, seed=8)
+    got = _check([lk, lp], [rk, rp], 8)
+    assert got["key"].size == math.floor(0.3 * 2_000_000)
+
+
 def test_config0_plain_merge_P1():
     # plain inner merge, P = 1: 1M x 1M, unique left keys, match fraction 0.3
     (lk, lp), (rk, rp) = datagen.match_fraction_tables(1_000_000, 1_000_000, 0.3, seed=0)
