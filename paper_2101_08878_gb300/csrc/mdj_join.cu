@@ -347,104 +347,101 @@ __device__ uint64_t look_back(unsigned long long *state, uint32_t it, uint64_t t
 
 // ------------------------------------------------------------ fused write
 //
-// Two 512-thread blocks per SM, so one block's global-memory phases overlap
-// the other's shared-memory phases.  Per item: load its build keys into
-// shared memory and its probe keys into registers, build, probe, block-scan
-// the match counts, reserve the item's output range, write.  Probe rows with
-// exactly one match (the common case) are written cooperatively from a
-// shared-memory match list, so consecutive threads store consecutive output
-// rows; rows with several matches are expanded by their own thread.  The
-// next item's ticket and descriptor are fetched while the current one runs.
+// Two 512-thread blocks per SM.  Per item:
+//   1. the build chunk's keys, row ids and first payload column go to shared
+//      memory by asynchronous copies (cp.async) while the probe keys load
+//      into registers and the table heads are cleared;
+//   2. build: a chained table, heads[slot] -> row, nxt[row] -> row, one
+//      atomicExch per build row (no probing loop, no compare-and-swap);
+//   3. probe: walk the key's chain; first match and match count per row;
+//   4. the row ids and first payload of matching probe rows are loaded, so
+//      their latency overlaps the offset computation;
+//   5. offsets: rows with one match are ordered by (round j, warp, lane), so
+//      the matching lanes of one warp store consecutive output rows (ballot +
+//      popc); rows with several matches follow, each expanded by its thread;
+//      the item's range is reserved (atomicAdd) or looked back (ordered);
+//   6. write: build-side values from shared memory, probe-side from registers.
+// The next item's ticket and descriptor are fetched while the current one runs.
 
 constexpr int kWT = 512;                        // threads of the write block
 constexpr int kWPF = 8;                         // probe rows per thread
+constexpr int kWW = kWT / 32;                   // warps of the write block
 static_assert(kWPF * kWT == (int)kWriteChunk, "probe chunk = one round");
 
 template <typename KeyT>
 struct WriteLayout {
-  size_t keys, slots, nxt, list, total;
-  uint32_t tsz;  // slots of the largest table
+  size_t keys, rid, pay, heads, nxt, cnt1, total;
+  uint32_t tsz;  // chain heads of the largest table (>= cap: mean chain length <= 1)
   __host__ __device__ WriteLayout(uint32_t cap) {
     tsz = 32;
-    while (tsz < 2 * cap) tsz *= 2;
+    while (tsz < cap) tsz *= 2;
     keys = 0;
-    slots = align16((size_t)cap * sizeof(KeyT));
-    nxt = slots + (size_t)tsz * 4;
-    list = align16(nxt + (size_t)cap * 2);
-    total = list + (size_t)kWriteChunk * 4;
+    rid = align16((size_t)cap * sizeof(KeyT));
+    pay = align16(rid + (size_t)cap * 4);
+    heads = align16(pay + (size_t)cap * 8);
+    nxt = heads + (size_t)tsz * 4;
+    cnt1 = align16(nxt + (size_t)cap * 2);
+    total = cnt1 + (size_t)kWPF * kWW * 4;
   }
 };
 
-// Write-pass table: 32-bit fold of the key, one multiply for the slot and
-// one for the tag.  (The count pass keeps the 64-bit hash and counters.)
-__device__ __forceinline__ void slot_tag32(uint64_t kb, uint32_t logt, uint32_t &slot, uint32_t &tag) {
+// Chain-head slot of a key: 32-bit fold, one multiply, top logt bits.
+__device__ __forceinline__ uint32_t chain_slot(uint64_t kb, uint32_t logt) {
   const uint32_t f = (uint32_t)kb ^ (uint32_t)(kb >> 32);
-  slot = (f * 0x9E3779B1u) >> (32 - logt);
-  tag = (f * 0x85EBCA6Bu) >> 16;
+  return (f * 0x9E3779B1u) >> (32 - logt);
 }
 
-// Slots hold (tag16 << 16 | head + 1); one slot per distinct key; rows of a
-// key are chained through nxt[] (0 ends the chain).
-template <typename KeyT>
-__device__ __forceinline__ void build_chain_table(const KeyT *keys, uint32_t nl, uint32_t logt, uint32_t *slots,
-                                                  uint16_t *nxt) {
-  const uint32_t mask = (1u << logt) - 1;
-  for (uint32_t i = threadIdx.x; i < nl; i += blockDim.x) {
-    const KeyT k = keys[i];
-    uint32_t s, tag;
-    slot_tag32(key_bits(k), logt, s, tag);
-    const uint32_t w = (tag << 16) | (i + 1);
-    for (uint32_t probe = 0; probe <= mask; probe++) {
-      uint32_t cur = slots[s];
-      if (cur == 0) {
-        const uint32_t prev = atomicCAS(&slots[s], 0u, w);
-        if (prev == 0) {
-          nxt[i] = 0;
-          break;
-        }
-        cur = prev;
-      }
-      if ((cur >> 16) == tag && keys[(cur & 0xFFFFu) - 1] == k) {
-        const uint32_t prev = atomicExch(&slots[s], w);
-        nxt[i] = (uint16_t)(prev & 0xFFFFu);
-        break;
-      }
-      s = (s + 1) & mask;
-    }
-  }
+__device__ __forceinline__ void cp_async_4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(__cvta_generic_to_global(src))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(__cvta_generic_to_global(src))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
-// Chain head (row index + 1) of key k, 0 if absent.
-template <typename KeyT>
-__device__ __forceinline__ uint32_t find_head(const KeyT k, const KeyT *keys, const uint32_t *slots, uint32_t logt) {
-  const uint32_t mask = (1u << logt) - 1;
-  uint32_t s, tag;
-  slot_tag32(key_bits(k), logt, s, tag);
-  for (uint32_t probe = 0; probe <= mask; probe++) {
-    const uint32_t w = slots[s];
-    if (w == 0) return 0;
-    if ((w >> 16) == tag && keys[(w & 0xFFFFu) - 1] == k) return w & 0xFFFFu;
-    s = (s + 1) & mask;
-  }
-  return 0;
-}
-
-__device__ __forceinline__ void copy_cols_row(const JSide &L, const JSide &R, const JOut &out, uint64_t pos,
-                                              uint32_t lrow, uint32_t r) {
-  out.lrow[pos] = L.rid ? L.rid[lrow] : lrow;
-  out.rrow[pos] = R.rid ? R.rid[r] : r;
-  for (int cc = 0; cc < L.ncols; cc++) {
+// Non-key columns after the first of each side (gathered from global memory).
+__device__ __forceinline__ void copy_extra_cols(const JSide &L, const JSide &R, const JOut &out, uint64_t pos,
+                                                uint32_t lrow, uint32_t r) {
+  for (int cc = 1; cc < L.ncols; cc++) {
     if (L.width[cc] == 8)
       ((uint64_t *)out.lcols[cc])[pos] = ((const uint64_t *)L.cols[cc])[lrow];
     else
       ((uint32_t *)out.lcols[cc])[pos] = ((const uint32_t *)L.cols[cc])[lrow];
   }
-  for (int cc = 0; cc < R.ncols; cc++) {
+  for (int cc = 1; cc < R.ncols; cc++) {
     if (R.width[cc] == 8)
       ((uint64_t *)out.rcols[cc])[pos] = ((const uint64_t *)R.cols[cc])[r];
     else
       ((uint32_t *)out.rcols[cc])[pos] = ((const uint32_t *)R.cols[cc])[r];
   }
+}
+
+// One output row: build row li of the staged chunk, probe row r with row id
+// rr and first payload rp.
+template <typename KeyT>
+__device__ __forceinline__ void write_row(const JSide &L, const JSide &R, const JOut &out, uint64_t pos,
+                                          const KeyT *bkey, const uint32_t *brid, const uint64_t *bpay, uint32_t li,
+                                          uint32_t lbeg, uint32_t r, uint32_t rr, uint64_t rp) {
+  ((KeyT *)out.key)[pos] = bkey[li];
+  out.lrow[pos] = brid[li];
+  out.rrow[pos] = rr;
+  if (L.ncols > 0) {
+    if (L.width[0] == 8)
+      ((uint64_t *)out.lcols[0])[pos] = bpay[li];
+    else
+      ((uint32_t *)out.lcols[0])[pos] = (uint32_t)bpay[li];
+  }
+  if (R.ncols > 0) {
+    if (R.width[0] == 8)
+      ((uint64_t *)out.rcols[0])[pos] = rp;
+    else
+      ((uint32_t *)out.rcols[0])[pos] = (uint32_t)rp;
+  }
+  if (L.ncols > 1 || R.ncols > 1) copy_extra_cols(L, R, out, pos, lbeg + li, r);
 }
 
 template <typename KeyT, bool HAVE_OFFSETS>
@@ -454,19 +451,22 @@ __global__ void __launch_bounds__(kWT, 2)
                  uint64_t capacity, int *flags, int withhold_first, int ordered, JOut out) {
   extern __shared__ __align__(16) unsigned char smem[];
   const WriteLayout<KeyT> lay(cap);
-  KeyT *keys = (KeyT *)(smem + lay.keys);
-  uint32_t *slots = (uint32_t *)(smem + lay.slots);
+  KeyT *bkey = (KeyT *)(smem + lay.keys);
+  uint32_t *brid = (uint32_t *)(smem + lay.rid);
+  uint64_t *bpay = (uint64_t *)(smem + lay.pay);
+  uint32_t *heads = (uint32_t *)(smem + lay.heads);
   uint16_t *nxt = (uint16_t *)(smem + lay.nxt);
-  uint32_t *list = (uint32_t *)(smem + lay.list);
+  uint32_t *cnt1 = (uint32_t *)(smem + lay.cnt1);
   __shared__ Item s_item;
-  __shared__ uint32_t s_it;
+  __shared__ uint32_t s_it, s_single;
   __shared__ uint64_t s_base;
   __shared__ uint64_t scratch64[33];
 
   const KeyT *__restrict__ Lkey = (const KeyT *)L.key;
   const KeyT *__restrict__ Rkey = (const KeyT *)R.key;
-  KeyT *okey = (KeyT *)out.key;
-  const uint32_t tid = threadIdx.x;
+  const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int lpw = L.ncols > 0 ? L.width[0] : 0;
+  const int rpw = R.ncols > 0 ? R.width[0] : 0;
 
   if (tid == 0) {
     s_it = atomicAdd(ticket, 1u);
@@ -484,57 +484,108 @@ __global__ void __launch_bounds__(kWT, 2)
       nx = atomicAdd(ticket, 1u);
       if (nx < nitems) dn = desc[nx];
     }
+
+    // 1. stage the build chunk; probe keys to registers; clear the heads
+    for (uint32_t i = tid; i < d.nl; i += kWT) {
+      const uint32_t g = d.lbeg + i;
+      if (sizeof(KeyT) == 8)
+        cp_async_8(&bkey[i], &Lkey[g]);
+      else
+        cp_async_4(&bkey[i], &Lkey[g]);
+      if (L.rid)
+        cp_async_4(&brid[i], &L.rid[g]);
+      else
+        brid[i] = g;
+      if (lpw == 8) cp_async_8(&bpay[i], &((const uint64_t *)L.cols[0])[g]);
+      if (lpw == 4) cp_async_4(&bpay[i], &((const uint32_t *)L.cols[0])[g]);
+    }
     KeyT rk[kWPF];
 #pragma unroll
     for (int j = 0; j < kWPF; j++) {
       const uint32_t rl = j * kWT + tid;
       rk[j] = rl < d.nr ? Rkey[d.rbeg + rl] : KeyT(0);
     }
-    for (uint32_t i0 = 0; i0 < d.nl; i0 += 4 * kWT) {
-      KeyT v[4];
-#pragma unroll
-      for (int u = 0; u < 4; u++) {
-        const uint32_t i = i0 + u * kWT + tid;
-        v[u] = i < d.nl ? Lkey[d.lbeg + i] : KeyT(0);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; u++) {
-        const uint32_t i = i0 + u * kWT + tid;
-        if (i < d.nl) keys[i] = v[u];
-      }
-    }
-    const uint32_t logt = table_log<KeyT>(d.nl), tsz = 1u << logt;
+    uint32_t logt = 5;
+    while ((1u << logt) < d.nl) logt++;
+    const uint32_t tsz = 1u << logt;
     {
       const uint4 z = make_uint4(0, 0, 0, 0);
-      for (uint32_t s = tid * 4; s < tsz; s += kWT * 4) *(uint4 *)(slots + s) = z;
+      for (uint32_t s = tid * 4; s < tsz; s += kWT * 4) *(uint4 *)(heads + s) = z;
     }
-    __syncthreads();
-    build_chain_table<KeyT>(keys, d.nl, logt, slots, nxt);
+    cp_async_wait_all();
     __syncthreads();
 
-    // probe: head of each row's key; c = chain length (1 in the common case)
-    uint32_t c[kWPF], hd[kWPF];
-    uint32_t n1 = 0, nm = 0;
+    // 2. build: push every row onto its slot's chain
+    for (uint32_t i = tid; i < d.nl; i += kWT) {
+      const uint32_t s = chain_slot(key_bits(bkey[i]), logt);
+      nxt[i] = (uint16_t)atomicExch(&heads[s], i + 1);
+    }
+    __syncthreads();
+
+    // 3. probe: ch[j] = (matches << 16) | (first matching row + 1)
+    uint32_t ch[kWPF];
+    uint32_t nm = 0;
 #pragma unroll
     for (int j = 0; j < kWPF; j++) {
-      const uint32_t rl = j * kWT + tid;
-      hd[j] = rl < d.nr ? find_head<KeyT>(rk[j], keys, slots, logt) : 0u;
-      c[j] = 0;
-      if (hd[j]) {
-        uint32_t n = 1, li = nxt[hd[j] - 1];
+      ch[j] = 0;
+      if (j * kWT + tid < d.nr) {
+        const KeyT k = rk[j];
+        uint32_t li = heads[chain_slot(key_bits(k), logt)], first = 0, c = 0;
         while (li) {
-          n++;
+          if (bkey[li - 1] == k) {
+            if (!c) first = li;
+            c++;
+          }
           li = nxt[li - 1];
         }
-        c[j] = n;
+        ch[j] = (c << 16) | first;
+        if (c >= 2) nm += c;
       }
-      if (c[j] == 1) n1++;
-      else nm += c[j];
     }
-    uint64_t tot64;
-    const uint64_t ex64 = block_exclusive_scan<uint64_t>(((uint64_t)n1 << 32) | nm, scratch64, &tot64);
-    const uint32_t S = (uint32_t)(tot64 >> 32);
-    const uint64_t item_total = S + (tot64 & 0xFFFFFFFFull);
+
+    // 4. probe-side row id and first payload of every matching row
+    uint32_t rr[kWPF];
+    uint64_t rp[kWPF];
+#pragma unroll
+    for (int j = 0; j < kWPF; j++) {
+      rr[j] = 0;
+      rp[j] = 0;
+      if (ch[j]) {
+        const uint32_t r = d.rbeg + j * kWT + tid;
+        rr[j] = R.rid ? R.rid[r] : r;
+        if (rpw == 8) rp[j] = ((const uint64_t *)R.cols[0])[r];
+        if (rpw == 4) rp[j] = ((const uint32_t *)R.cols[0])[r];
+      }
+    }
+
+    // 5. offsets: single-match rows by (j, warp, lane), then the rest
+#pragma unroll
+    for (int j = 0; j < kWPF; j++) {
+      const uint32_t bal = __ballot_sync(0xffffffffu, (ch[j] >> 16) == 1);
+      if (lane == 0) cnt1[j * kWW + warp] = __popc(bal);
+    }
+    uint64_t mtot;
+    const uint64_t mex = block_exclusive_scan<uint64_t>(nm, scratch64, &mtot);  // barriers inside
+    if (warp == 0) {
+      constexpr int per = kWPF * kWW / 32;
+      uint32_t v[per], sum = 0;
+#pragma unroll
+      for (int q = 0; q < per; q++) {
+        v[q] = cnt1[lane * per + q];
+        sum += v[q];
+      }
+      const uint32_t inc = warp_inclusive_scan(sum);
+      uint32_t run = inc - sum;
+#pragma unroll
+      for (int q = 0; q < per; q++) {
+        cnt1[lane * per + q] = run;
+        run += v[q];
+      }
+      if (lane == 31) s_single = inc;
+    }
+    __syncthreads();
+    const uint32_t S = s_single;
+    const uint64_t item_total = S + mtot;
     if (tid == 0) {
       uint64_t base;
       if (HAVE_OFFSETS) {
@@ -553,35 +604,32 @@ __global__ void __launch_bounds__(kWT, 2)
       }
       s_base = base;
     }
-    {
-      uint32_t e = (uint32_t)(ex64 >> 32);
-#pragma unroll
-      for (int j = 0; j < kWPF; j++)
-        if (c[j] == 1) list[e++] = ((j * kWT + tid) << 16) | (hd[j] - 1);
-    }
     __syncthreads();
+
+    // 6. write
     const uint64_t base = s_base;
     if (base != ~0ull && base + item_total <= capacity) {
-      // single-match rows: consecutive threads write consecutive rows
-      for (uint32_t e = tid; e < S; e += kWT) {
-        const uint32_t w = list[e];
-        const uint32_t li = w & 0xFFFFu;
-        const uint64_t pos = base + e;
-        okey[pos] = keys[li];
-        copy_cols_row(L, R, out, pos, d.lbeg + li, d.rbeg + (w >> 16));
+#pragma unroll
+      for (int j = 0; j < kWPF; j++) {
+        const bool one = (ch[j] >> 16) == 1;
+        const uint32_t bal = __ballot_sync(0xffffffffu, one);
+        if (one) {
+          const uint64_t pos = base + cnt1[j * kWW + warp] + __popc(bal & lanemask_lt());
+          write_row<KeyT>(L, R, out, pos, bkey, brid, bpay, (ch[j] & 0xFFFFu) - 1, d.lbeg, d.rbeg + j * kWT + tid,
+                          rr[j], rp[j]);
+        }
       }
-      // rows with several matches: each thread expands its own
       if (nm) {
-        uint64_t pos = base + S + (ex64 & 0xFFFFFFFFull);
+        uint64_t pos = base + S + mex;
 #pragma unroll
         for (int j = 0; j < kWPF; j++) {
-          if (c[j] < 2) continue;
-          const uint32_t r = d.rbeg + j * kWT + tid;
-          uint32_t li = hd[j];
+          if ((ch[j] >> 16) < 2) continue;
+          uint32_t li = ch[j] & 0xFFFFu;
+          const KeyT k = bkey[li - 1];
           while (li) {
-            okey[pos] = keys[li - 1];
-            copy_cols_row(L, R, out, pos, d.lbeg + li - 1, r);
-            pos++;
+            if (bkey[li - 1] == k)
+              write_row<KeyT>(L, R, out, pos++, bkey, brid, bpay, li - 1, d.lbeg, d.rbeg + j * kWT + tid, rr[j],
+                              rp[j]);
             li = nxt[li - 1];
           }
         }
@@ -773,7 +821,7 @@ int run_join(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, md
   mdj_result r;
   JOut o;
   MDJ_TRY(alloc_result(ws, Ls, Rs, sizeof(KeyT), cap_rows, &r, &o));
-  const size_t sm = WriteLayout<KeyT>(plan.cap).total;  // ~88 KB at cap 4096: two blocks per SM
+  const size_t sm = WriteLayout<KeyT>(plan.cap).total;  // ~105 KB at cap 4096: two blocks per SM
   if (nitems) {
     int grid;
     MDJ_TRY(resident_grid(k_join_write<KeyT, false>, sm, nitems, &grid, kWT));

@@ -550,55 +550,89 @@ __global__ void __launch_bounds__(kPT, 2)
 // The merge needs every row in its sub-bucket, not the input order inside a
 // bucket, so its shuffle drops stability (the public partition keeps it):
 //
-//   k_tot      rows per final sub-bucket (shared counters, flushed with one
-//              global add per counter); the next chunk's keys load while the
-//              current chunk is counted
-//   k_shuffle  one tile of 4096 rows: every column of a row is loaded at the
-//              start, a row's rank in its bucket is a shared-memory atomic,
-//              each (tile, bucket) run is reserved with one global atomicAdd
-//              on the bucket's cursor, and the columns are staged in bucket
-//              order and leave as runs; three block barriers per tile.
+//   k_tot      rows per final sub-bucket, and rows per (pass-1 bucket, slab)
+//              where slab s is a contiguous range of tiles (shared counters;
+//              the next chunk's keys load while the current one is counted)
+//   k_shuffle  tiles of 4096 rows: every column of a row is loaded before the
+//              tile is processed (the next tile's while the current one is
+//              written out), a row's rank in its bucket is a shared-memory
+//              atomic, and the columns are staged in bucket order and leave
+//              as runs; three block barriers per tile.
+//              Pass 1: block s walks slab s and keeps one cursor per bucket
+//              in shared memory, starting at the scanned (bucket, slab)
+//              counts, so no two blocks share a cursor.
 //              PASS2: rows already grouped by pass-1 bucket (sub-bucket / F2)
-//              are split into their sub-buckets, as in k_scatter's RESERVE.
-// A pass-1 bucket's cursor starts at the offset of its first sub-bucket
-// (pass-1 bucket b = sub-bucket / F2, see BucketSpec), so one count of the
-// final sub-buckets serves both passes.
+//              are split into their sub-buckets; each (tile, sub-bucket) run
+//              is reserved with one global atomicAdd, as in k_scatter's
+//              RESERVE (thousands of cursors, so atomics rarely collide).
+// A pass-1 bucket holds the rows of sub-buckets [b * F2, (b + 1) * F2)
+// (pass-1 bucket = sub-bucket / F2, see BucketSpec), so the scanned counts
+// of the final sub-buckets also place the pass-1 buckets.
 
 constexpr int kTotThreads = 1024;
 constexpr int kTotU = 8;                        // keys per thread per chunk
-constexpr int kFT = 512;                        // threads of k_shuffle
-constexpr uint32_t kFTile = (uint32_t)kFT * kRPL;  // 4096 rows
-constexpr uint32_t kFSpan = 1024;               // local buckets of one tile
+// k_shuffle: NT threads, tiles of NT * kRPL rows, at most 2 * NT local
+// buckets per tile, 1024 / NT blocks per SM.
+constexpr int kShuffleNT = 512;
+template <int NT>
+__host__ __device__ constexpr uint32_t shuffle_tile() { return (uint32_t)NT * kRPL; }
+template <int NT>
+__host__ __device__ constexpr uint32_t shuffle_span() { return 2u * NT; }
+template <int NT>
+constexpr size_t shuffle_smem_bytes() {
+  return (size_t)shuffle_tile<NT>() * (8 + 8 + 4 + 4) + (size_t)shuffle_span<NT>() * 12 + 40 * 4;
+}
 
-size_t shuffle_smem_bytes() { return (size_t)kFTile * (8 + 8 + 4 + 4) + (size_t)kFSpan * 8 + 40 * 4; }
-
-template <typename KeyT>
-__device__ __forceinline__ void tot_load(const KeyT *__restrict__ keys, uint64_t base, uint32_t n, KeyT (&v)[kTotU]) {
-#pragma unroll
-  for (int u = 0; u < kTotU; u++) {
-    const uint64_t r = base + (uint64_t)u * kTotThreads + threadIdx.x;
-    v[u] = r < n ? keys[r] : KeyT(0);
-  }
+// First tile of slab s when ntiles tiles are cut into NS slabs.
+__host__ __device__ __forceinline__ uint32_t slab_lo(uint32_t s, uint32_t ntiles, uint32_t NS) {
+  return (uint32_t)((uint64_t)s * ntiles / NS);
 }
 
 template <typename KeyT>
-__global__ void __launch_bounds__(kTotThreads) k_tot(const KeyT *__restrict__ keys, uint32_t n, BucketSpec bs,
-                                                     uint32_t nsub, uint32_t *__restrict__ tot) {
-  extern __shared__ uint32_t cnt[];
-  for (uint32_t i = threadIdx.x; i < nsub; i += kTotThreads) cnt[i] = 0;
-  __syncthreads();
-  const uint64_t chunk = (uint64_t)kTotThreads * kTotU, stride = chunk * gridDim.x;
-  uint64_t base = chunk * blockIdx.x;
-  KeyT cur[kTotU], nxt[kTotU];
-  tot_load<KeyT>(keys, base, n, cur);
-  for (; base < n; base += stride) {
-    tot_load<KeyT>(keys, base + stride, n, nxt);
+__device__ __forceinline__ void tot_load(const KeyT *__restrict__ keys, uint64_t base, uint64_t end,
+                                         KeyT (&v)[kTotU]) {
 #pragma unroll
-    for (int u = 0; u < kTotU; u++) {
-      const uint64_t r = base + (uint64_t)u * kTotThreads + threadIdx.x;
-      if (r < n) atomicAdd(&cnt[sub_bucket_of(fmix64(key_bits(cur[u])), bs)], 1u);
-      cur[u] = nxt[u];
+  for (int u = 0; u < kTotU; u++) {
+    const uint64_t r = base + (uint64_t)u * kTotThreads + threadIdx.x;
+    v[u] = r < end ? keys[r] : KeyT(0);
+  }
+}
+
+// tot[sb] += rows of sub-bucket sb (spec bs, nsub = P * S); slab_cnt[b * NS +
+// s] = rows of slab s (tiles of `tile` rows) in pass-1 bucket b = p * S1 +
+// floor(hi32(h) * S1 / 2^32), b < F1.  Block b counts slabs b, b + gridDim.x, ...
+template <typename KeyT>
+__global__ void __launch_bounds__(kTotThreads)
+    k_tot(const KeyT *__restrict__ keys, uint32_t n, BucketSpec bs, uint32_t nsub, uint32_t *__restrict__ tot,
+          uint32_t S1, uint32_t F1, uint32_t tile, uint32_t ntiles, uint32_t NS, uint32_t *__restrict__ slab_cnt) {
+  extern __shared__ uint32_t cnt[];
+  uint32_t *c1 = cnt + nsub;
+  for (uint32_t i = threadIdx.x; i < nsub; i += kTotThreads) cnt[i] = 0;
+  const uint64_t chunk = (uint64_t)kTotThreads * kTotU;
+  for (uint32_t s = blockIdx.x; s < NS; s += gridDim.x) {
+    for (uint32_t i = threadIdx.x; i < F1; i += kTotThreads) c1[i] = 0;
+    __syncthreads();
+    const uint64_t lo = (uint64_t)slab_lo(s, ntiles, NS) * tile;
+    const uint64_t hi_t = (uint64_t)slab_lo(s + 1, ntiles, NS) * tile;
+    const uint64_t hi = hi_t < n ? hi_t : n;
+    KeyT cur[kTotU], nxt[kTotU];
+    tot_load<KeyT>(keys, lo, hi, cur);
+    for (uint64_t base = lo; base < hi; base += chunk) {
+      tot_load<KeyT>(keys, base + chunk, hi, nxt);
+#pragma unroll
+      for (int u = 0; u < kTotU; u++) {
+        const uint64_t r = base + (uint64_t)u * kTotThreads + threadIdx.x;
+        if (r < hi) {
+          const uint64_t h = fmix64(key_bits(cur[u]));
+          const uint32_t p = mod_p(h, bs), x = (uint32_t)(h >> 32);
+          atomicAdd(&cnt[p * bs.S + __umulhi(x, bs.S)], 1u);
+          atomicAdd(&c1[p * S1 + __umulhi(x, S1)], 1u);
+        }
+        cur[u] = nxt[u];
+      }
     }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < F1; i += kTotThreads) slab_cnt[(size_t)i * NS + s] = c1[i];
   }
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < nsub; i += kTotThreads)
@@ -627,34 +661,18 @@ __device__ __noinline__ void shuffle_direct(const KeyT *__restrict__ keys, uint3
   scatter_direct<KeyT>(kv, wrow0, rend, bs, cursors, cm, rid_in, rid_out);
 }
 
-// Rows of tile blockIdx.x: warp w holds rows row0 + w*256 + c*32 + lane
-// (c < kRPL), the layout scatter_direct uses.  `reg_col` is the non-key column
-// carried in registers from the start (-1: none); the other non-key columns
-// are loaded and staged one at a time after the first write-out.
-template <typename KeyT, bool PASS2>
-__global__ void __launch_bounds__(kFT, 2)
-    k_shuffle(const KeyT *__restrict__ keys, uint32_t n, BucketSpec bs, uint32_t F, uint32_t F2,
-              uint32_t *__restrict__ cursors, ColMove cm, int reg_col, const uint32_t *__restrict__ rid_in,
-              uint32_t *__restrict__ rid_out) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  KeyT *sk = (KeyT *)smem;
-  uint64_t *sp = (uint64_t *)(smem + (size_t)kFTile * 8);
-  uint32_t *sr = (uint32_t *)(smem + (size_t)kFTile * 16);
-  uint32_t *dstmap = sr + kFTile;
-  uint32_t *lstart = dstmap + kFTile;
-  uint32_t *gbase = lstart + kFSpan;
-  uint32_t *scratch = gbase + kFSpan;
-
-  const uint32_t row0 = blockIdx.x * kFTile;
-  const uint32_t rows = min(kFTile, n - row0);
-  const uint32_t rend = row0 + rows;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t wrow0 = row0 + warp * 32 * kRPL;
-
-  KeyT kv[kRPL];
-  uint64_t pv[kRPL];
-  uint32_t rv[kRPL];
-  const int pw = reg_col >= 0 ? cm.width[reg_col] : 0;
+// Loads the carried columns of tile t into registers: warp w holds rows
+// row0 + w*256 + c*32 + lane (c < kRPL), the layout scatter_direct uses.
+// PASS2 also fetches the tile's first and last key (its pass-1 bucket span).
+template <int NT, typename KeyT, bool PASS2>
+__device__ __forceinline__ void shuffle_load(const KeyT *__restrict__ keys, uint32_t n, uint32_t t, const ColMove &cm,
+                                             int reg_col, int pw, const uint32_t *__restrict__ rid_in,
+                                             KeyT (&kv)[kRPL], uint64_t (&pv)[kRPL], uint32_t (&rv)[kRPL],
+                                             KeyT &kfirst, KeyT &klast) {
+  const uint32_t row0 = t * shuffle_tile<NT>();
+  const uint32_t rend = min(row0 + shuffle_tile<NT>(), n);
+  const uint32_t wrow0 = row0 + (threadIdx.x >> 5) * 32 * kRPL;
+  const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int c = 0; c < kRPL; c++) {
     const uint32_t r = wrow0 + c * 32 + lane;
@@ -665,101 +683,174 @@ __global__ void __launch_bounds__(kFT, 2)
     if (ok && pw == 4) pv[c] = ((const uint32_t *)cm.src[reg_col])[r];
     rv[c] = rid_in ? (ok ? rid_in[r] : 0u) : r;
   }
-
-  uint32_t lb0 = 0, Floc = F;
   if (PASS2) {
-    const uint32_t b1f = sub_bucket_of(fmix64(key_bits(keys[row0])), bs) / F2;
-    const uint32_t b1l = sub_bucket_of(fmix64(key_bits(keys[rend - 1])), bs) / F2;
-    lb0 = b1f * F2;
-    Floc = (b1l - b1f + 1) * F2;
-    if (Floc > kFSpan) {
-      shuffle_direct<KeyT>(keys, wrow0, rend, bs, cursors, cm, rid_in, rid_out);
-      return;
+    kfirst = keys[row0];
+    klast = keys[rend - 1];
+  }
+}
+
+// Persistent: block b takes tiles b, b + gridDim.x, ...  Once a tile is
+// staged its registers are free, so the next tile's columns are loaded into
+// them before the staged tile is written out; the DRAM latency of the load
+// overlaps the write-out.  `reg_col` is the non-key column carried in
+// registers (-1: none); with EXTRA, the other non-key columns are loaded and
+// staged one at a time after the first write-out (and the next tile's load
+// waits until they are done).
+template <int NT, typename KeyT, bool PASS2, bool EXTRA>
+__global__ void __launch_bounds__(NT, 1024 / NT)
+    k_shuffle(const KeyT *__restrict__ keys, uint32_t n, uint32_t ntiles, BucketSpec bs, uint32_t F, uint32_t F2,
+              uint32_t *__restrict__ cursors, const uint32_t *__restrict__ slab_base, uint32_t NS, ColMove cm,
+              int reg_col, const uint32_t *__restrict__ rid_in, uint32_t *__restrict__ rid_out) {
+  constexpr uint32_t kFTile = shuffle_tile<NT>(), kFSpan = shuffle_span<NT>();
+  constexpr int kFT = NT;
+  extern __shared__ __align__(16) unsigned char smem[];
+  KeyT *sk = (KeyT *)smem;
+  uint64_t *sp = (uint64_t *)(smem + (size_t)kFTile * 8);
+  uint32_t *sr = (uint32_t *)(smem + (size_t)kFTile * 16);
+  uint32_t *dstmap = sr + kFTile;
+  uint32_t *lstart = dstmap + kFTile;
+  uint32_t *gbase = lstart + kFSpan;
+  uint32_t *scur = gbase + kFSpan;
+  uint32_t *scratch = scur + kFSpan;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pw = reg_col >= 0 ? cm.width[reg_col] : 0;
+  KeyT kv[kRPL];
+  uint64_t pv[kRPL];
+  uint32_t rv[kRPL];
+  KeyT kfirst = KeyT(0), klast = KeyT(0);
+  // slab mode (slab_base given, pass 1 only): the tiles of slab blockIdx.x in
+  // order; otherwise tiles blockIdx.x + k * gridDim.x with global cursors
+  const bool slab = !PASS2 && slab_base != nullptr;
+  uint32_t t = slab ? slab_lo(blockIdx.x, ntiles, NS) : blockIdx.x;
+  const uint32_t tend = slab ? slab_lo(blockIdx.x + 1, ntiles, NS) : ntiles;
+  const uint32_t tstep = slab ? 1u : gridDim.x;
+  if (t >= tend) return;
+  if (slab)
+    for (uint32_t b = threadIdx.x; b < F; b += kFT) scur[b] = slab_base[(size_t)b * NS + blockIdx.x];
+  shuffle_load<NT, KeyT, PASS2>(keys, n, t, cm, reg_col, pw, rid_in, kv, pv, rv, kfirst, klast);
+
+  while (t < tend) {
+    const uint32_t row0 = t * kFTile;
+    const uint32_t rows = min(kFTile, n - row0);
+    const uint32_t rend = row0 + rows;
+    const uint32_t wrow0 = row0 + warp * 32 * kRPL;
+    const uint32_t tn = t + tstep;
+
+    uint32_t lb0 = 0, Floc = F;
+    if (PASS2) {
+      const uint32_t b1f = sub_bucket_of(fmix64(key_bits(kfirst)), bs) / F2;
+      const uint32_t b1l = sub_bucket_of(fmix64(key_bits(klast)), bs) / F2;
+      lb0 = b1f * F2;
+      Floc = (b1l - b1f + 1) * F2;
+      if (Floc > kFSpan) {  // uniform over the block: no barrier inside
+        shuffle_direct<KeyT>(keys, wrow0, rend, bs, cursors, cm, rid_in, rid_out);
+        if (tn < tend) shuffle_load<NT, KeyT, PASS2>(keys, n, tn, cm, reg_col, pw, rid_in, kv, pv, rv, kfirst, klast);
+        t = tn;
+        continue;
+      }
     }
-  }
 
-  // 1. rank of each row in its bucket (order among equal buckets: arbitrary)
-  uint32_t *cnt = lstart;
-  for (uint32_t i = threadIdx.x; i < Floc; i += kFT) cnt[i] = 0;
-  __syncthreads();
-  uint32_t pk[kRPL];
-#pragma unroll
-  for (int c = 0; c < kRPL; c++) {
-    pk[c] = 0xFFFFFFFFu;
-    if (wrow0 + c * 32 + lane < rend) {
-      const uint64_t h = fmix64(key_bits(kv[c]));
-      const uint32_t b = (PASS2 ? sub_bucket_of(h, bs) : bucket_of(h, bs)) - lb0;
-      pk[c] = (b << 16) | atomicAdd(&cnt[b], 1u);
-    }
-  }
-  __syncthreads();
-
-  // 2. reserve every non-empty run (two buckets per thread) and scan the counts
-  const uint32_t b0 = 2 * threadIdx.x, b1 = b0 + 1;
-  const uint32_t c0 = b0 < Floc ? cnt[b0] : 0u, c1 = b1 < Floc ? cnt[b1] : 0u;
-  const uint32_t g0 = c0 ? atomicAdd(&cursors[lb0 + b0], c0) : 0u;
-  const uint32_t g1 = c1 ? atomicAdd(&cursors[lb0 + b1], c1) : 0u;
-  uint32_t total;
-  const uint32_t ex = block_exclusive_scan<uint32_t>(c0 + c1, scratch, &total);
-  if (b0 < Floc) {
-    lstart[b0] = ex;
-    gbase[b0] = g0;
-  }
-  if (b1 < Floc) {
-    lstart[b1] = ex + c0;
-    gbase[b1] = g1;
-  }
-  __syncthreads();
-
-  // 3. stage every carried column in bucket order, with each row's destination
-  uint32_t lp[kRPL];
-#pragma unroll
-  for (int c = 0; c < kRPL; c++) {
-    lp[c] = 0xFFFFFFFFu;
-    if (pk[c] != 0xFFFFFFFFu) {
-      const uint32_t b = pk[c] >> 16, rank = pk[c] & 0xFFFFu;
-      lp[c] = lstart[b] + rank;
-      dstmap[lp[c]] = gbase[b] + rank;
-      sk[lp[c]] = kv[c];
-      sp[lp[c]] = pv[c];
-      sr[lp[c]] = rv[c];
-    }
-  }
-  __syncthreads();
-
-  // 4. write-out: consecutive threads store consecutive rows of one run
-  KeyT *kdst = (KeyT *)cm.dst[cm.key_index];
-  for (uint32_t i = threadIdx.x; i < rows; i += kFT) {
-    const uint32_t d = dstmap[i];
-    kdst[d] = sk[i];
-    if (pw == 8) ((uint64_t *)cm.dst[reg_col])[d] = sp[i];
-    if (pw == 4) ((uint32_t *)cm.dst[reg_col])[d] = (uint32_t)sp[i];
-    if (rid_out) rid_out[d] = sr[i];
-  }
-
-  // 5. any further column, one at a time through the payload stage
-  for (int j = 0; j < cm.n; j++) {
-    if (j == cm.key_index || j == reg_col) continue;
-    const int w = cm.width[j];
-    uint64_t v[kRPL];
+    // 1. rank of each row in its bucket (order among equal buckets: arbitrary)
+    uint32_t *cnt = lstart;
+    for (uint32_t i = threadIdx.x; i < Floc; i += kFT) cnt[i] = 0;
+    __syncthreads();
+    uint32_t pk[kRPL];
 #pragma unroll
     for (int c = 0; c < kRPL; c++) {
-      const uint32_t r = wrow0 + c * 32 + lane;
-      v[c] = 0;
-      if (r < rend) v[c] = w == 8 ? ((const uint64_t *)cm.src[j])[r] : ((const uint32_t *)cm.src[j])[r];
+      pk[c] = 0xFFFFFFFFu;
+      if (wrow0 + c * 32 + lane < rend) {
+        const uint64_t h = fmix64(key_bits(kv[c]));
+        const uint32_t b = (PASS2 ? sub_bucket_of(h, bs) : bucket_of(h, bs)) - lb0;
+        pk[c] = (b << 16) | atomicAdd(&cnt[b], 1u);
+      }
     }
     __syncthreads();
-#pragma unroll
-    for (int c = 0; c < kRPL; c++)
-      if (lp[c] != 0xFFFFFFFFu) sp[lp[c]] = v[c];
+
+    // 2. place every non-empty run (two buckets per thread), scan the counts
+    const uint32_t b0 = 2 * threadIdx.x, b1 = b0 + 1;
+    const uint32_t c0 = b0 < Floc ? cnt[b0] : 0u, c1 = b1 < Floc ? cnt[b1] : 0u;
+    uint32_t g0 = 0, g1 = 0;
+    if (!slab) {
+      g0 = c0 ? atomicAdd(&cursors[lb0 + b0], c0) : 0u;
+      g1 = c1 ? atomicAdd(&cursors[lb0 + b1], c1) : 0u;
+    } else {
+      if (b0 < Floc) {
+        g0 = scur[b0];
+        scur[b0] = g0 + c0;
+      }
+      if (b1 < Floc) {
+        g1 = scur[b1];
+        scur[b1] = g1 + c1;
+      }
+    }
+    uint32_t total;
+    const uint32_t ex = block_exclusive_scan<uint32_t>(c0 + c1, scratch, &total);
+    if (b0 < Floc) {
+      lstart[b0] = ex;
+      gbase[b0] = g0;
+    }
+    if (b1 < Floc) {
+      lstart[b1] = ex + c0;
+      gbase[b1] = g1;
+    }
     __syncthreads();
+
+    // 3. stage the carried columns in bucket order, with each row's destination
+    uint32_t lp[kRPL];
+#pragma unroll
+    for (int c = 0; c < kRPL; c++) {
+      lp[c] = 0xFFFFFFFFu;
+      if (pk[c] != 0xFFFFFFFFu) {
+        const uint32_t b = pk[c] >> 16, rank = pk[c] & 0xFFFFu;
+        lp[c] = lstart[b] + rank;
+        dstmap[lp[c]] = gbase[b] + rank;
+        sk[lp[c]] = kv[c];
+        sp[lp[c]] = pv[c];
+        sr[lp[c]] = rv[c];
+      }
+    }
+    __syncthreads();
+    if (!EXTRA && tn < tend) shuffle_load<NT, KeyT, PASS2>(keys, n, tn, cm, reg_col, pw, rid_in, kv, pv, rv, kfirst, klast);
+
+    // 4. write-out: consecutive threads store consecutive rows of one run
+    KeyT *kdst = (KeyT *)cm.dst[cm.key_index];
     for (uint32_t i = threadIdx.x; i < rows; i += kFT) {
       const uint32_t d = dstmap[i];
-      if (w == 8)
-        ((uint64_t *)cm.dst[j])[d] = sp[i];
-      else
-        ((uint32_t *)cm.dst[j])[d] = (uint32_t)sp[i];
+      kdst[d] = sk[i];
+      if (pw == 8) ((uint64_t *)cm.dst[reg_col])[d] = sp[i];
+      if (pw == 4) ((uint32_t *)cm.dst[reg_col])[d] = (uint32_t)sp[i];
+      if (rid_out) rid_out[d] = sr[i];
     }
+
+    // 5. any further column, one at a time through the payload stage
+    if (EXTRA) {
+      for (int j = 0; j < cm.n; j++) {
+        if (j == cm.key_index || j == reg_col) continue;
+        const int w = cm.width[j];
+        uint64_t v[kRPL];
+#pragma unroll
+        for (int c = 0; c < kRPL; c++) {
+          const uint32_t r = wrow0 + c * 32 + lane;
+          v[c] = 0;
+          if (r < rend) v[c] = w == 8 ? ((const uint64_t *)cm.src[j])[r] : ((const uint32_t *)cm.src[j])[r];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < kRPL; c++)
+          if (lp[c] != 0xFFFFFFFFu) sp[lp[c]] = v[c];
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < rows; i += kFT) {
+          const uint32_t d = dstmap[i];
+          if (w == 8)
+            ((uint64_t *)cm.dst[j])[d] = sp[i];
+          else
+            ((uint32_t *)cm.dst[j])[d] = (uint32_t)sp[i];
+        }
+      }
+      if (tn < tend) shuffle_load<NT, KeyT, PASS2>(keys, n, tn, cm, reg_col, pw, rid_in, kv, pv, rv, kfirst, klast);
+    }
+    t = tn;
   }
 }
 
@@ -1015,61 +1106,71 @@ bool fast_shuffle_enabled() {
   return !(e && e[0] == '1');
 }
 
+// MDJ_SLAB_CURSORS=1: pass 1 walks contiguous slabs with private cursors
+// (measured slower on GB300 than shared atomic cursors; kept for study).
+bool slab_mode() {
+  const char *e = getenv("MDJ_SLAB_CURSORS");
+  return e && e[0] == '1';
+}
+
 template <typename KeyT>
 int set_shuffle_attrs() {
   static bool done = false;
   if (done) return MDJ_OK;
-  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_shuffle<KeyT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)shuffle_smem_bytes()));
-  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_shuffle<KeyT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)shuffle_smem_bytes()));
+  constexpr int NT = kShuffleNT;
+  const int sm = (int)shuffle_smem_bytes<NT>();
+  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_shuffle<NT, KeyT, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_shuffle<NT, KeyT, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_shuffle<NT, KeyT, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_shuffle<NT, KeyT, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   MDJ_CUDA_TRY(cudaFuncSetAttribute(k_tot<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(kMaxSubBuckets * 4)));
+                                    (int)((kMaxSubBuckets + kMaxFanout) * 4)));
   done = true;
   return MDJ_OK;
 }
 
-// Rows per sub-bucket of spec `bs` (nsub = P * S) into tot[0..nsub), which
-// the call zeroes first.
 template <typename KeyT>
-int count_sub_buckets(Workspace &ws, const KeyT *keys, uint32_t n, const BucketSpec &bs, uint32_t nsub,
-                      uint32_t *tot) {
-  cudaStream_t s = ws.stream();
-  MDJ_CUDA_TRY(cudaMemsetAsync(tot, 0, (size_t)nsub * 4, s));
-  if (n == 0) return MDJ_OK;
-  const size_t smem = (size_t)nsub * 4;
+auto shuffle_kernel(bool pass2, bool extra) {
+  constexpr int NT = kShuffleNT;
+  if (pass2) return extra ? k_shuffle<NT, KeyT, true, true> : k_shuffle<NT, KeyT, true, false>;
+  return extra ? k_shuffle<NT, KeyT, false, true> : k_shuffle<NT, KeyT, false, false>;
+}
+
+// Resident blocks of a k_shuffle launch over ntiles tiles (its grid).
+template <typename KeyT>
+int shuffle_grid(bool pass2, bool extra, uint32_t ntiles, uint32_t *grid) {
   int per_sm = 0;
-  MDJ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tot<KeyT>, kTotThreads, smem));
+  MDJ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, shuffle_kernel<KeyT>(pass2, extra), kShuffleNT,
+                                                             shuffle_smem_bytes<kShuffleNT>()));
   if (per_sm < 1) per_sm = 1;
-  const uint64_t chunks = ((uint64_t)n + (uint64_t)kTotThreads * kTotU - 1) / ((uint64_t)kTotThreads * kTotU);
-  const uint64_t full = (uint64_t)num_sms() * per_sm;
-  const unsigned grid = (unsigned)(chunks < full ? chunks : full);
-  {
-    TraceScope tr("hist", s);
-    k_tot<KeyT><<<grid, kTotThreads, smem, s>>>(keys, n, bs, nsub, tot);
-  }
-  MDJ_LAUNCH_CHECK();
+  const uint32_t full = (uint32_t)(num_sms() * per_sm);
+  *grid = ntiles < full ? ntiles : full;
   return MDJ_OK;
 }
 
-// One unstable shuffle pass (see k_shuffle) of n rows with run cursors `cur`.
+// One unstable shuffle pass (see k_shuffle) of n rows on `grid` blocks.
+// Pass 1 takes slab bases (F buckets x NS = grid slabs, bucket-major);
+// pass 2 takes run cursors per sub-bucket.
 template <typename KeyT, bool PASS2>
-int shuffle_pass(Workspace &ws, const KeyT *keys, uint32_t n, const BucketSpec &bs, uint32_t F, uint32_t F2,
-                 uint32_t *cur, const ColMove &cm, const uint32_t *rid_in, uint32_t *rid_out) {
-  const uint32_t ntiles = (n + kFTile - 1) / kFTile;
+int shuffle_pass(Workspace &ws, const KeyT *keys, uint32_t n, uint32_t grid, const BucketSpec &bs, uint32_t F,
+                 uint32_t F2, uint32_t *cur, const uint32_t *slab_base, const ColMove &cm, const uint32_t *rid_in,
+                 uint32_t *rid_out) {
+  constexpr int NT = kShuffleNT;
+  const uint32_t ntiles = (n + shuffle_tile<NT>() - 1) / shuffle_tile<NT>();
   if (ntiles == 0) return MDJ_OK;
   int reg_col = -1;
   for (int j = 0; j < cm.n && reg_col < 0; j++)
     if (j != cm.key_index) reg_col = j;
   TraceScope tr(PASS2 ? "scatter_reserve" : "scatter_stable", ws.stream());
-  k_shuffle<KeyT, PASS2><<<ntiles, kFT, shuffle_smem_bytes(), ws.stream()>>>(keys, n, bs, F, F2, cur, cm, reg_col,
-                                                                            rid_in, rid_out);
+  shuffle_kernel<KeyT>(PASS2, cm.n > 2)<<<grid, NT, shuffle_smem_bytes<NT>(), ws.stream()>>>(
+      keys, n, ntiles, bs, F, F2, cur, slab_base, grid, cm, reg_col, rid_in, rid_out);
   MDJ_LAUNCH_CHECK();
   return MDJ_OK;
 }
 
 // The merge's partition of one side with the unstable passes: count the
-// final sub-buckets, scan them into `off`, then one pass (F2 == 1) or two.
+// final sub-buckets and the (pass-1 bucket, slab) rows, scan both, then one
+// pass (F2 == 1) or two.
 template <typename KeyT>
 int shuffle_side_t(Workspace &ws, const mdj_table *t, int32_t key_col, const Plan &plan, uint32_t *off,
                    TableBufs *fin) {
@@ -1077,38 +1178,63 @@ int shuffle_side_t(Workspace &ws, const mdj_table *t, int32_t key_col, const Pla
   MDJ_TRY(set_shuffle_attrs<KeyT>());
   const uint32_t n = (uint32_t)t->nrows;
   const uint32_t nsub = plan.nbuckets;
+  const uint32_t F1 = plan.F2 == 1 ? nsub : plan.F1;
   const void *src[MDJ_MAX_COLS];
   for (int j = 0; j < t->ncols; j++) src[j] = t->cols[j].data;
   const KeyT *keys = (const KeyT *)src[key_col];
   const BucketSpec sub = make_spec(plan.P, plan.S, 1);
+  const BucketSpec p1spec = make_spec(plan.P, plan.S, plan.F2);
+  const bool extra = t->ncols > 2;
+  const uint32_t tile = shuffle_tile<kShuffleNT>();
+  const uint32_t ntiles = (n + tile - 1) / tile;
 
-  MDJ_TRY(count_sub_buckets<KeyT>(ws, keys, n, sub, nsub, off));
-  MDJ_TRY(exclusive_scan_u32(ws, off, off, (size_t)nsub + 1));
-  uint32_t *cur = (uint32_t *)ws.get((size_t)(nsub + 1) * 4);
-  if (!cur) return MDJ_ERR_OOM;
+  MDJ_CUDA_TRY(cudaMemsetAsync(off, 0, (size_t)(nsub + 1) * 4, s));
   MDJ_TRY(alloc_table_bufs(ws, t, fin, true));
+  if (n == 0) return MDJ_OK;
+  uint32_t NS = 0;
+  MDJ_TRY(shuffle_grid<KeyT>(false, extra, ntiles, &NS));
+  const bool slabs = slab_mode();
+  uint32_t *slab = (uint32_t *)ws.get(((size_t)F1 * NS + 1) * 4);
+  uint32_t *cur = (uint32_t *)ws.get((size_t)(nsub + 1) * 4);
+  if (!slab || !cur) return MDJ_ERR_OOM;
+  {
+    const size_t smem = (size_t)(nsub + F1) * 4;
+    int per_sm = 0;
+    MDJ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tot<KeyT>, kTotThreads, smem));
+    if (per_sm < 1) per_sm = 1;
+    const uint32_t full = (uint32_t)(num_sms() * per_sm);
+    const uint32_t grid = NS < full ? NS : full;
+    TraceScope tr("hist", s);
+    k_tot<KeyT><<<grid, kTotThreads, smem, s>>>(keys, n, sub, nsub, off, p1spec.S1, F1, tile, ntiles, NS, slab);
+  }
+  MDJ_LAUNCH_CHECK();
+  MDJ_TRY(exclusive_scan_u32(ws, off, off, (size_t)nsub + 1));
+  MDJ_TRY(exclusive_scan_u32(ws, slab, slab, (size_t)F1 * NS));
+  if (!slabs) {
+    // pass-1 cursors: the first row of every pass-1 bucket
+    TraceScope tr("pass1_cursors", s);
+    k_pass1_cursors<<<(F1 + 255) / 256, 256, 0, s>>>(off, F1, plan.F2, cur);
+  }
+  MDJ_LAUNCH_CHECK();
+  const uint32_t *sb = slabs ? slab : nullptr;
   if (plan.F2 == 1) {
-    MDJ_CUDA_TRY(cudaMemcpyAsync(cur, off, (size_t)nsub * 4, cudaMemcpyDeviceToDevice, s));
     ColMove cm = make_move(t, key_col, src, fin->cols);
-    MDJ_TRY((shuffle_pass<KeyT, false>(ws, keys, n, sub, nsub, 1, cur, cm, nullptr, fin->rid)));
+    MDJ_TRY((shuffle_pass<KeyT, false>(ws, keys, n, NS, sub, nsub, 1, cur, sb, cm, nullptr, fin->rid)));
   } else {
     TableBufs p1;
     MDJ_TRY(alloc_table_bufs(ws, t, &p1, true));
-    {
-      TraceScope tr("pass1_cursors", s);
-      k_pass1_cursors<<<(plan.F1 + 255) / 256, 256, 0, s>>>(off, plan.F1, plan.F2, cur);
-    }
-    MDJ_LAUNCH_CHECK();
     ColMove cm1 = make_move(t, key_col, src, p1.cols);
-    MDJ_TRY((shuffle_pass<KeyT, false>(ws, keys, n, make_spec(plan.P, plan.S, plan.F2), plan.F1, plan.F2, cur, cm1,
-                                       nullptr, p1.rid)));
+    MDJ_TRY((shuffle_pass<KeyT, false>(ws, keys, n, NS, p1spec, F1, plan.F2, cur, sb, cm1, nullptr, p1.rid)));
     MDJ_CUDA_TRY(cudaMemcpyAsync(cur, off, (size_t)nsub * 4, cudaMemcpyDeviceToDevice, s));
+    uint32_t grid2 = 0;
+    MDJ_TRY(shuffle_grid<KeyT>(true, extra, ntiles, &grid2));
     ColMove cm2 = make_move(t, key_col, p1.cols, fin->cols);
-    MDJ_TRY((shuffle_pass<KeyT, true>(ws, (const KeyT *)p1.cols[key_col], n, sub, 0, plan.F2, cur, cm2, p1.rid,
-                                      fin->rid)));
+    MDJ_TRY((shuffle_pass<KeyT, true>(ws, (const KeyT *)p1.cols[key_col], n, grid2, sub, 0, plan.F2, cur, nullptr,
+                                      cm2, p1.rid, fin->rid)));
     release_table_bufs(ws, t, &p1);
   }
   ws.give_back(cur);
+  ws.give_back(slab);
   return MDJ_OK;
 }
 
@@ -1288,7 +1414,12 @@ Plan make_plan(uint64_t n_build, uint32_t P, uint32_t cap, bool force_partition)
     pl.nbuckets = pl.F1;
     return pl;
   }
-  uint32_t S1 = kMergeFanout / P;
+  uint32_t fan = kMergeFanout;
+  if (const char *e = getenv("MDJ_MERGE_FANOUT")) {  // pass-1 buckets, for tuning studies
+    const int v = atoi(e);
+    if (v >= 8 && v <= (int)kMaxFanout) fan = (uint32_t)v;
+  }
+  uint32_t S1 = fan / P;
   if (S1 < 1) S1 = 1;
   uint64_t F2 = (S + S1 - 1) / S1;
   uint64_t max_f2 = kMaxSubBuckets / ((uint64_t)P * S1);
