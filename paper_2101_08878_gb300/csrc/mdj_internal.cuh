@@ -184,7 +184,10 @@ inline int dtype_width(int32_t dt) {
 }
 
 // Every temporary buffer of one call, from the caller's allocator (or
-// cudaMallocAsync), released in stream order when the call ends.
+// cudaMallocAsync), released in stream order when the call ends.  Requests of
+// at most kArenaMax bytes are carved from kArenaChunk-byte chunks (one
+// allocator call per chunk, not per buffer; give_back of such a piece is a
+// no-op until the call ends), larger ones are allocated one by one.
 class Workspace {
  public:
   Workspace(const mdj_allocator *a, cudaStream_t s) : alloc_(a), stream_(s) {}
@@ -211,6 +214,10 @@ class Workspace {
   cudaStream_t stream_;
   std::vector<void *> owned_;
   int *flag_ = nullptr;
+  unsigned char *arena_ = nullptr;  // current chunk
+  size_t arena_used_ = 0;
+  static constexpr size_t kArenaMax = 1u << 20;
+  static constexpr size_t kArenaChunk = 8u << 20;
 };
 
 // Launch tracing (mdj_profile_*): events around each launch when enabled.

@@ -803,24 +803,30 @@ template <typename KeyT>
 int run_join(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, mdj_result *res,
              bool force_ordered = false, ItemMap *map = nullptr) {
   cudaStream_t s = ws.stream();
+  // the optimistic output buffer first: its allocation overlaps the device
+  // work still queued, before make_items waits for the item count
+  const uint64_t cap_rows = output_capacity_hint(Ls.nrows, Rs.nrows);
+  mdj_result r;
+  JOut o;
+  MDJ_TRY(alloc_result(ws, Ls, Rs, sizeof(KeyT), cap_rows, &r, &o));
   Item *desc;
   uint32_t nitems;
-  MDJ_TRY(make_items(ws, Ls, Rs, plan.nbuckets, plan.cap, kWriteChunk, &desc, &nitems,
-                     map ? &map->bucket_items : nullptr));
+  int rc = make_items(ws, Ls, Rs, plan.nbuckets, plan.cap, kWriteChunk, &desc, &nitems,
+                      map ? &map->bucket_items : nullptr);
   // state[nitems] | item_off[nitems] | total | ticket | flags
   const size_t words = 2 * (size_t)nitems + 4;
-  unsigned long long *state = (unsigned long long *)ws.get(words * 8);
-  if (!state) return MDJ_ERR_OOM;
-  MDJ_CUDA_TRY(cudaMemsetAsync(state, 0, words * 8, s));
+  unsigned long long *state = rc == MDJ_OK ? (unsigned long long *)ws.get(words * 8) : nullptr;
+  if (rc == MDJ_OK && !state) rc = MDJ_ERR_OOM;
+  if (rc == MDJ_OK) rc = cuda_status(cudaMemsetAsync(state, 0, words * 8, s));
+  if (rc != MDJ_OK) {
+    mdj_result_release(&r, ws.allocator(), (void *)s);
+    return rc;
+  }
   uint64_t *item_off = (uint64_t *)(state + nitems);
   unsigned long long *total = state + 2 * (size_t)nitems;
   uint32_t *ticket = (uint32_t *)(total + 1);
   int *flags = (int *)(total + 2);
 
-  const uint64_t cap_rows = output_capacity_hint(Ls.nrows, Rs.nrows);
-  mdj_result r;
-  JOut o;
-  MDJ_TRY(alloc_result(ws, Ls, Rs, sizeof(KeyT), cap_rows, &r, &o));
   const size_t sm = WriteLayout<KeyT>(plan.cap).total;  // ~105 KB at cap 4096: two blocks per SM
   if (nitems) {
     int grid;

@@ -550,21 +550,18 @@ __global__ void __launch_bounds__(kPT, 2)
 // The merge needs every row in its sub-bucket, not the input order inside a
 // bucket, so its shuffle drops stability (the public partition keeps it):
 //
-//   k_tot      rows per final sub-bucket, and rows per (pass-1 bucket, slab)
-//              where slab s is a contiguous range of tiles (shared counters;
-//              the next chunk's keys load while the current one is counted)
-//   k_shuffle  tiles of 4096 rows: every column of a row is loaded before the
-//              tile is processed (the next tile's while the current one is
-//              written out), a row's rank in its bucket is a shared-memory
-//              atomic, and the columns are staged in bucket order and leave
-//              as runs; three block barriers per tile.
-//              Pass 1: block s walks slab s and keeps one cursor per bucket
-//              in shared memory, starting at the scanned (bucket, slab)
-//              counts, so no two blocks share a cursor.
+//   k_tot      rows per final sub-bucket (shared counters, flushed with one
+//              global add per counter); the next chunk's keys load while the
+//              current chunk is counted
+//   k_shuffle  persistent blocks over tiles of 4096 rows: every column of a
+//              row is loaded before the tile is processed (the next tile's
+//              while the current one is written out), a row's rank in its
+//              bucket is a shared-memory atomic, each (tile, bucket) run is
+//              reserved with one global atomicAdd on the bucket's cursor, and
+//              the columns are staged in bucket order and leave as runs;
+//              three block barriers per tile.
 //              PASS2: rows already grouped by pass-1 bucket (sub-bucket / F2)
-//              are split into their sub-buckets; each (tile, sub-bucket) run
-//              is reserved with one global atomicAdd, as in k_scatter's
-//              RESERVE (thousands of cursors, so atomics rarely collide).
+//              are split into their sub-buckets, as in k_scatter's RESERVE.
 // A pass-1 bucket holds the rows of sub-buckets [b * F2, (b + 1) * F2)
 // (pass-1 bucket = sub-bucket / F2, see BucketSpec), so the scanned counts
 // of the final sub-buckets also place the pass-1 buckets.
@@ -580,59 +577,37 @@ template <int NT>
 __host__ __device__ constexpr uint32_t shuffle_span() { return 2u * NT; }
 template <int NT>
 constexpr size_t shuffle_smem_bytes() {
-  return (size_t)shuffle_tile<NT>() * (8 + 8 + 4 + 4) + (size_t)shuffle_span<NT>() * 12 + 40 * 4;
-}
-
-// First tile of slab s when ntiles tiles are cut into NS slabs.
-__host__ __device__ __forceinline__ uint32_t slab_lo(uint32_t s, uint32_t ntiles, uint32_t NS) {
-  return (uint32_t)((uint64_t)s * ntiles / NS);
+  return (size_t)shuffle_tile<NT>() * (8 + 8 + 4 + 4) + (size_t)shuffle_span<NT>() * 8 + 40 * 4;
 }
 
 template <typename KeyT>
-__device__ __forceinline__ void tot_load(const KeyT *__restrict__ keys, uint64_t base, uint64_t end,
-                                         KeyT (&v)[kTotU]) {
+__device__ __forceinline__ void tot_load(const KeyT *__restrict__ keys, uint64_t base, uint32_t n, KeyT (&v)[kTotU]) {
 #pragma unroll
   for (int u = 0; u < kTotU; u++) {
     const uint64_t r = base + (uint64_t)u * kTotThreads + threadIdx.x;
-    v[u] = r < end ? keys[r] : KeyT(0);
+    v[u] = r < n ? keys[r] : KeyT(0);
   }
 }
 
-// tot[sb] += rows of sub-bucket sb (spec bs, nsub = P * S); slab_cnt[b * NS +
-// s] = rows of slab s (tiles of `tile` rows) in pass-1 bucket b = p * S1 +
-// floor(hi32(h) * S1 / 2^32), b < F1.  Block b counts slabs b, b + gridDim.x, ...
+// tot[sb] += rows of sub-bucket sb (spec bs, nsub = P * S).
 template <typename KeyT>
-__global__ void __launch_bounds__(kTotThreads)
-    k_tot(const KeyT *__restrict__ keys, uint32_t n, BucketSpec bs, uint32_t nsub, uint32_t *__restrict__ tot,
-          uint32_t S1, uint32_t F1, uint32_t tile, uint32_t ntiles, uint32_t NS, uint32_t *__restrict__ slab_cnt) {
+__global__ void __launch_bounds__(kTotThreads) k_tot(const KeyT *__restrict__ keys, uint32_t n, BucketSpec bs,
+                                                     uint32_t nsub, uint32_t *__restrict__ tot) {
   extern __shared__ uint32_t cnt[];
-  uint32_t *c1 = cnt + nsub;
   for (uint32_t i = threadIdx.x; i < nsub; i += kTotThreads) cnt[i] = 0;
-  const uint64_t chunk = (uint64_t)kTotThreads * kTotU;
-  for (uint32_t s = blockIdx.x; s < NS; s += gridDim.x) {
-    for (uint32_t i = threadIdx.x; i < F1; i += kTotThreads) c1[i] = 0;
-    __syncthreads();
-    const uint64_t lo = (uint64_t)slab_lo(s, ntiles, NS) * tile;
-    const uint64_t hi_t = (uint64_t)slab_lo(s + 1, ntiles, NS) * tile;
-    const uint64_t hi = hi_t < n ? hi_t : n;
-    KeyT cur[kTotU], nxt[kTotU];
-    tot_load<KeyT>(keys, lo, hi, cur);
-    for (uint64_t base = lo; base < hi; base += chunk) {
-      tot_load<KeyT>(keys, base + chunk, hi, nxt);
+  __syncthreads();
+  const uint64_t chunk = (uint64_t)kTotThreads * kTotU, stride = chunk * gridDim.x;
+  uint64_t base = chunk * blockIdx.x;
+  KeyT cur[kTotU], nxt[kTotU];
+  tot_load<KeyT>(keys, base, n, cur);
+  for (; base < n; base += stride) {
+    tot_load<KeyT>(keys, base + stride, n, nxt);
 #pragma unroll
-      for (int u = 0; u < kTotU; u++) {
-        const uint64_t r = base + (uint64_t)u * kTotThreads + threadIdx.x;
-        if (r < hi) {
-          const uint64_t h = fmix64(key_bits(cur[u]));
-          const uint32_t p = mod_p(h, bs), x = (uint32_t)(h >> 32);
-          atomicAdd(&cnt[p * bs.S + __umulhi(x, bs.S)], 1u);
-          atomicAdd(&c1[p * S1 + __umulhi(x, S1)], 1u);
-        }
-        cur[u] = nxt[u];
-      }
+    for (int u = 0; u < kTotU; u++) {
+      const uint64_t r = base + (uint64_t)u * kTotThreads + threadIdx.x;
+      if (r < n) atomicAdd(&cnt[sub_bucket_of(fmix64(key_bits(cur[u])), bs)], 1u);
+      cur[u] = nxt[u];
     }
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < F1; i += kTotThreads) slab_cnt[(size_t)i * NS + s] = c1[i];
   }
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < nsub; i += kTotThreads)
@@ -699,8 +674,8 @@ __device__ __forceinline__ void shuffle_load(const KeyT *__restrict__ keys, uint
 template <int NT, typename KeyT, bool PASS2, bool EXTRA>
 __global__ void __launch_bounds__(NT, 1024 / NT)
     k_shuffle(const KeyT *__restrict__ keys, uint32_t n, uint32_t ntiles, BucketSpec bs, uint32_t F, uint32_t F2,
-              uint32_t *__restrict__ cursors, const uint32_t *__restrict__ slab_base, uint32_t NS, ColMove cm,
-              int reg_col, const uint32_t *__restrict__ rid_in, uint32_t *__restrict__ rid_out) {
+              uint32_t *__restrict__ cursors, ColMove cm, int reg_col, const uint32_t *__restrict__ rid_in,
+              uint32_t *__restrict__ rid_out) {
   constexpr uint32_t kFTile = shuffle_tile<NT>(), kFSpan = shuffle_span<NT>();
   constexpr int kFT = NT;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -710,8 +685,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
   uint32_t *dstmap = sr + kFTile;
   uint32_t *lstart = dstmap + kFTile;
   uint32_t *gbase = lstart + kFSpan;
-  uint32_t *scur = gbase + kFSpan;
-  uint32_t *scratch = scur + kFSpan;
+  uint32_t *scratch = gbase + kFSpan;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int pw = reg_col >= 0 ? cm.width[reg_col] : 0;
@@ -719,15 +693,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
   uint64_t pv[kRPL];
   uint32_t rv[kRPL];
   KeyT kfirst = KeyT(0), klast = KeyT(0);
-  // slab mode (slab_base given, pass 1 only): the tiles of slab blockIdx.x in
-  // order; otherwise tiles blockIdx.x + k * gridDim.x with global cursors
-  const bool slab = !PASS2 && slab_base != nullptr;
-  uint32_t t = slab ? slab_lo(blockIdx.x, ntiles, NS) : blockIdx.x;
-  const uint32_t tend = slab ? slab_lo(blockIdx.x + 1, ntiles, NS) : ntiles;
-  const uint32_t tstep = slab ? 1u : gridDim.x;
+  uint32_t t = blockIdx.x;
+  const uint32_t tend = ntiles, tstep = gridDim.x;
   if (t >= tend) return;
-  if (slab)
-    for (uint32_t b = threadIdx.x; b < F; b += kFT) scur[b] = slab_base[(size_t)b * NS + blockIdx.x];
   shuffle_load<NT, KeyT, PASS2>(keys, n, t, cm, reg_col, pw, rid_in, kv, pv, rv, kfirst, klast);
 
   while (t < tend) {
@@ -767,23 +735,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
     }
     __syncthreads();
 
-    // 2. place every non-empty run (two buckets per thread), scan the counts
+    // 2. reserve every non-empty run (two buckets per thread), scan the counts
     const uint32_t b0 = 2 * threadIdx.x, b1 = b0 + 1;
     const uint32_t c0 = b0 < Floc ? cnt[b0] : 0u, c1 = b1 < Floc ? cnt[b1] : 0u;
-    uint32_t g0 = 0, g1 = 0;
-    if (!slab) {
-      g0 = c0 ? atomicAdd(&cursors[lb0 + b0], c0) : 0u;
-      g1 = c1 ? atomicAdd(&cursors[lb0 + b1], c1) : 0u;
-    } else {
-      if (b0 < Floc) {
-        g0 = scur[b0];
-        scur[b0] = g0 + c0;
-      }
-      if (b1 < Floc) {
-        g1 = scur[b1];
-        scur[b1] = g1 + c1;
-      }
-    }
+    const uint32_t g0 = c0 ? atomicAdd(&cursors[lb0 + b0], c0) : 0u;
+    const uint32_t g1 = c1 ? atomicAdd(&cursors[lb0 + b1], c1) : 0u;
     uint32_t total;
     const uint32_t ex = block_exclusive_scan<uint32_t>(c0 + c1, scratch, &total);
     if (b0 < Floc) {
@@ -1060,30 +1016,31 @@ int reserve_pass(Workspace &ws, const KeyT *keys, uint32_t n, const BucketSpec &
   return MDJ_OK;
 }
 
-// Buffers of one partitioned copy of a table.
+// Buffers of one partitioned copy of a table: every column and the row ids
+// carved from one allocation (each part 256-byte aligned).
 struct TableBufs {
   void *cols[MDJ_MAX_COLS];
   uint32_t *rid;
+  void *block;
 };
 
 int alloc_table_bufs(Workspace &ws, const mdj_table *t, TableBufs *b, bool with_rid) {
   const size_t n = t->nrows;
+  auto part = [](size_t bytes) { return (bytes + 255) & ~(size_t)255; };
+  size_t total = with_rid ? part(n * 4) : 0;
+  for (int j = 0; j < t->ncols; j++) total += part(n * dtype_width(t->cols[j].dtype));
+  b->block = ws.get(total ? total : 256);
+  if (!b->block) return MDJ_ERR_OOM;
+  unsigned char *p = (unsigned char *)b->block;
   for (int j = 0; j < t->ncols; j++) {
-    b->cols[j] = ws.get(n * dtype_width(t->cols[j].dtype));
-    if (!b->cols[j]) return MDJ_ERR_OOM;
+    b->cols[j] = p;
+    p += part(n * dtype_width(t->cols[j].dtype));
   }
-  b->rid = nullptr;
-  if (with_rid) {
-    b->rid = (uint32_t *)ws.get(n * 4);
-    if (!b->rid) return MDJ_ERR_OOM;
-  }
+  b->rid = with_rid ? (uint32_t *)p : nullptr;
   return MDJ_OK;
 }
 
-void release_table_bufs(Workspace &ws, const mdj_table *t, TableBufs *b) {
-  for (int j = 0; j < t->ncols; j++) ws.give_back(b->cols[j]);
-  if (b->rid) ws.give_back(b->rid);
-}
+void release_table_bufs(Workspace &ws, const mdj_table *, TableBufs *b) { ws.give_back(b->block); }
 
 ColMove make_move(const mdj_table *t, int32_t key_col, const void *const *src, void *const *dst) {
   ColMove cm;
@@ -1106,13 +1063,6 @@ bool fast_shuffle_enabled() {
   return !(e && e[0] == '1');
 }
 
-// MDJ_SLAB_CURSORS=1: pass 1 walks contiguous slabs with private cursors
-// (measured slower on GB300 than shared atomic cursors; kept for study).
-bool slab_mode() {
-  const char *e = getenv("MDJ_SLAB_CURSORS");
-  return e && e[0] == '1';
-}
-
 template <typename KeyT>
 int set_shuffle_attrs() {
   static bool done = false;
@@ -1124,7 +1074,7 @@ int set_shuffle_attrs() {
   MDJ_CUDA_TRY(cudaFuncSetAttribute(k_shuffle<NT, KeyT, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   MDJ_CUDA_TRY(cudaFuncSetAttribute(k_shuffle<NT, KeyT, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   MDJ_CUDA_TRY(cudaFuncSetAttribute(k_tot<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)((kMaxSubBuckets + kMaxFanout) * 4)));
+                                    (int)(kMaxSubBuckets * 4)));
   done = true;
   return MDJ_OK;
 }
@@ -1148,13 +1098,11 @@ int shuffle_grid(bool pass2, bool extra, uint32_t ntiles, uint32_t *grid) {
   return MDJ_OK;
 }
 
-// One unstable shuffle pass (see k_shuffle) of n rows on `grid` blocks.
-// Pass 1 takes slab bases (F buckets x NS = grid slabs, bucket-major);
-// pass 2 takes run cursors per sub-bucket.
+// One unstable shuffle pass (see k_shuffle) of n rows on `grid` blocks with
+// run cursors `cur` (pass 1: one per pass-1 bucket; pass 2: one per sub-bucket).
 template <typename KeyT, bool PASS2>
 int shuffle_pass(Workspace &ws, const KeyT *keys, uint32_t n, uint32_t grid, const BucketSpec &bs, uint32_t F,
-                 uint32_t F2, uint32_t *cur, const uint32_t *slab_base, const ColMove &cm, const uint32_t *rid_in,
-                 uint32_t *rid_out) {
+                 uint32_t F2, uint32_t *cur, const ColMove &cm, const uint32_t *rid_in, uint32_t *rid_out) {
   constexpr int NT = kShuffleNT;
   const uint32_t ntiles = (n + shuffle_tile<NT>() - 1) / shuffle_tile<NT>();
   if (ntiles == 0) return MDJ_OK;
@@ -1163,14 +1111,13 @@ int shuffle_pass(Workspace &ws, const KeyT *keys, uint32_t n, uint32_t grid, con
     if (j != cm.key_index) reg_col = j;
   TraceScope tr(PASS2 ? "scatter_reserve" : "scatter_stable", ws.stream());
   shuffle_kernel<KeyT>(PASS2, cm.n > 2)<<<grid, NT, shuffle_smem_bytes<NT>(), ws.stream()>>>(
-      keys, n, ntiles, bs, F, F2, cur, slab_base, grid, cm, reg_col, rid_in, rid_out);
+      keys, n, ntiles, bs, F, F2, cur, cm, reg_col, rid_in, rid_out);
   MDJ_LAUNCH_CHECK();
   return MDJ_OK;
 }
 
 // The merge's partition of one side with the unstable passes: count the
-// final sub-buckets and the (pass-1 bucket, slab) rows, scan both, then one
-// pass (F2 == 1) or two.
+// final sub-buckets, scan them into `off`, then one pass (F2 == 1) or two.
 template <typename KeyT>
 int shuffle_side_t(Workspace &ws, const mdj_table *t, int32_t key_col, const Plan &plan, uint32_t *off,
                    TableBufs *fin) {
@@ -1183,58 +1130,53 @@ int shuffle_side_t(Workspace &ws, const mdj_table *t, int32_t key_col, const Pla
   for (int j = 0; j < t->ncols; j++) src[j] = t->cols[j].data;
   const KeyT *keys = (const KeyT *)src[key_col];
   const BucketSpec sub = make_spec(plan.P, plan.S, 1);
-  const BucketSpec p1spec = make_spec(plan.P, plan.S, plan.F2);
   const bool extra = t->ncols > 2;
-  const uint32_t tile = shuffle_tile<kShuffleNT>();
-  const uint32_t ntiles = (n + tile - 1) / tile;
+  const uint32_t ntiles = (n + shuffle_tile<kShuffleNT>() - 1) / shuffle_tile<kShuffleNT>();
 
   MDJ_CUDA_TRY(cudaMemsetAsync(off, 0, (size_t)(nsub + 1) * 4, s));
   MDJ_TRY(alloc_table_bufs(ws, t, fin, true));
   if (n == 0) return MDJ_OK;
-  uint32_t NS = 0;
-  MDJ_TRY(shuffle_grid<KeyT>(false, extra, ntiles, &NS));
-  const bool slabs = slab_mode();
-  uint32_t *slab = (uint32_t *)ws.get(((size_t)F1 * NS + 1) * 4);
   uint32_t *cur = (uint32_t *)ws.get((size_t)(nsub + 1) * 4);
-  if (!slab || !cur) return MDJ_ERR_OOM;
+  if (!cur) return MDJ_ERR_OOM;
   {
-    const size_t smem = (size_t)(nsub + F1) * 4;
+    const size_t smem = (size_t)nsub * 4;
     int per_sm = 0;
     MDJ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tot<KeyT>, kTotThreads, smem));
     if (per_sm < 1) per_sm = 1;
-    const uint32_t full = (uint32_t)(num_sms() * per_sm);
-    const uint32_t grid = NS < full ? NS : full;
+    const uint64_t chunks = ((uint64_t)n + (uint64_t)kTotThreads * kTotU - 1) / ((uint64_t)kTotThreads * kTotU);
+    const uint64_t full = (uint64_t)num_sms() * per_sm;
+    const unsigned grid = (unsigned)(chunks < full ? chunks : full);
     TraceScope tr("hist", s);
-    k_tot<KeyT><<<grid, kTotThreads, smem, s>>>(keys, n, sub, nsub, off, p1spec.S1, F1, tile, ntiles, NS, slab);
+    k_tot<KeyT><<<grid, kTotThreads, smem, s>>>(keys, n, sub, nsub, off);
   }
   MDJ_LAUNCH_CHECK();
   MDJ_TRY(exclusive_scan_u32(ws, off, off, (size_t)nsub + 1));
-  MDJ_TRY(exclusive_scan_u32(ws, slab, slab, (size_t)F1 * NS));
-  if (!slabs) {
+  {
     // pass-1 cursors: the first row of every pass-1 bucket
     TraceScope tr("pass1_cursors", s);
     k_pass1_cursors<<<(F1 + 255) / 256, 256, 0, s>>>(off, F1, plan.F2, cur);
   }
   MDJ_LAUNCH_CHECK();
-  const uint32_t *sb = slabs ? slab : nullptr;
+  uint32_t grid1 = 0;
+  MDJ_TRY(shuffle_grid<KeyT>(false, extra, ntiles, &grid1));
   if (plan.F2 == 1) {
     ColMove cm = make_move(t, key_col, src, fin->cols);
-    MDJ_TRY((shuffle_pass<KeyT, false>(ws, keys, n, NS, sub, nsub, 1, cur, sb, cm, nullptr, fin->rid)));
+    MDJ_TRY((shuffle_pass<KeyT, false>(ws, keys, n, grid1, sub, nsub, 1, cur, cm, nullptr, fin->rid)));
   } else {
     TableBufs p1;
     MDJ_TRY(alloc_table_bufs(ws, t, &p1, true));
     ColMove cm1 = make_move(t, key_col, src, p1.cols);
-    MDJ_TRY((shuffle_pass<KeyT, false>(ws, keys, n, NS, p1spec, F1, plan.F2, cur, sb, cm1, nullptr, p1.rid)));
+    MDJ_TRY((shuffle_pass<KeyT, false>(ws, keys, n, grid1, make_spec(plan.P, plan.S, plan.F2), F1, plan.F2, cur,
+                                       cm1, nullptr, p1.rid)));
     MDJ_CUDA_TRY(cudaMemcpyAsync(cur, off, (size_t)nsub * 4, cudaMemcpyDeviceToDevice, s));
     uint32_t grid2 = 0;
     MDJ_TRY(shuffle_grid<KeyT>(true, extra, ntiles, &grid2));
     ColMove cm2 = make_move(t, key_col, p1.cols, fin->cols);
-    MDJ_TRY((shuffle_pass<KeyT, true>(ws, (const KeyT *)p1.cols[key_col], n, grid2, sub, 0, plan.F2, cur, nullptr,
-                                      cm2, p1.rid, fin->rid)));
+    MDJ_TRY((shuffle_pass<KeyT, true>(ws, (const KeyT *)p1.cols[key_col], n, grid2, sub, 0, plan.F2, cur, cm2,
+                                      p1.rid, fin->rid)));
     release_table_bufs(ws, t, &p1);
   }
   ws.give_back(cur);
-  ws.give_back(slab);
   return MDJ_OK;
 }
 

@@ -36,6 +36,19 @@ void Workspace::raw_free(void *p) {
 }
 
 void *Workspace::get(size_t bytes) {
+  if (bytes <= kArenaMax) {
+    const size_t need = ((bytes ? bytes : 1) + 255) & ~(size_t)255;
+    if (!arena_ || arena_used_ + need > kArenaChunk) {
+      void *c = raw_alloc(kArenaChunk);
+      if (!c) return nullptr;
+      owned_.push_back(c);
+      arena_ = (unsigned char *)c;
+      arena_used_ = 0;
+    }
+    void *p = arena_ + arena_used_;
+    arena_used_ += need;
+    return p;
+  }
   void *p = raw_alloc(bytes);
   if (p) owned_.push_back(p);
   return p;
@@ -65,6 +78,8 @@ void Workspace::release_all() {
   for (size_t i = owned_.size(); i-- > 0;) raw_free(owned_[i]);
   owned_.clear();
   flag_ = nullptr;
+  arena_ = nullptr;
+  arena_used_ = 0;
 }
 
 // ------------------------------------------------------------------- helpers
