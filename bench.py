@@ -158,6 +158,22 @@ def cpu_baseline(n_sample: int, reps: int = 1):
 
 # --------------------------------------------------------------- GPU arm
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over all ranks (x itself when there is one rank): the
+    job's time is its slowest replica's."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(rows_per_rank: int, world: int, seconds: float) -> float:
+    """Rows merged by all replicas per second of the slowest one."""
+    return rows_per_rank * world / seconds
+
+
 def alg_bytes_per_launch(kernel: str, n_side: int, n_left: int, n_right: int, m: int):
     """Bytes the method must move in one launch of `kernel` (8-byte keys and
     payloads, 4-byte row ids); None for kernels outside the model."""
@@ -224,14 +240,10 @@ def run_gpu(args):
         barrier()
     mdj.profile_enable(False)
     prof = mdj.profile_collect()
-    ms_total = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     ms_step = ms_total / args.steps
     rows_step = (N_LEFT + N_RIGHT) * world
-    value = rows_step / (ms_step / 1e3)
+    value = whole_job_rate(N_LEFT + N_RIGHT, world, ms_step / 1e3)
 
     # ---- roofline: dominant kernel by total device time inside the timed region
     peak, peak_kind = peaks()
@@ -273,12 +285,8 @@ def run_gpu(args):
             assert out.nrows == m_expect
             del out
         torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) / args.e2e_steps
-        if dist is not None:
-            t = torch.tensor([dt], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": rows_step / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+        dt = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, dist, dev)
+        e2e = {"value": whole_job_rate(N_LEFT + N_RIGHT, world, dt), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": round(dt * 1e3, 3), "steps": args.e2e_steps}
 
     if rank != 0:
