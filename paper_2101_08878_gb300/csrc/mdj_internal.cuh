@@ -271,6 +271,20 @@ Plan make_plan(uint64_t n_build, uint32_t P, uint32_t cap, bool force_partition)
 int partition_side(Workspace &ws, const mdj_table *t, int32_t key_col, const Plan &plan,
                    Side *out);
 
+// Two-level merge plans (F2 > 1, unstable passes) in two halves, for the
+// fused pass-2 + join path: pass 1 leaves `p1` (rows grouped by pass-1
+// bucket, off = final sub-bucket offsets: pass-1 bucket b holds sub-buckets
+// [b * F2, (b + 1) * F2)); pass 2 produces the final side from it.
+struct Side1 {
+  Side p1;                              // pass-1 copy: key, non-key columns, row ids, final offsets
+  const void *all_cols[MDJ_MAX_COLS];   // the same columns in table order
+  void *block;                          // the pass-1 allocation
+};
+bool merge_shuffle_unstable();  // false under MDJ_STABLE_SHUFFLE=1
+int partition_side_pass1(Workspace &ws, const mdj_table *t, int32_t key_col, const Plan &plan, Side1 *out);
+int partition_side_pass2(Workspace &ws, const mdj_table *t, int32_t key_col, const Plan &plan, const Side1 &in,
+                         Side *out);
+
 // Segmented partition of a batch: segment i = rows [seg_off[i], seg_off[i+1])
 // (host array) is split into seg_nb[i] = P_i * S_i buckets numbered from
 // seg_base[i]: bucket p * S_i + floor(hi32(h) * S_i / 2^32), p = h mod P_i,

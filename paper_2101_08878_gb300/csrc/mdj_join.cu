@@ -26,47 +26,13 @@
 #include <string.h>
 
 #include "mdj_internal.cuh"
+#include "mdj_join_dev.cuh"
+#include "mdj_shuffle_dev.cuh"
 #include "mdj_tma.cuh"
 
 namespace mdj {
 namespace {
 
-constexpr int kJoinThreads = 512;
-constexpr int kPF = 8;                                   // probe rows per thread per round
-constexpr uint32_t kWriteChunk = kPF * kJoinThreads;     // probe rows per write item (one round)
-constexpr uint32_t kCountChunk = 65536;                  // probe rows per count item
-constexpr uint32_t kDefaultCap = 4096;
-constexpr uint32_t kMaxCap = 8192;      // write-pass table: 8-byte keys fit 227 KB of shared memory
-constexpr uint32_t kCountCapMax = 4096;  // count/checksum table (per-slot counts and sums)
-constexpr uint64_t kWaitLimitNs = 1000000000ull;         // look-back wait bound: 1 s of device time
-constexpr uint32_t kPollLimit = 1u << 26;                // and a poll-count bound as a backstop
-constexpr uint64_t kFlagAgg = 1ull << 62, kFlagInc = 2ull << 62, kValMask = (1ull << 62) - 1;
-
-struct JSide {
-  const void *key;
-  const uint32_t *rid;  // NULL: identity
-  const uint32_t *off;  // bucket offsets [nbuckets + 1]
-  const void *cols[MDJ_MAX_COLS];
-  int32_t width[MDJ_MAX_COLS];
-  int32_t ncols;
-};
-
-struct JOut {
-  void *key;
-  uint32_t *lrow;
-  uint32_t *rrow;
-  void *lcols[MDJ_MAX_COLS];
-  void *rcols[MDJ_MAX_COLS];
-};
-
-struct Item {
-  uint32_t lbeg, nl, rbeg, nr;
-};
-
-// flags[] words shared by the join kernels and the host
-enum { FLAG_OVERFLOW = 0, FLAG_TIMEOUT = 1, FLAG_ABORT = 2, FLAG_WORDS = 4 };
-
-__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 template <typename KeyT>
 size_t join_smem_bytes(uint32_t cap, bool fsum) {
@@ -301,173 +267,17 @@ __global__ void __launch_bounds__(kJoinThreads, 2)
   }
 }
 
-// ------------------------------------------------------------ fused write
-
-// Exclusive output offset of item `it` whose own count is `total`: publish the
-// count, then walk back over predecessors until one whose inclusive prefix is
-// known.  Bounded: after kWaitLimitNs (or kPollLimit polls) the wait is
-// abandoned, FLAG_TIMEOUT and FLAG_ABORT are set (other waiters then stop
-// too) and ~0 is returned.  `withhold_first` (test hook) keeps item 0 from
-// publishing, so that every later wait runs out.
-__device__ uint64_t look_back(unsigned long long *state, uint32_t it, uint64_t total, int *flags,
-                              int withhold_first) {
-  volatile unsigned long long *vs = state;
-  if (it == 0) {
-    if (withhold_first) return ~0ull;
-    __threadfence();
-    atomicExch(&state[0], kFlagInc | total);
-    return 0;
-  }
-  __threadfence();
-  atomicExch(&state[it], kFlagAgg | total);
-  uint64_t excl = 0;
-  uint32_t j = it - 1;
-  uint32_t polls = 0;
-  const uint64_t t0 = globaltimer_ns();
-  for (;;) {
-    const unsigned long long v = vs[j];
-    const uint64_t flag = v & ~kValMask;
-    if (flag == 0) {
-      if (++polls > kPollLimit || globaltimer_ns() - t0 > kWaitLimitNs || ((volatile int *)flags)[FLAG_ABORT]) {
-        atomicExch(&flags[FLAG_TIMEOUT], 1);
-        atomicExch(&flags[FLAG_ABORT], 1);
-        return ~0ull;
-      }
-      __nanosleep(64);
-      continue;
-    }
-    excl += v & kValMask;
-    if (flag == kFlagInc || j == 0) break;
-    j--;
-  }
-  __threadfence();
-  atomicExch(&state[it], kFlagInc | (excl + total));
-  return excl;
-}
-
-// ------------------------------------------------------------ fused write
-//
-// Two 512-thread blocks per SM.  Per item:
-//   1. the build chunk's keys, row ids and first payload column go to shared
-//      memory by asynchronous copies (cp.async) while the probe keys load
-//      into registers and the table heads are cleared;
-//   2. build: a chained table, heads[slot] -> row, nxt[row] -> row, one
-//      atomicExch per build row (no probing loop, no compare-and-swap);
-//   3. probe: walk the key's chain; first match and match count per row;
-//   4. the row ids and first payload of matching probe rows are loaded, so
-//      their latency overlaps the offset computation;
-//   5. offsets: rows with one match are ordered by (round j, warp, lane), so
-//      the matching lanes of one warp store consecutive output rows (ballot +
-//      popc); rows with several matches follow, each expanded by its thread;
-//      the item's range is reserved (atomicAdd) or looked back (ordered);
-//   6. write: build-side values from shared memory, probe-side from registers.
-// The next item's ticket and descriptor are fetched while the current one runs.
-
-constexpr int kWT = 512;                        // threads of the write block
-constexpr int kWPF = 8;                         // probe rows per thread
-constexpr int kWW = kWT / 32;                   // warps of the write block
-static_assert(kWPF * kWT == (int)kWriteChunk, "probe chunk = one round");
-
-template <typename KeyT>
-struct WriteLayout {
-  size_t keys, rid, pay, heads, nxt, cnt1, total;
-  uint32_t tsz;  // chain heads of the largest table (>= cap: mean chain length <= 1)
-  __host__ __device__ WriteLayout(uint32_t cap) {
-    tsz = 32;
-    while (tsz < cap) tsz *= 2;
-    keys = 0;
-    rid = align16((size_t)cap * sizeof(KeyT));
-    pay = align16(rid + (size_t)cap * 4);
-    heads = align16(pay + (size_t)cap * 8);
-    nxt = heads + (size_t)tsz * 4;
-    cnt1 = align16(nxt + (size_t)cap * 2);
-    total = cnt1 + (size_t)kWPF * kWW * 4;
-  }
-};
-
-// Chain-head slot of a key: 32-bit fold, one multiply, top logt bits.
-__device__ __forceinline__ uint32_t chain_slot(uint64_t kb, uint32_t logt) {
-  const uint32_t f = (uint32_t)kb ^ (uint32_t)(kb >> 32);
-  return (f * 0x9E3779B1u) >> (32 - logt);
-}
-
-__device__ __forceinline__ void cp_async_4(void *dst, const void *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(__cvta_generic_to_global(src))
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_8(void *dst, const void *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(__cvta_generic_to_global(src))
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-}
-
-// Non-key columns after the first of each side (gathered from global memory).
-__device__ __forceinline__ void copy_extra_cols(const JSide &L, const JSide &R, const JOut &out, uint64_t pos,
-                                                uint32_t lrow, uint32_t r) {
-  for (int cc = 1; cc < L.ncols; cc++) {
-    if (L.width[cc] == 8)
-      ((uint64_t *)out.lcols[cc])[pos] = ((const uint64_t *)L.cols[cc])[lrow];
-    else
-      ((uint32_t *)out.lcols[cc])[pos] = ((const uint32_t *)L.cols[cc])[lrow];
-  }
-  for (int cc = 1; cc < R.ncols; cc++) {
-    if (R.width[cc] == 8)
-      ((uint64_t *)out.rcols[cc])[pos] = ((const uint64_t *)R.cols[cc])[r];
-    else
-      ((uint32_t *)out.rcols[cc])[pos] = ((const uint32_t *)R.cols[cc])[r];
-  }
-}
-
-// One output row: build row li of the staged chunk, probe row r with row id
-// rr and first payload rp.
-template <typename KeyT>
-__device__ __forceinline__ void write_row(const JSide &L, const JSide &R, const JOut &out, uint64_t pos,
-                                          const KeyT *bkey, const uint32_t *brid, const uint64_t *bpay, uint32_t li,
-                                          uint32_t lbeg, uint32_t r, uint32_t rr, uint64_t rp) {
-  ((KeyT *)out.key)[pos] = bkey[li];
-  out.lrow[pos] = brid[li];
-  out.rrow[pos] = rr;
-  if (L.ncols > 0) {
-    if (L.width[0] == 8)
-      ((uint64_t *)out.lcols[0])[pos] = bpay[li];
-    else
-      ((uint32_t *)out.lcols[0])[pos] = (uint32_t)bpay[li];
-  }
-  if (R.ncols > 0) {
-    if (R.width[0] == 8)
-      ((uint64_t *)out.rcols[0])[pos] = rp;
-    else
-      ((uint32_t *)out.rcols[0])[pos] = (uint32_t)rp;
-  }
-  if (L.ncols > 1 || R.ncols > 1) copy_extra_cols(L, R, out, pos, lbeg + li, r);
-}
-
 template <typename KeyT, bool HAVE_OFFSETS>
 __global__ void __launch_bounds__(kWT, 2)
     k_join_write(JSide L, JSide R, const Item *__restrict__ desc, uint32_t nitems, uint32_t cap, uint32_t *ticket,
                  unsigned long long *state, uint64_t *__restrict__ item_off, unsigned long long *total,
                  uint64_t capacity, int *flags, int withhold_first, int ordered, JOut out) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const WriteLayout<KeyT> lay(cap);
-  KeyT *bkey = (KeyT *)(smem + lay.keys);
-  uint32_t *brid = (uint32_t *)(smem + lay.rid);
-  uint64_t *bpay = (uint64_t *)(smem + lay.pay);
-  uint32_t *heads = (uint32_t *)(smem + lay.heads);
-  uint16_t *nxt = (uint16_t *)(smem + lay.nxt);
-  uint32_t *cnt1 = (uint32_t *)(smem + lay.cnt1);
   __shared__ Item s_item;
-  __shared__ uint32_t s_it, s_single;
-  __shared__ uint64_t s_base;
-  __shared__ uint64_t scratch64[33];
-
-  const KeyT *__restrict__ Lkey = (const KeyT *)L.key;
-  const KeyT *__restrict__ Rkey = (const KeyT *)R.key;
-  const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int lpw = L.ncols > 0 ? L.width[0] : 0;
-  const int rpw = R.ncols > 0 ? R.width[0] : 0;
-
+  __shared__ uint32_t s_it;
+  __shared__ JoinShared js;
+  const uint32_t tid = threadIdx.x;
+  const Resv rs = {state, item_off, total, capacity, flags, withhold_first, ordered};
   if (tid == 0) {
     s_it = atomicAdd(ticket, 1u);
     if (s_it < nitems) s_item = desc[s_it];
@@ -484,157 +294,7 @@ __global__ void __launch_bounds__(kWT, 2)
       nx = atomicAdd(ticket, 1u);
       if (nx < nitems) dn = desc[nx];
     }
-
-    // 1. stage the build chunk; probe keys to registers; clear the heads
-    for (uint32_t i = tid; i < d.nl; i += kWT) {
-      const uint32_t g = d.lbeg + i;
-      if (sizeof(KeyT) == 8)
-        cp_async_8(&bkey[i], &Lkey[g]);
-      else
-        cp_async_4(&bkey[i], &Lkey[g]);
-      if (L.rid)
-        cp_async_4(&brid[i], &L.rid[g]);
-      else
-        brid[i] = g;
-      if (lpw == 8) cp_async_8(&bpay[i], &((const uint64_t *)L.cols[0])[g]);
-      if (lpw == 4) cp_async_4(&bpay[i], &((const uint32_t *)L.cols[0])[g]);
-    }
-    KeyT rk[kWPF];
-#pragma unroll
-    for (int j = 0; j < kWPF; j++) {
-      const uint32_t rl = j * kWT + tid;
-      rk[j] = rl < d.nr ? Rkey[d.rbeg + rl] : KeyT(0);
-    }
-    uint32_t logt = 5;
-    while ((1u << logt) < d.nl) logt++;
-    const uint32_t tsz = 1u << logt;
-    {
-      const uint4 z = make_uint4(0, 0, 0, 0);
-      for (uint32_t s = tid * 4; s < tsz; s += kWT * 4) *(uint4 *)(heads + s) = z;
-    }
-    cp_async_wait_all();
-    __syncthreads();
-
-    // 2. build: push every row onto its slot's chain
-    for (uint32_t i = tid; i < d.nl; i += kWT) {
-      const uint32_t s = chain_slot(key_bits(bkey[i]), logt);
-      nxt[i] = (uint16_t)atomicExch(&heads[s], i + 1);
-    }
-    __syncthreads();
-
-    // 3. probe: ch[j] = (matches << 16) | (first matching row + 1)
-    uint32_t ch[kWPF];
-    uint32_t nm = 0;
-#pragma unroll
-    for (int j = 0; j < kWPF; j++) {
-      ch[j] = 0;
-      if (j * kWT + tid < d.nr) {
-        const KeyT k = rk[j];
-        uint32_t li = heads[chain_slot(key_bits(k), logt)], first = 0, c = 0;
-        while (li) {
-          if (bkey[li - 1] == k) {
-            if (!c) first = li;
-            c++;
-          }
-          li = nxt[li - 1];
-        }
-        ch[j] = (c << 16) | first;
-        if (c >= 2) nm += c;
-      }
-    }
-
-    // 4. probe-side row id and first payload of every matching row
-    uint32_t rr[kWPF];
-    uint64_t rp[kWPF];
-#pragma unroll
-    for (int j = 0; j < kWPF; j++) {
-      rr[j] = 0;
-      rp[j] = 0;
-      if (ch[j]) {
-        const uint32_t r = d.rbeg + j * kWT + tid;
-        rr[j] = R.rid ? R.rid[r] : r;
-        if (rpw == 8) rp[j] = ((const uint64_t *)R.cols[0])[r];
-        if (rpw == 4) rp[j] = ((const uint32_t *)R.cols[0])[r];
-      }
-    }
-
-    // 5. offsets: single-match rows by (j, warp, lane), then the rest
-#pragma unroll
-    for (int j = 0; j < kWPF; j++) {
-      const uint32_t bal = __ballot_sync(0xffffffffu, (ch[j] >> 16) == 1);
-      if (lane == 0) cnt1[j * kWW + warp] = __popc(bal);
-    }
-    uint64_t mtot;
-    const uint64_t mex = block_exclusive_scan<uint64_t>(nm, scratch64, &mtot);  // barriers inside
-    if (warp == 0) {
-      constexpr int per = kWPF * kWW / 32;
-      uint32_t v[per], sum = 0;
-#pragma unroll
-      for (int q = 0; q < per; q++) {
-        v[q] = cnt1[lane * per + q];
-        sum += v[q];
-      }
-      const uint32_t inc = warp_inclusive_scan(sum);
-      uint32_t run = inc - sum;
-#pragma unroll
-      for (int q = 0; q < per; q++) {
-        cnt1[lane * per + q] = run;
-        run += v[q];
-      }
-      if (lane == 31) s_single = inc;
-    }
-    __syncthreads();
-    const uint32_t S = s_single;
-    const uint64_t item_total = S + mtot;
-    if (tid == 0) {
-      uint64_t base;
-      if (HAVE_OFFSETS) {
-        base = item_off[it];
-      } else {
-        if (ordered) {
-          base = look_back(state, it, item_total, flags, withhold_first);
-          if (base != ~0ull && item_total) atomicAdd(total, (unsigned long long)item_total);
-        } else {
-          base = item_total ? atomicAdd(total, (unsigned long long)item_total) : 0ull;
-        }
-        if (base != ~0ull) {
-          item_off[it] = base;
-          if (base + item_total > capacity) atomicExch(&flags[FLAG_OVERFLOW], 1);
-        }
-      }
-      s_base = base;
-    }
-    __syncthreads();
-
-    // 6. write
-    const uint64_t base = s_base;
-    if (base != ~0ull && base + item_total <= capacity) {
-#pragma unroll
-      for (int j = 0; j < kWPF; j++) {
-        const bool one = (ch[j] >> 16) == 1;
-        const uint32_t bal = __ballot_sync(0xffffffffu, one);
-        if (one) {
-          const uint64_t pos = base + cnt1[j * kWW + warp] + __popc(bal & lanemask_lt());
-          write_row<KeyT>(L, R, out, pos, bkey, brid, bpay, (ch[j] & 0xFFFFu) - 1, d.lbeg, d.rbeg + j * kWT + tid,
-                          rr[j], rp[j]);
-        }
-      }
-      if (nm) {
-        uint64_t pos = base + S + mex;
-#pragma unroll
-        for (int j = 0; j < kWPF; j++) {
-          if ((ch[j] >> 16) < 2) continue;
-          uint32_t li = ch[j] & 0xFFFFu;
-          const KeyT k = bkey[li - 1];
-          while (li) {
-            if (bkey[li - 1] == k)
-              write_row<KeyT>(L, R, out, pos++, bkey, brid, bpay, li - 1, d.lbeg, d.rbeg + j * kWT + tid, rr[j],
-                              rp[j]);
-            li = nxt[li - 1];
-          }
-        }
-      }
-    }
+    join_item<KeyT, HAVE_OFFSETS>(smem, cap, L, R, d, it, rs, out, js);
     if (tid == 0) {
       s_it = nx;
       if (nx < nitems) s_item = dn;
@@ -881,6 +541,444 @@ int run_join(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, md
   return MDJ_OK;
 }
 
+// ------------------------------------------------- fused pass 2 + join
+//
+// For a two-level plan the pass-2 copy of every side is written once and read
+// once by the join.  k_fused keeps it in L2 instead: pass-1 bucket w (a
+// "wave") is split by pass 2 into scratch slot w % kFuseSlots, and its join
+// items read the slot right after.  One persistent kernel runs both kinds of
+// work units, taken in a fixed order from one ticket:
+//   P2(0), P2(1), ..., P2(lag - 1), then P2(w), J(w - lag) for w = lag.. ,
+// where P2(w) = the pass-2 tiles of wave w (left side, then right side) and
+// J(w) = the join items of wave w.  J(w) waits until every P2(w) tile is done;
+// P2(w) waits until every J(w - kFuseSlots) item is done (its slot is free).
+// Each wait is on units with smaller tickets, all held by running blocks, so
+// the order cannot deadlock; every wait is still bounded (kFuseWaitNs of
+// %globaltimer time, then FLAG_TIMEOUT + FLAG_ABORT and the block stops).
+// Join units read the slot through L2 only (join_item's COHERENT mode).
+
+constexpr uint32_t kFuseSlots = 4;
+constexpr uint32_t kFuseLag = 2;
+constexpr uint64_t kFuseWaitNs = 2000000000ull;
+constexpr uint32_t kFuseTile = shuffle_tile<kShuffleNT>();
+static_assert(kFuseLag < kFuseSlots, "a wave's slot is reused only after its items ran");
+
+struct FuseWave {
+  uint32_t row0[2], rows[2];  // the wave's rows on each side (pass-1 order = final region)
+  uint32_t tiles[2];          // pass-2 tiles per side
+  uint32_t item0, nitems;     // its join items
+};
+
+// Scratch columns of one side in one slot: key, first payload, row ids.
+struct FuseSideSlot {
+  size_t key, pay, rid;  // byte offsets in the side's part of a slot
+  size_t bytes;          // the side's part of a slot
+};
+
+struct FuseArgs {
+  const ColMove *moves;   // [slot][side]: pass-1 copy -> the slot's scratch columns
+  const JSide *jsides;    // [slot][side]: the slot's scratch columns as join sides
+  const FuseWave *waves;
+  const uint32_t *seg_start;  // first unit of each segment (2 * (F1 + lag) + 1 entries)
+  uint32_t nseg, F1, F2;
+  const Item *desc;
+  uint32_t *ticket;
+  uint32_t *p2_done, *j_done;  // per wave
+  uint32_t *cursors[2];        // absolute sub-bucket cursors per side
+  const void *p1_key[2], *p1_pay[2];
+  const uint32_t *p1_rid[2];
+  int key_w, pay_w[2];         // widths (pay_w 0: no payload column)
+  unsigned char *slots;
+  size_t slot_bytes;
+  FuseSideSlot side[2];
+  BucketSpec sub;
+  uint32_t cap;
+};
+
+// Thread 0 waits until *ctr >= target; false when the wait ran out or another
+// block gave up.
+__device__ bool fuse_wait(const uint32_t *ctr, uint32_t target, int *flags) {
+  volatile const uint32_t *v = ctr;
+  if (*v >= target) {
+    __threadfence();
+    return true;
+  }
+  const uint64_t t0 = globaltimer_ns();
+  while (*v < target) {
+    if (((volatile int *)flags)[FLAG_ABORT]) return false;
+    if (globaltimer_ns() - t0 > kFuseWaitNs) {
+      atomicExch(&flags[FLAG_TIMEOUT], 1);
+      atomicExch(&flags[FLAG_ABORT], 1);
+      return false;
+    }
+    __nanosleep(200);
+  }
+  __threadfence();
+  return true;
+}
+
+// The waves, the unit order (segment starts) and the largest wave per side
+// (out[0], out[1]) and the unit count (out[2]); one block of 1024 threads.
+__global__ void __launch_bounds__(1024)
+    k_fuse_plan(const uint32_t *__restrict__ offL, const uint32_t *__restrict__ offR,
+                const uint64_t *__restrict__ bucket_items, uint32_t F1, uint32_t F2, FuseWave *__restrict__ waves,
+                uint32_t *__restrict__ seg_start, uint32_t *__restrict__ out) {
+  __shared__ uint32_t scratch[40];
+  __shared__ uint32_t mx[2];
+  if (threadIdx.x < 2) mx[threadIdx.x] = 0;
+  __syncthreads();
+  for (uint32_t w = threadIdx.x; w < F1; w += blockDim.x) {
+    FuseWave v;
+    const uint32_t a = w * F2, b = (w + 1) * F2;
+    v.row0[0] = offL[a];
+    v.rows[0] = offL[b] - offL[a];
+    v.row0[1] = offR[a];
+    v.rows[1] = offR[b] - offR[a];
+    v.tiles[0] = (v.rows[0] + kFuseTile - 1) / kFuseTile;
+    v.tiles[1] = (v.rows[1] + kFuseTile - 1) / kFuseTile;
+    v.item0 = (uint32_t)bucket_items[a];
+    v.nitems = (uint32_t)(bucket_items[b] - bucket_items[a]);
+    waves[w] = v;
+    atomicMax(&mx[0], v.rows[0]);
+    atomicMax(&mx[1], v.rows[1]);
+  }
+  __syncthreads();
+  // segment sizes in unit order, then an in-place exclusive scan
+  const uint32_t nseg = 2 * (F1 + kFuseLag);
+  for (uint32_t s = threadIdx.x; s <= nseg; s += blockDim.x) {
+    const uint32_t q = s / 2;
+    uint32_t size = 0;
+    if (s == nseg) {
+      size = 0;
+    } else if (s % 2 == 0) {
+      if (q < F1) size = waves[q].tiles[0] + waves[q].tiles[1];
+    } else if (q >= kFuseLag && q - kFuseLag < F1) {
+      size = waves[q - kFuseLag].nitems;
+    }
+    seg_start[s] = size;
+  }
+  __syncthreads();
+  block_scan_array(seg_start, nseg + 1, scratch);  // seg_start[nseg] = units (its input was 0)
+  if (threadIdx.x == 0) {
+    out[0] = mx[0];
+    out[1] = mx[1];
+    out[2] = seg_start[nseg];
+  }
+}
+
+// Segment of unit u (the last s with seg_start[s] <= u) and u's index in it.
+__device__ __forceinline__ void fuse_decode(const FuseArgs &a, uint32_t u, uint32_t *seg, uint32_t *local) {
+  uint32_t lo = 0, hi = a.nseg - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) / 2;
+    if (a.seg_start[mid] <= u)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  *seg = lo;
+  *local = u - a.seg_start[lo];
+}
+
+// The counter a unit of segment `seg` waits for and its target (ctr = NULL:
+// no wait): items of wave w wait for its pass-2 tiles, pass-2 tiles of wave
+// w >= kFuseSlots for the items of wave w - kFuseSlots.
+__device__ __forceinline__ const uint32_t *fuse_dep(const FuseArgs &a, uint32_t seg, uint32_t *target) {
+  const uint32_t q = seg / 2;
+  if (seg % 2 == 0) {
+    if (q < kFuseSlots) return nullptr;
+    *target = a.waves[q - kFuseSlots].nitems;
+    return &a.j_done[q - kFuseSlots];
+  }
+  const FuseWave &wv = a.waves[q - kFuseLag];
+  *target = wv.tiles[0] + wv.tiles[1];
+  return &a.p2_done[q - kFuseLag];
+}
+
+// Thread 0: the unit's dependency already met (one read, no waiting)?
+__device__ __forceinline__ int fuse_ready_now(const FuseArgs &a, uint32_t seg) {
+  uint32_t target = 0;
+  const uint32_t *ctr = fuse_dep(a, seg, &target);
+  if (!ctr) return 1;
+  if (*(volatile const uint32_t *)ctr < target) return 0;
+  __threadfence();
+  return 1;
+}
+
+template <typename KeyT>
+__global__ void __launch_bounds__(kShuffleNT, 2)
+    k_fused(FuseArgs a, Resv rs, JOut out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ JoinShared js;
+  __shared__ uint32_t s_unit, s_seg, s_local;
+  __shared__ int s_ready, s_ok;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t nunits = a.seg_start[a.nseg];
+  // the block's first unit; every later one is fetched while the previous
+  // unit runs, and decoded and checked while the block finishes it
+  if (tid == 0) {
+    s_unit = atomicAdd(a.ticket, 1u);
+    if (s_unit < nunits) {
+      fuse_decode(a, s_unit, &s_seg, &s_local);
+      s_ready = fuse_ready_now(a, s_seg);
+    }
+  }
+  __syncthreads();
+  for (;;) {
+    const uint32_t u = s_unit;
+    if (u >= nunits) break;
+    const uint32_t seg = s_seg, local = s_local;
+    const int ready = s_ready;
+    uint32_t nx = 0;
+    if (tid == 0) nx = atomicAdd(a.ticket, 1u);
+    if (!ready) {  // s_ready was read by every thread above; the wait reports in s_ok
+      if (tid == 0) {
+        uint32_t target = 0;
+        const uint32_t *ctr = fuse_dep(a, seg, &target);
+        s_ok = fuse_wait(ctr, target, rs.flags);
+      }
+      __syncthreads();
+      if (!s_ok) break;
+    }
+    const uint32_t q = seg / 2;
+    uint32_t w;
+    if (seg % 2 == 0) {
+      // ---- a pass-2 tile of wave q
+      w = q;
+      const FuseWave wv = a.waves[w];
+      const int side = local < wv.tiles[0] ? 0 : 1;
+      const uint32_t k = side ? local - wv.tiles[0] : local;
+      const uint32_t row0 = wv.row0[side] + k * kFuseTile;
+      const uint32_t rend = min(row0 + kFuseTile, wv.row0[side] + wv.rows[side]);
+      const ColMove &cm = a.moves[(w % kFuseSlots) * 2 + side];
+      const int reg_col = a.pay_w[side] ? 1 : -1;
+      KeyT kv[kRPL];
+      uint64_t pv[kRPL];
+      uint32_t rv[kRPL];
+      KeyT kf, kl;
+      const KeyT *keys = (const KeyT *)a.p1_key[side];
+      shuffle_load<KeyT, true>(keys, row0, rend, cm, reg_col, a.pay_w[side], a.p1_rid[side], kv, pv, rv, kf, kl);
+      shuffle_one_tile<kShuffleNT, KeyT, true, false>(smem, keys, row0, rend, w * a.F2, a.F2, a.sub,
+                                                      a.cursors[side], wv.row0[side], cm, reg_col, a.pay_w[side],
+                                                      a.p1_rid[side], (uint32_t *)cm.dst[2], kv, pv, rv, 0u, 0u, kf,
+                                                      kl);
+    } else {
+      // ---- a join item of wave q - lag
+      w = q - kFuseLag;
+      const FuseWave wv = a.waves[w];
+      const uint32_t it = wv.item0 + local;
+      Item d = a.desc[it];
+      d.lbeg -= wv.row0[0];
+      d.rbeg -= wv.row0[1];
+      const JSide *jside = a.jsides + (w % kFuseSlots) * 2;
+      join_item<KeyT, false, true>(smem, a.cap, jside[0], jside[1], d, it, rs, out, js);
+    }
+    uint32_t nseg = 0, nlocal = 0;
+    int nready = 0;
+    if (tid == 0 && nx < nunits) {
+      fuse_decode(a, nx, &nseg, &nlocal);
+      nready = fuse_ready_now(a, nseg);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      atomicAdd(seg % 2 == 0 ? &a.p2_done[w] : &a.j_done[w], 1u);
+      s_unit = nx;
+      s_seg = nseg;
+      s_local = nlocal;
+      s_ready = nready;
+    }
+    __syncthreads();
+  }
+}
+
+// Resident blocks of k_fused (grid), and its dynamic shared memory.
+template <typename KeyT>
+int fused_launch_shape(uint32_t cap, size_t *smem, int *grid) {
+  const size_t a = shuffle_smem_bytes<kShuffleNT>(), b = WriteLayout<KeyT>(cap).total;
+  *smem = a > b ? a : b;
+  int per_sm = 0;
+  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_fused<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem));
+  MDJ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<KeyT>, kShuffleNT, *smem));
+  if (per_sm < 1) return MDJ_ERR_INTERNAL;
+  *grid = num_sms() * per_sm;
+  return MDJ_OK;
+}
+
+// MDJ_FUSED=1 turns the fused pass-2 + join path on.  Measured on GB300 for
+// the 100M x 100M merge it is slower than pass 2 + k_join_write (5.1-5.7 vs
+// 3.3 ms): join units wait on pass-2 tiles still in flight, and the slot
+// ring (4 x 16 MB) does not stay in L2 beside the streaming traffic.
+bool fused_enabled() {
+  const char *e = getenv("MDJ_FUSED");
+  return e && e[0] == '1';
+}
+
+constexpr size_t kFuseSlotBudget = 1ull << 30;  // scratch bytes at most (else the unfused path)
+
+// The fused pass 2 + join of a two-level plan from both sides' pass-1 copies.
+// *fallback = true (and no result) when the scratch would exceed its budget
+// or the output outgrew the optimistic buffer: the caller then runs pass 2
+// and the join separately.
+template <typename KeyT>
+int run_fused(Workspace &ws, const Side1 &L1, const Side1 &R1, const Plan &plan, mdj_result *res, bool *fallback) {
+  cudaStream_t s = ws.stream();
+  *fallback = false;
+  const Side &Ls = L1.p1, &Rs = R1.p1;
+  const uint32_t nb = plan.nbuckets, F1 = plan.F1, F2 = plan.F2;
+  const uint64_t cap_rows = output_capacity_hint(Ls.nrows, Rs.nrows);
+  mdj_result r;
+  JOut o;
+  MDJ_TRY(alloc_result(ws, Ls, Rs, sizeof(KeyT), cap_rows, &r, &o));
+  auto fail = [&](int rc) {
+    mdj_result_release(&r, ws.allocator(), (void *)s);
+    return rc;
+  };
+  // items per final sub-bucket, the waves and the unit order
+  uint64_t *bucket_items = (uint64_t *)ws.get((size_t)(nb + 1) * 8);
+  const uint32_t nseg = 2 * (F1 + kFuseLag);
+  FuseWave *waves = (FuseWave *)ws.get((size_t)F1 * sizeof(FuseWave));
+  uint32_t *seg = (uint32_t *)ws.get((size_t)(nseg + 1) * 4);
+  uint32_t *pout = (uint32_t *)ws.get(16);
+  if (!bucket_items || !waves || !seg || !pout) return fail(MDJ_ERR_OOM);
+  {
+    TraceScope tr("join_items", s);
+    k_items<<<(nb + 1 + 255) / 256, 256, 0, s>>>(Ls.off, Rs.off, nb, plan.cap, kWriteChunk, bucket_items);
+  }
+  if (cudaGetLastError() != cudaSuccess) return fail(MDJ_ERR_CUDA);
+  int rc = exclusive_scan_u64(ws, bucket_items, bucket_items, nb + 1);
+  if (rc != MDJ_OK) return fail(rc);
+  {
+    TraceScope tr("fuse_plan", s);
+    k_fuse_plan<<<1, 1024, 0, s>>>(Ls.off, Rs.off, bucket_items, F1, F2, waves, seg, pout);
+  }
+  uint64_t nitems = 0;
+  uint32_t hp[4] = {0, 0, 0, 0};
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&nitems, bucket_items + nb, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hp, pout, 12, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(cuda_status(e));
+  if (nitems >= (1ull << 31)) return fail(MDJ_ERR_TOO_LARGE);
+
+  FuseArgs a;
+  memset(&a, 0, sizeof a);
+  a.key_w = (int)sizeof(KeyT);
+  const Side *sd[2] = {&Ls, &Rs};
+  const uint32_t maxrows[2] = {hp[0], hp[1]};
+  auto part = [](size_t bytes) { return (bytes + 255) & ~(size_t)255; };
+  for (int i = 0; i < 2; i++) {
+    a.pay_w[i] = sd[i]->ncols ? sd[i]->widths[0] : 0;
+    a.side[i].key = 0;
+    a.side[i].pay = part((size_t)maxrows[i] * sizeof(KeyT));
+    a.side[i].rid = a.side[i].pay + part((size_t)maxrows[i] * (a.pay_w[i] ? a.pay_w[i] : 0));
+    a.side[i].bytes = a.side[i].rid + part((size_t)maxrows[i] * 4);
+    a.p1_key[i] = sd[i]->key;
+    a.p1_pay[i] = sd[i]->ncols ? sd[i]->cols[0] : nullptr;
+    a.p1_rid[i] = sd[i]->rid;
+  }
+  a.slot_bytes = a.side[0].bytes + a.side[1].bytes;
+  if (a.slot_bytes * kFuseSlots > kFuseSlotBudget || nitems == 0) {
+    mdj_result_release(&r, ws.allocator(), (void *)s);
+    *fallback = true;
+    return MDJ_OK;
+  }
+  Item *desc = (Item *)ws.get((size_t)nitems * sizeof(Item));
+  a.slots = (unsigned char *)ws.get(a.slot_bytes * kFuseSlots);
+  // p2_done[F1] | j_done[F1] | ticket | cursors L[nb] | cursors R[nb]
+  const size_t cwords = 2 * (size_t)F1 + 1 + 2 * (size_t)nb;
+  uint32_t *cw = (uint32_t *)ws.get(cwords * 4);
+  // item_off[nitems] | total | flags
+  unsigned long long *st = (unsigned long long *)ws.get(((size_t)nitems + 3) * 8);
+  if (!desc || !a.slots || !cw || !st) return fail(MDJ_ERR_OOM);
+  {
+    TraceScope tr("join_expand", s);
+    const uint64_t want = (nitems + 255) / 256, most = (uint64_t)num_sms() * 8;
+    k_expand<<<(unsigned)(want < most ? want : most), 256, 0, s>>>(Ls.off, Rs.off, nb, plan.cap, kWriteChunk,
+                                                                   bucket_items, (uint32_t)nitems, desc);
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemsetAsync(cw, 0, (2 * (size_t)F1 + 1) * 4, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cw + 2 * F1 + 1, Ls.off, (size_t)nb * 4, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cw + 2 * F1 + 1 + nb, Rs.off, (size_t)nb * 4, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, ((size_t)nitems + 3) * 8, s);
+  if (e != cudaSuccess) return fail(cuda_status(e));
+  // per (slot, side): the pass-2 column move (key, payload, and the row ids
+  // as dst[2]) and the join side over the slot's scratch columns
+  ColMove hm[kFuseSlots * 2];
+  JSide hj[kFuseSlots * 2];
+  memset(hm, 0, sizeof hm);
+  memset(hj, 0, sizeof hj);
+  for (uint32_t k = 0; k < kFuseSlots; k++)
+    for (int i = 0; i < 2; i++) {
+      unsigned char *base = a.slots + (size_t)k * a.slot_bytes + (i ? a.side[0].bytes : 0);
+      ColMove &m = hm[k * 2 + i];
+      m.n = a.pay_w[i] ? 2 : 1;
+      m.key_index = 0;
+      m.src[0] = a.p1_key[i];
+      m.dst[0] = base + a.side[i].key;
+      m.width[0] = (int)sizeof(KeyT);
+      m.src[1] = a.p1_pay[i];
+      m.dst[1] = base + a.side[i].pay;
+      m.width[1] = a.pay_w[i];
+      m.dst[2] = base + a.side[i].rid;
+      JSide &j = hj[k * 2 + i];
+      j.key = base + a.side[i].key;
+      j.rid = (const uint32_t *)(base + a.side[i].rid);
+      j.cols[0] = base + a.side[i].pay;
+      j.width[0] = a.pay_w[i];
+      j.ncols = a.pay_w[i] ? 1 : 0;
+    }
+  ColMove *dm = (ColMove *)ws.get(sizeof hm);
+  JSide *dj = (JSide *)ws.get(sizeof hj);
+  if (!dm || !dj) return fail(MDJ_ERR_OOM);
+  e = cudaMemcpyAsync(dm, hm, sizeof hm, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dj, hj, sizeof hj, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return fail(cuda_status(e));
+  a.moves = dm;
+  a.jsides = dj;
+  a.waves = waves;
+  a.seg_start = seg;
+  a.nseg = nseg;
+  a.F1 = F1;
+  a.F2 = F2;
+  a.desc = desc;
+  a.p2_done = cw;
+  a.j_done = cw + F1;
+  a.ticket = cw + 2 * F1;
+  a.cursors[0] = cw + 2 * F1 + 1;
+  a.cursors[1] = cw + 2 * F1 + 1 + nb;
+  a.sub = make_spec(plan.P, plan.S, 1);
+  a.cap = plan.cap;
+  unsigned long long *total = st + nitems;
+  int *flags = (int *)(st + nitems + 1);
+  const Resv rs = {nullptr, (uint64_t *)st, total, cap_rows, flags, 0, 0};
+  size_t smem = 0;
+  int grid = 0;
+  rc = fused_launch_shape<KeyT>(plan.cap, &smem, &grid);
+  if (rc != MDJ_OK) return fail(rc);
+  {
+    TraceScope tr("fused_p2_join", s);
+    k_fused<KeyT><<<grid, kShuffleNT, smem, s>>>(a, rs, o);
+  }
+  unsigned long long host_total = 0;
+  int host_flags[FLAG_WORDS] = {0, 0, 0, 0};
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&host_total, total, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host_flags, flags, sizeof host_flags, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(cuda_status(e));
+  if (host_flags[FLAG_TIMEOUT]) return fail(MDJ_ERR_DEVICE_TIMEOUT);
+  if (host_total > cap_rows) {
+    mdj_result_release(&r, ws.allocator(), (void *)s);
+    *fallback = true;
+    return MDJ_OK;
+  }
+  r.nrows = host_total;
+  *res = r;
+  return MDJ_OK;
+}
+
 // pair_off[i] = output offset of pair i's first item (or of the next pair's,
 // for a pair without items); pair_off[npairs] = total rows.
 __global__ void k_pair_offsets(const uint32_t *__restrict__ seg_base, uint32_t npairs, uint32_t nb,
@@ -936,10 +1034,25 @@ int merge_impl(const mdj_table *left, int32_t lk, const mdj_table *right, int32_
   Plan plan = make_plan(left->nrows, P, cap_from_env(), P > 1);
   // ordered output is deterministic only over stable partition passes
   plan.stable = ordered_output() != 0;
+  const bool k64 = left->cols[lk].dtype == MDJ_I64;
+  if (!checksum_mode && fused_enabled() && merge_shuffle_unstable() && plan.partition && !plan.lsd &&
+      !plan.stable && plan.F2 > 1 && left->ncols <= 2 && right->ncols <= 2) {
+    // two-level plan: pass 2 and the join fused through L2-resident scratch
+    Side1 L1, R1;
+    MDJ_TRY(partition_side_pass1(ws, left, lk, plan, &L1));
+    MDJ_TRY(partition_side_pass1(ws, right, rk, plan, &R1));
+    bool fallback = false;
+    MDJ_TRY(k64 ? run_fused<int64_t>(ws, L1, R1, plan, out, &fallback)
+                : run_fused<int32_t>(ws, L1, R1, plan, out, &fallback));
+    if (!fallback) return MDJ_OK;
+    Side L, R;
+    MDJ_TRY(partition_side_pass2(ws, left, lk, plan, L1, &L));
+    MDJ_TRY(partition_side_pass2(ws, right, rk, plan, R1, &R));
+    return k64 ? run_join<int64_t>(ws, L, R, plan, out) : run_join<int32_t>(ws, L, R, plan, out);
+  }
   Side L, R;
   MDJ_TRY(partition_side(ws, left, lk, plan, &L));
   MDJ_TRY(partition_side(ws, right, rk, plan, &R));
-  const bool k64 = left->cols[lk].dtype == MDJ_I64;
   if (checksum_mode)
     return k64 ? run_count<int64_t>(ws, L, R, plan, count, checksum) : run_count<int32_t>(ws, L, R, plan, count, checksum);
   return k64 ? run_join<int64_t>(ws, L, R, plan, out) : run_join<int32_t>(ws, L, R, plan, out);

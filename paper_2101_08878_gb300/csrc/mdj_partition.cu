@@ -19,23 +19,14 @@
 #include <string.h>
 
 #include "mdj_internal.cuh"
+#include "mdj_shuffle_dev.cuh"
 #include "mdj_tma.cuh"
 
 namespace mdj {
 namespace {
 
-constexpr int kNW = 16;                     // warps per scatter block
-constexpr int kRPL = 8;                     // rows per lane per tile
-constexpr uint32_t kTile = kNW * 32 * kRPL; // 4096 rows per tile
 constexpr int kHistThreads = 512;
 
-struct ColMove {
-  const void *src[MDJ_MAX_COLS];
-  void *dst[MDJ_MAX_COLS];
-  int32_t width[MDJ_MAX_COLS];
-  int32_t n;
-  int32_t key_index;
-};
 
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
@@ -95,39 +86,6 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(const KeyT *__restrict__ 
 }
 
 // --------------------------------------------------------------- k_scatter
-
-// Direct path of a pass-2 tile whose rows span too many buckets for shared
-// memory (tiny or very skewed pass-1 buckets): warp-aggregated reservation,
-// each row written straight to its slot.
-template <typename KeyT>
-__device__ void scatter_direct(const KeyT (&kv)[kRPL], uint32_t wrow0, uint32_t rend, const BucketSpec &bs,
-                               uint32_t *__restrict__ cursors, const ColMove &cm,
-                               const uint32_t *__restrict__ rid_in, uint32_t *__restrict__ rid_out) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll 1
-  for (int c = 0; c < kRPL; c++) {
-    uint32_t r = wrow0 + c * 32 + lane;
-    bool valid = r < rend;
-    uint32_t fb = valid ? sub_bucket_of(fmix64(key_bits(kv[c])), bs) : 0xFFFFFFFFu;
-    uint32_t peers = __match_any_sync(0xffffffffu, fb);
-    int leader = __ffs(peers) - 1;
-    uint32_t base = 0;
-    if (valid && lane == leader) base = atomicAdd(&cursors[fb], (uint32_t)__popc(peers));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (!valid) continue;
-    uint32_t pos = base + __popc(peers & lanemask_lt());
-    for (int j = 0; j < cm.n; j++) {
-      if (cm.width[j] == 8) {
-        uint64_t v = j == cm.key_index ? (uint64_t)kv[c] : ((const uint64_t *)cm.src[j])[r];
-        ((uint64_t *)cm.dst[j])[pos] = v;
-      } else {
-        uint32_t v = j == cm.key_index ? (uint32_t)kv[c] : ((const uint32_t *)cm.src[j])[r];
-        ((uint32_t *)cm.dst[j])[pos] = v;
-      }
-    }
-    if (rid_out) rid_out[pos] = rid_in ? rid_in[r] : r;
-  }
-}
 
 // SEG (with RESERVE): tiles come from `seg_tiles` and never cross a segment;
 // a segment with P_seg partitions of S_seg sub-buckets each puts a row in its
@@ -568,18 +526,6 @@ __global__ void __launch_bounds__(kPT, 2)
 
 constexpr int kTotThreads = 1024;
 constexpr int kTotU = 8;                        // keys per thread per chunk
-// k_shuffle: NT threads, tiles of NT * kRPL rows, at most 2 * NT local
-// buckets per tile, 1024 / NT blocks per SM.
-constexpr int kShuffleNT = 512;
-template <int NT>
-__host__ __device__ constexpr uint32_t shuffle_tile() { return (uint32_t)NT * kRPL; }
-template <int NT>
-__host__ __device__ constexpr uint32_t shuffle_span() { return 2u * NT; }
-template <int NT>
-constexpr size_t shuffle_smem_bytes() {
-  return (size_t)shuffle_tile<NT>() * (8 + 8 + 4 + 4) + (size_t)shuffle_span<NT>() * 8 + 40 * 4;
-}
-
 template <typename KeyT>
 __device__ __forceinline__ void tot_load(const KeyT *__restrict__ keys, uint64_t base, uint32_t n, KeyT (&v)[kTotU]) {
 #pragma unroll
@@ -621,49 +567,6 @@ __global__ void k_pass1_cursors(const uint32_t *__restrict__ off, uint32_t F1, u
   if (b < F1) cur[b] = off[(size_t)b * F2];
 }
 
-// scatter_direct for k_shuffle, reading the keys again from memory so that
-// the caller's key registers need no addressable copy.
-template <typename KeyT>
-__device__ __noinline__ void shuffle_direct(const KeyT *__restrict__ keys, uint32_t wrow0, uint32_t rend,
-                                            const BucketSpec &bs, uint32_t *__restrict__ cursors, const ColMove &cm,
-                                            const uint32_t *__restrict__ rid_in, uint32_t *__restrict__ rid_out) {
-  KeyT kv[kRPL];
-#pragma unroll
-  for (int c = 0; c < kRPL; c++) {
-    const uint32_t r = wrow0 + c * 32 + (threadIdx.x & 31);
-    kv[c] = r < rend ? keys[r] : KeyT(0);
-  }
-  scatter_direct<KeyT>(kv, wrow0, rend, bs, cursors, cm, rid_in, rid_out);
-}
-
-// Loads the carried columns of tile t into registers: warp w holds rows
-// row0 + w*256 + c*32 + lane (c < kRPL), the layout scatter_direct uses.
-// PASS2 also fetches the tile's first and last key (its pass-1 bucket span).
-template <int NT, typename KeyT, bool PASS2>
-__device__ __forceinline__ void shuffle_load(const KeyT *__restrict__ keys, uint32_t n, uint32_t t, const ColMove &cm,
-                                             int reg_col, int pw, const uint32_t *__restrict__ rid_in,
-                                             KeyT (&kv)[kRPL], uint64_t (&pv)[kRPL], uint32_t (&rv)[kRPL],
-                                             KeyT &kfirst, KeyT &klast) {
-  const uint32_t row0 = t * shuffle_tile<NT>();
-  const uint32_t rend = min(row0 + shuffle_tile<NT>(), n);
-  const uint32_t wrow0 = row0 + (threadIdx.x >> 5) * 32 * kRPL;
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int c = 0; c < kRPL; c++) {
-    const uint32_t r = wrow0 + c * 32 + lane;
-    const bool ok = r < rend;
-    kv[c] = ok ? keys[r] : KeyT(0);
-    pv[c] = 0;
-    if (ok && pw == 8) pv[c] = ((const uint64_t *)cm.src[reg_col])[r];
-    if (ok && pw == 4) pv[c] = ((const uint32_t *)cm.src[reg_col])[r];
-    rv[c] = rid_in ? (ok ? rid_in[r] : 0u) : r;
-  }
-  if (PASS2) {
-    kfirst = keys[row0];
-    klast = keys[rend - 1];
-  }
-}
-
 // Persistent: block b takes tiles b, b + gridDim.x, ...  Once a tile is
 // staged its registers are free, so the next tile's columns are loaded into
 // them before the staged tile is written out; the DRAM latency of the load
@@ -677,17 +580,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
               uint32_t *__restrict__ cursors, ColMove cm, int reg_col, const uint32_t *__restrict__ rid_in,
               uint32_t *__restrict__ rid_out) {
   constexpr uint32_t kFTile = shuffle_tile<NT>(), kFSpan = shuffle_span<NT>();
-  constexpr int kFT = NT;
   extern __shared__ __align__(16) unsigned char smem[];
-  KeyT *sk = (KeyT *)smem;
-  uint64_t *sp = (uint64_t *)(smem + (size_t)kFTile * 8);
-  uint32_t *sr = (uint32_t *)(smem + (size_t)kFTile * 16);
-  uint32_t *dstmap = sr + kFTile;
-  uint32_t *lstart = dstmap + kFTile;
-  uint32_t *gbase = lstart + kFSpan;
-  uint32_t *scratch = gbase + kFSpan;
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
   const int pw = reg_col >= 0 ? cm.width[reg_col] : 0;
   KeyT kv[kRPL];
   uint64_t pv[kRPL];
@@ -696,15 +590,13 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
   uint32_t t = blockIdx.x;
   const uint32_t tend = ntiles, tstep = gridDim.x;
   if (t >= tend) return;
-  shuffle_load<NT, KeyT, PASS2>(keys, n, t, cm, reg_col, pw, rid_in, kv, pv, rv, kfirst, klast);
+  shuffle_load<KeyT, PASS2>(keys, t * kFTile, min(t * kFTile + kFTile, n), cm, reg_col, pw, rid_in, kv, pv, rv, kfirst,
+                            klast);
 
   while (t < tend) {
-    const uint32_t row0 = t * kFTile;
-    const uint32_t rows = min(kFTile, n - row0);
-    const uint32_t rend = row0 + rows;
-    const uint32_t wrow0 = row0 + warp * 32 * kRPL;
     const uint32_t tn = t + tstep;
-
+    const uint32_t row0 = t * kFTile, rend = min(row0 + kFTile, n);
+    const uint32_t nrow0 = tn < tend ? tn * kFTile : 0u, nrend = tn < tend ? min(nrow0 + kFTile, n) : 0u;
     uint32_t lb0 = 0, Floc = F;
     if (PASS2) {
       const uint32_t b1f = sub_bucket_of(fmix64(key_bits(kfirst)), bs) / F2;
@@ -712,100 +604,15 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
       lb0 = b1f * F2;
       Floc = (b1l - b1f + 1) * F2;
       if (Floc > kFSpan) {  // uniform over the block: no barrier inside
-        shuffle_direct<KeyT>(keys, wrow0, rend, bs, cursors, cm, rid_in, rid_out);
-        if (tn < tend) shuffle_load<NT, KeyT, PASS2>(keys, n, tn, cm, reg_col, pw, rid_in, kv, pv, rv, kfirst, klast);
+        shuffle_direct<KeyT>(keys, row0 + warp * 32 * kRPL, rend, bs, cursors, cm, rid_in, rid_out);
+        if (nrow0 < nrend)
+          shuffle_load<KeyT, PASS2>(keys, nrow0, nrend, cm, reg_col, pw, rid_in, kv, pv, rv, kfirst, klast);
         t = tn;
         continue;
       }
     }
-
-    // 1. rank of each row in its bucket (order among equal buckets: arbitrary)
-    uint32_t *cnt = lstart;
-    for (uint32_t i = threadIdx.x; i < Floc; i += kFT) cnt[i] = 0;
-    __syncthreads();
-    uint32_t pk[kRPL];
-#pragma unroll
-    for (int c = 0; c < kRPL; c++) {
-      pk[c] = 0xFFFFFFFFu;
-      if (wrow0 + c * 32 + lane < rend) {
-        const uint64_t h = fmix64(key_bits(kv[c]));
-        const uint32_t b = (PASS2 ? sub_bucket_of(h, bs) : bucket_of(h, bs)) - lb0;
-        pk[c] = (b << 16) | atomicAdd(&cnt[b], 1u);
-      }
-    }
-    __syncthreads();
-
-    // 2. reserve every non-empty run (two buckets per thread), scan the counts
-    const uint32_t b0 = 2 * threadIdx.x, b1 = b0 + 1;
-    const uint32_t c0 = b0 < Floc ? cnt[b0] : 0u, c1 = b1 < Floc ? cnt[b1] : 0u;
-    const uint32_t g0 = c0 ? atomicAdd(&cursors[lb0 + b0], c0) : 0u;
-    const uint32_t g1 = c1 ? atomicAdd(&cursors[lb0 + b1], c1) : 0u;
-    uint32_t total;
-    const uint32_t ex = block_exclusive_scan<uint32_t>(c0 + c1, scratch, &total);
-    if (b0 < Floc) {
-      lstart[b0] = ex;
-      gbase[b0] = g0;
-    }
-    if (b1 < Floc) {
-      lstart[b1] = ex + c0;
-      gbase[b1] = g1;
-    }
-    __syncthreads();
-
-    // 3. stage the carried columns in bucket order, with each row's destination
-    uint32_t lp[kRPL];
-#pragma unroll
-    for (int c = 0; c < kRPL; c++) {
-      lp[c] = 0xFFFFFFFFu;
-      if (pk[c] != 0xFFFFFFFFu) {
-        const uint32_t b = pk[c] >> 16, rank = pk[c] & 0xFFFFu;
-        lp[c] = lstart[b] + rank;
-        dstmap[lp[c]] = gbase[b] + rank;
-        sk[lp[c]] = kv[c];
-        sp[lp[c]] = pv[c];
-        sr[lp[c]] = rv[c];
-      }
-    }
-    __syncthreads();
-    if (!EXTRA && tn < tend) shuffle_load<NT, KeyT, PASS2>(keys, n, tn, cm, reg_col, pw, rid_in, kv, pv, rv, kfirst, klast);
-
-    // 4. write-out: consecutive threads store consecutive rows of one run
-    KeyT *kdst = (KeyT *)cm.dst[cm.key_index];
-    for (uint32_t i = threadIdx.x; i < rows; i += kFT) {
-      const uint32_t d = dstmap[i];
-      kdst[d] = sk[i];
-      if (pw == 8) ((uint64_t *)cm.dst[reg_col])[d] = sp[i];
-      if (pw == 4) ((uint32_t *)cm.dst[reg_col])[d] = (uint32_t)sp[i];
-      if (rid_out) rid_out[d] = sr[i];
-    }
-
-    // 5. any further column, one at a time through the payload stage
-    if (EXTRA) {
-      for (int j = 0; j < cm.n; j++) {
-        if (j == cm.key_index || j == reg_col) continue;
-        const int w = cm.width[j];
-        uint64_t v[kRPL];
-#pragma unroll
-        for (int c = 0; c < kRPL; c++) {
-          const uint32_t r = wrow0 + c * 32 + lane;
-          v[c] = 0;
-          if (r < rend) v[c] = w == 8 ? ((const uint64_t *)cm.src[j])[r] : ((const uint32_t *)cm.src[j])[r];
-        }
-        __syncthreads();
-#pragma unroll
-        for (int c = 0; c < kRPL; c++)
-          if (lp[c] != 0xFFFFFFFFu) sp[lp[c]] = v[c];
-        __syncthreads();
-        for (uint32_t i = threadIdx.x; i < rows; i += kFT) {
-          const uint32_t d = dstmap[i];
-          if (w == 8)
-            ((uint64_t *)cm.dst[j])[d] = sp[i];
-          else
-            ((uint32_t *)cm.dst[j])[d] = (uint32_t)sp[i];
-        }
-      }
-      if (tn < tend) shuffle_load<NT, KeyT, PASS2>(keys, n, tn, cm, reg_col, pw, rid_in, kv, pv, rv, kfirst, klast);
-    }
+    shuffle_one_tile<NT, KeyT, PASS2, EXTRA>(smem, keys, row0, rend, lb0, Floc, bs, cursors, 0u, cm, reg_col, pw,
+                                             rid_in, rid_out, kv, pv, rv, nrow0, nrend, kfirst, klast);
     t = tn;
   }
 }
@@ -1116,11 +923,12 @@ int shuffle_pass(Workspace &ws, const KeyT *keys, uint32_t n, uint32_t grid, con
   return MDJ_OK;
 }
 
-// The merge's partition of one side with the unstable passes: count the
-// final sub-buckets, scan them into `off`, then one pass (F2 == 1) or two.
+// The merge's partition of one side with the unstable passes, first half:
+// count the final sub-buckets, scan them into `off`, then the only pass
+// (F2 == 1) or pass 1 (two-level plans) into freshly allocated `out`.
 template <typename KeyT>
-int shuffle_side_t(Workspace &ws, const mdj_table *t, int32_t key_col, const Plan &plan, uint32_t *off,
-                   TableBufs *fin) {
+int shuffle_count_pass1_t(Workspace &ws, const mdj_table *t, int32_t key_col, const Plan &plan, uint32_t *off,
+                          TableBufs *out) {
   cudaStream_t s = ws.stream();
   MDJ_TRY(set_shuffle_attrs<KeyT>());
   const uint32_t n = (uint32_t)t->nrows;
@@ -1130,11 +938,10 @@ int shuffle_side_t(Workspace &ws, const mdj_table *t, int32_t key_col, const Pla
   for (int j = 0; j < t->ncols; j++) src[j] = t->cols[j].data;
   const KeyT *keys = (const KeyT *)src[key_col];
   const BucketSpec sub = make_spec(plan.P, plan.S, 1);
-  const bool extra = t->ncols > 2;
   const uint32_t ntiles = (n + shuffle_tile<kShuffleNT>() - 1) / shuffle_tile<kShuffleNT>();
 
   MDJ_CUDA_TRY(cudaMemsetAsync(off, 0, (size_t)(nsub + 1) * 4, s));
-  MDJ_TRY(alloc_table_bufs(ws, t, fin, true));
+  MDJ_TRY(alloc_table_bufs(ws, t, out, true));
   if (n == 0) return MDJ_OK;
   uint32_t *cur = (uint32_t *)ws.get((size_t)(nsub + 1) * 4);
   if (!cur) return MDJ_ERR_OOM;
@@ -1158,25 +965,49 @@ int shuffle_side_t(Workspace &ws, const mdj_table *t, int32_t key_col, const Pla
   }
   MDJ_LAUNCH_CHECK();
   uint32_t grid1 = 0;
-  MDJ_TRY(shuffle_grid<KeyT>(false, extra, ntiles, &grid1));
+  MDJ_TRY(shuffle_grid<KeyT>(false, t->ncols > 2, ntiles, &grid1));
+  ColMove cm = make_move(t, key_col, src, out->cols);
   if (plan.F2 == 1) {
-    ColMove cm = make_move(t, key_col, src, fin->cols);
-    MDJ_TRY((shuffle_pass<KeyT, false>(ws, keys, n, grid1, sub, nsub, 1, cur, cm, nullptr, fin->rid)));
+    MDJ_TRY((shuffle_pass<KeyT, false>(ws, keys, n, grid1, sub, nsub, 1, cur, cm, nullptr, out->rid)));
   } else {
-    TableBufs p1;
-    MDJ_TRY(alloc_table_bufs(ws, t, &p1, true));
-    ColMove cm1 = make_move(t, key_col, src, p1.cols);
-    MDJ_TRY((shuffle_pass<KeyT, false>(ws, keys, n, grid1, make_spec(plan.P, plan.S, plan.F2), F1, plan.F2, cur,
-                                       cm1, nullptr, p1.rid)));
-    MDJ_CUDA_TRY(cudaMemcpyAsync(cur, off, (size_t)nsub * 4, cudaMemcpyDeviceToDevice, s));
-    uint32_t grid2 = 0;
-    MDJ_TRY(shuffle_grid<KeyT>(true, extra, ntiles, &grid2));
-    ColMove cm2 = make_move(t, key_col, p1.cols, fin->cols);
-    MDJ_TRY((shuffle_pass<KeyT, true>(ws, (const KeyT *)p1.cols[key_col], n, grid2, sub, 0, plan.F2, cur, cm2,
-                                      p1.rid, fin->rid)));
-    release_table_bufs(ws, t, &p1);
+    MDJ_TRY((shuffle_pass<KeyT, false>(ws, keys, n, grid1, make_spec(plan.P, plan.S, plan.F2), F1, plan.F2, cur, cm,
+                                       nullptr, out->rid)));
   }
   ws.give_back(cur);
+  return MDJ_OK;
+}
+
+// Second half of a two-level plan: pass 2 from the pass-1 copy `p1` into
+// freshly allocated `fin` (sub-bucket offsets `off` from the first half).
+template <typename KeyT>
+int shuffle_pass2_t(Workspace &ws, const mdj_table *t, int32_t key_col, const Plan &plan, const uint32_t *off,
+                    const TableBufs &p1, TableBufs *fin) {
+  cudaStream_t s = ws.stream();
+  const uint32_t n = (uint32_t)t->nrows;
+  const uint32_t nsub = plan.nbuckets;
+  MDJ_TRY(alloc_table_bufs(ws, t, fin, true));
+  if (n == 0) return MDJ_OK;
+  const uint32_t ntiles = (n + shuffle_tile<kShuffleNT>() - 1) / shuffle_tile<kShuffleNT>();
+  uint32_t *cur = (uint32_t *)ws.get((size_t)(nsub + 1) * 4);
+  if (!cur) return MDJ_ERR_OOM;
+  MDJ_CUDA_TRY(cudaMemcpyAsync(cur, off, (size_t)nsub * 4, cudaMemcpyDeviceToDevice, s));
+  uint32_t grid2 = 0;
+  MDJ_TRY(shuffle_grid<KeyT>(true, t->ncols > 2, ntiles, &grid2));
+  ColMove cm2 = make_move(t, key_col, p1.cols, fin->cols);
+  MDJ_TRY((shuffle_pass<KeyT, true>(ws, (const KeyT *)p1.cols[key_col], n, grid2, make_spec(plan.P, plan.S, 1), 0,
+                                    plan.F2, cur, cm2, p1.rid, fin->rid)));
+  ws.give_back(cur);
+  return MDJ_OK;
+}
+
+template <typename KeyT>
+int shuffle_side_t(Workspace &ws, const mdj_table *t, int32_t key_col, const Plan &plan, uint32_t *off,
+                   TableBufs *fin) {
+  if (plan.F2 == 1) return shuffle_count_pass1_t<KeyT>(ws, t, key_col, plan, off, fin);
+  TableBufs p1;
+  MDJ_TRY(shuffle_count_pass1_t<KeyT>(ws, t, key_col, plan, off, &p1));
+  MDJ_TRY(shuffle_pass2_t<KeyT>(ws, t, key_col, plan, off, p1, fin));
+  release_table_bufs(ws, t, &p1);
   return MDJ_OK;
 }
 
@@ -1378,6 +1209,56 @@ Plan make_plan(uint64_t n_build, uint32_t P, uint32_t cap, bool force_partition)
 int partition_side(Workspace &ws, const mdj_table *t, int32_t key_col, const Plan &plan, Side *out) {
   if (t->cols[key_col].dtype == MDJ_I64) return partition_side_t<int64_t>(ws, t, key_col, plan, out);
   return partition_side_t<int32_t>(ws, t, key_col, plan, out);
+}
+
+namespace {
+void fill_side(const mdj_table *t, int32_t key_col, const TableBufs &b, uint32_t *off, Side *out) {
+  out->key = b.cols[key_col];
+  out->key_dtype = t->cols[key_col].dtype;
+  out->ncols = 0;
+  for (int j = 0; j < t->ncols; j++) {
+    if (j == key_col) continue;
+    out->cols[out->ncols] = b.cols[j];
+    out->widths[out->ncols] = dtype_width(t->cols[j].dtype);
+    out->dtypes[out->ncols] = t->cols[j].dtype;
+    out->ncols++;
+  }
+  out->rid = b.rid;
+  out->off = off;
+  out->nrows = t->nrows;
+}
+}  // namespace
+
+bool merge_shuffle_unstable() { return fast_shuffle_enabled(); }
+
+int partition_side_pass1(Workspace &ws, const mdj_table *t, int32_t key_col, const Plan &plan, Side1 *out) {
+  if (plan.F2 < 2 || plan.lsd || !plan.partition) return MDJ_ERR_INTERNAL;
+  uint32_t *off = (uint32_t *)ws.get((size_t)(plan.nbuckets + 1) * 4);
+  if (!off) return MDJ_ERR_OOM;
+  TableBufs p1;
+  if (t->cols[key_col].dtype == MDJ_I64)
+    MDJ_TRY(shuffle_count_pass1_t<int64_t>(ws, t, key_col, plan, off, &p1));
+  else
+    MDJ_TRY(shuffle_count_pass1_t<int32_t>(ws, t, key_col, plan, off, &p1));
+  memset(out, 0, sizeof *out);
+  fill_side(t, key_col, p1, off, &out->p1);
+  for (int j = 0; j < t->ncols; j++) out->all_cols[j] = p1.cols[j];
+  out->block = p1.block;
+  return MDJ_OK;
+}
+
+int partition_side_pass2(Workspace &ws, const mdj_table *t, int32_t key_col, const Plan &plan, const Side1 &in,
+                         Side *out) {
+  TableBufs p1, fin;
+  for (int j = 0; j < t->ncols; j++) p1.cols[j] = const_cast<void *>(in.all_cols[j]);
+  p1.rid = (uint32_t *)in.p1.rid;
+  p1.block = in.block;
+  if (t->cols[key_col].dtype == MDJ_I64)
+    MDJ_TRY(shuffle_pass2_t<int64_t>(ws, t, key_col, plan, in.p1.off, p1, &fin));
+  else
+    MDJ_TRY(shuffle_pass2_t<int32_t>(ws, t, key_col, plan, in.p1.off, p1, &fin));
+  fill_side(t, key_col, fin, (uint32_t *)in.p1.off, out);
+  return MDJ_OK;
 }
 
 int stable_partition(Workspace &ws, const mdj_table *t, int32_t key_col, uint32_t P, void *const *out_cols,

@@ -126,6 +126,27 @@ def test_two_level_plan_stable_passes(monkeypatch):
     assert got["key"].size == math.floor(0.3 * 2_000_000)
 
 
+def test_two_level_plan_fused_pass2_join(monkeypatch):
+    # pass 2 and the join in one kernel through scratch slots (MDJ_FUSED=1)
+    monkeypatch.setenv("MDJ_FUSED", "1")
+    (lk, lp), (rk, rp) = datagen.match_fraction_tables(4_000_000, 2_000_000, 0.3, seed=8)
+    got = _check([lk, lp], [rk, rp], 8)
+    assert got["key"].size == math.floor(0.3 * 2_000_000)
+
+
+@pytest.mark.parametrize("kd,pd", [(np.int32, np.float32), (np.int64, np.float32), (np.int32, np.float64)])
+def test_two_level_plan_fused_dtypes_and_duplicates(monkeypatch, kd, pd):
+    monkeypatch.setenv("MDJ_FUSED", "1")
+    # 5M build rows: more sub-buckets than one pass can make, so two passes
+    rng = np.random.default_rng(17)
+    n = 5_000_000
+    lk = rng.integers(0, 2_000_000, n).astype(kd)
+    rk = rng.integers(0, 4_000_000, n // 2).astype(kd)
+    lp = datagen.uniform_payload(rng, n, pd)
+    rp = datagen.uniform_payload(rng, n // 2, pd)
+    _check([lk, lp], [rk, rp], 8)
+
+
 def test_config0_plain_merge_P1():
     # plain inner merge, P = 1: 1M x 1M, unique left keys, match fraction 0.3
     (lk, lp), (rk, rp) = datagen.match_fraction_tables(1_000_000, 1_000_000, 0.3, seed=0)
