@@ -758,10 +758,12 @@ __global__ void __launch_bounds__(kShuffleNT, 2)
       KeyT kf, kl;
       const KeyT *keys = (const KeyT *)a.p1_key[side];
       shuffle_load<KeyT, true>(keys, row0, rend, cm, reg_col, a.pay_w[side], a.p1_rid[side], kv, pv, rv, kf, kl);
+      shuffle_clear_counters<kShuffleNT>(smem);  // the shared memory held a join item before
+      __syncthreads();
       shuffle_one_tile<kShuffleNT, KeyT, true, false>(smem, keys, row0, rend, w * a.F2, a.F2, a.sub,
                                                       a.cursors[side], wv.row0[side], cm, reg_col, a.pay_w[side],
                                                       a.p1_rid[side], (uint32_t *)cm.dst[2], kv, pv, rv, 0u, 0u, kf,
-                                                      kl);
+                                                      kl, 0);
     } else {
       // ---- a join item of wave q - lag
       w = q - kFuseLag;

@@ -592,6 +592,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
   if (t >= tend) return;
   shuffle_load<KeyT, PASS2>(keys, t * kFTile, min(t * kFTile + kFTile, n), cm, reg_col, pw, rid_in, kv, pv, rv, kfirst,
                             klast);
+  shuffle_clear_counters<NT>(smem);
+  __syncthreads();
+  int parity = 0;  // counter buffer of the next staged tile
 
   while (t < tend) {
     const uint32_t tn = t + tstep;
@@ -612,7 +615,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
       }
     }
     shuffle_one_tile<NT, KeyT, PASS2, EXTRA>(smem, keys, row0, rend, lb0, Floc, bs, cursors, 0u, cm, reg_col, pw,
-                                             rid_in, rid_out, kv, pv, rv, nrow0, nrend, kfirst, klast);
+                                             rid_in, rid_out, kv, pv, rv, nrow0, nrend, kfirst, klast, parity);
+    parity ^= 1;
     t = tn;
   }
 }

@@ -65,7 +65,10 @@ template <int NT>
 __host__ __device__ constexpr uint32_t shuffle_span() { return 2u * NT; }
 template <int NT>
 constexpr size_t shuffle_smem_bytes() {
-  return (size_t)shuffle_tile<NT>() * (8 + 8 + 4 + 4) + (size_t)shuffle_span<NT>() * 8 + 40 * 4;
+  // stage (16-byte key/payload record, 8-byte row id/destination) per row;
+  // two counter buffers and the packed (local start, destination base) per
+  // local bucket; warp sums
+  return (size_t)shuffle_tile<NT>() * (16 + 8) + (size_t)shuffle_span<NT>() * (4 + 4 + 8) + 32 * 4;
 }
 
 // scatter_direct for k_shuffle, reading the keys again from memory so that
@@ -117,6 +120,12 @@ __device__ __forceinline__ void shuffle_load(const KeyT *__restrict__ keys, uint
 // a row reserved at cursor value g lands at index g - dst_base of the
 // destination columns.  With next_row0 < next_rend the registers receive the
 // rows [next_row0, next_rend) once this tile is staged (before its write-out).
+//
+// Counters: buffer `parity` (all 2 * NT entries) must be zero on entry; the
+// tile zeroes buffer 1 - parity while it stages, so consecutive tiles of one
+// block alternate buffers and need no barrier between them: a warp may rank
+// the next tile while others still write this one out.  Four block barriers
+// per tile (after ranking, inside the scan, after the scan, after staging).
 template <int NT, typename KeyT, bool PASS2, bool EXTRA>
 __device__ __forceinline__ void shuffle_one_tile(unsigned char *smem, const KeyT *__restrict__ keys, uint32_t row0,
                                                  uint32_t rend, uint32_t lb0, uint32_t Floc, const BucketSpec &bs,
@@ -124,109 +133,123 @@ __device__ __forceinline__ void shuffle_one_tile(unsigned char *smem, const KeyT
                                                  int reg_col, int pw, const uint32_t *__restrict__ rid_in,
                                                  uint32_t *__restrict__ rid_out, KeyT (&kv)[kRPL],
                                                  uint64_t (&pv)[kRPL], uint32_t (&rv)[kRPL], uint32_t next_row0,
-                                                 uint32_t next_rend, KeyT &kfirst, KeyT &klast) {
+                                                 uint32_t next_rend, KeyT &kfirst, KeyT &klast, int parity) {
   constexpr uint32_t kFTile = shuffle_tile<NT>(), kFSpan = shuffle_span<NT>();
-  constexpr int kFT = NT;
-  KeyT *sk = (KeyT *)smem;
-  uint64_t *sp = (uint64_t *)(smem + (size_t)kFTile * 8);
-  uint32_t *sr = (uint32_t *)(smem + (size_t)kFTile * 16);
-  uint32_t *dstmap = sr + kFTile;
-  uint32_t *lstart = dstmap + kFTile;
-  uint32_t *gbase = lstart + kFSpan;
-  uint32_t *scratch = gbase + kFSpan;
+  constexpr int kFT = NT, kNWarps = NT / 32;
+  // stage: per row a 16-byte (key, payload) record and an 8-byte (row id,
+  // destination) pair, so a row is scattered with two stores, not four
+  ulonglong2 *rec = (ulonglong2 *)smem;
+  uint2 *meta = (uint2 *)(smem + (size_t)kFTile * 16);
+  uint32_t *cnt = (uint32_t *)(meta + kFTile) + (size_t)parity * kFSpan;
+  uint32_t *cnt_next = (uint32_t *)(meta + kFTile) + (size_t)(1 - parity) * kFSpan;
+  uint2 *lg = (uint2 *)((uint32_t *)(meta + kFTile) + 2 * kFSpan);  // (local start, destination base)
+  uint32_t *wsum = (uint32_t *)(lg + kFSpan);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rows = rend - row0;
   const uint32_t wrow0 = row0 + warp * 32 * kRPL;
 
-    // 1. rank of each row in its bucket (order among equal buckets: arbitrary)
-    uint32_t *cnt = lstart;
-    for (uint32_t i = threadIdx.x; i < Floc; i += kFT) cnt[i] = 0;
-    __syncthreads();
-    uint32_t pk[kRPL];
+  // 1. rank of each row in its bucket (order among equal buckets: arbitrary)
+  uint32_t pk[kRPL];
 #pragma unroll
-    for (int c = 0; c < kRPL; c++) {
-      pk[c] = 0xFFFFFFFFu;
-      if (wrow0 + c * 32 + lane < rend) {
-        const uint64_t h = fmix64(key_bits(kv[c]));
-        const uint32_t b = (PASS2 ? sub_bucket_of(h, bs) : bucket_of(h, bs)) - lb0;
-        pk[c] = (b << 16) | atomicAdd(&cnt[b], 1u);
+  for (int c = 0; c < kRPL; c++) {
+    pk[c] = 0xFFFFFFFFu;
+    if (wrow0 + c * 32 + lane < rend) {
+      const uint64_t h = fmix64(key_bits(kv[c]));
+      const uint32_t b = (PASS2 ? sub_bucket_of(h, bs) : bucket_of(h, bs)) - lb0;
+      pk[c] = (b << 16) | atomicAdd(&cnt[b], 1u);
+    }
+  }
+  __syncthreads();
+
+  // 2. reserve every non-empty run (two buckets per thread), scan the counts:
+  //    warp sums published once, each warp adds up the sums before it
+  const uint32_t b0 = 2 * threadIdx.x, b1 = b0 + 1;
+  const uint32_t c0 = b0 < Floc ? cnt[b0] : 0u, c1 = b1 < Floc ? cnt[b1] : 0u;
+  const uint32_t g0 = c0 ? atomicAdd(&cursors[lb0 + b0], c0) : 0u;
+  const uint32_t g1 = c1 ? atomicAdd(&cursors[lb0 + b1], c1) : 0u;
+  const uint32_t v = c0 + c1;
+  const uint32_t inc = warp_inclusive_scan(v);
+  if (lane == 31) wsum[warp] = inc;
+  __syncthreads();
+  uint32_t before = 0;
+#pragma unroll
+  for (int w = 0; w < kNWarps; w++)
+    if (w < warp) before += wsum[w];
+  const uint32_t ex = before + inc - v;
+  if (b0 < Floc) lg[b0] = make_uint2(ex, g0 - dst_base);
+  if (b1 < Floc) lg[b1] = make_uint2(ex + c0, g1 - dst_base);
+  __syncthreads();
+
+  // 3. stage the carried columns in bucket order, with each row's destination;
+  //    clear the other counter buffer for the next tile
+  for (uint32_t i = threadIdx.x; i < kFSpan; i += kFT) cnt_next[i] = 0;
+  uint32_t lp[kRPL];
+#pragma unroll
+  for (int c = 0; c < kRPL; c++) {
+    lp[c] = 0xFFFFFFFFu;
+    if (pk[c] != 0xFFFFFFFFu) {
+      const uint32_t b = pk[c] >> 16, rank = pk[c] & 0xFFFFu;
+      const uint2 e = lg[b];
+      lp[c] = e.x + rank;
+      uint64_t kb = 0;
+      memcpy(&kb, &kv[c], sizeof(KeyT));
+      rec[lp[c]] = make_ulonglong2(kb, pv[c]);
+      meta[lp[c]] = make_uint2(rv[c], e.y + rank);
+    }
+  }
+  __syncthreads();
+  if (!EXTRA && next_row0 < next_rend)
+    shuffle_load<KeyT, PASS2>(keys, next_row0, next_rend, cm, reg_col, pw, rid_in, kv, pv, rv, kfirst, klast);
+
+  // 4. write-out: consecutive threads store consecutive rows of one run
+  KeyT *kdst = (KeyT *)cm.dst[cm.key_index];
+  for (uint32_t i = threadIdx.x; i < rows; i += kFT) {
+    const ulonglong2 r = rec[i];
+    const uint2 m = meta[i];
+    const uint32_t d = m.y;
+    KeyT k;
+    memcpy(&k, &r.x, sizeof(KeyT));
+    kdst[d] = k;
+    if (pw == 8) ((uint64_t *)cm.dst[reg_col])[d] = r.y;
+    if (pw == 4) ((uint32_t *)cm.dst[reg_col])[d] = (uint32_t)r.y;
+    if (rid_out) rid_out[d] = m.x;
+  }
+
+  // 5. any further column, one at a time through the payload half of the stage
+  if (EXTRA) {
+    for (int j = 0; j < cm.n; j++) {
+      if (j == cm.key_index || j == reg_col) continue;
+      const int w = cm.width[j];
+      uint64_t val[kRPL];
+#pragma unroll
+      for (int c = 0; c < kRPL; c++) {
+        const uint32_t r = wrow0 + c * 32 + lane;
+        val[c] = 0;
+        if (r < rend) val[c] = w == 8 ? ((const uint64_t *)cm.src[j])[r] : ((const uint32_t *)cm.src[j])[r];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int c = 0; c < kRPL; c++)
+        if (lp[c] != 0xFFFFFFFFu) rec[lp[c]].y = val[c];
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < rows; i += kFT) {
+        const uint32_t d = meta[i].y;
+        if (w == 8)
+          ((uint64_t *)cm.dst[j])[d] = rec[i].y;
+        else
+          ((uint32_t *)cm.dst[j])[d] = (uint32_t)rec[i].y;
       }
     }
-    __syncthreads();
-
-    // 2. reserve every non-empty run (two buckets per thread), scan the counts
-    const uint32_t b0 = 2 * threadIdx.x, b1 = b0 + 1;
-    const uint32_t c0 = b0 < Floc ? cnt[b0] : 0u, c1 = b1 < Floc ? cnt[b1] : 0u;
-    const uint32_t g0 = c0 ? atomicAdd(&cursors[lb0 + b0], c0) : 0u;
-    const uint32_t g1 = c1 ? atomicAdd(&cursors[lb0 + b1], c1) : 0u;
-    uint32_t total;
-    const uint32_t ex = block_exclusive_scan<uint32_t>(c0 + c1, scratch, &total);
-    if (b0 < Floc) {
-      lstart[b0] = ex;
-      gbase[b0] = g0;
-    }
-    if (b1 < Floc) {
-      lstart[b1] = ex + c0;
-      gbase[b1] = g1;
-    }
-    __syncthreads();
-
-    // 3. stage the carried columns in bucket order, with each row's destination
-    uint32_t lp[kRPL];
-#pragma unroll
-    for (int c = 0; c < kRPL; c++) {
-      lp[c] = 0xFFFFFFFFu;
-      if (pk[c] != 0xFFFFFFFFu) {
-        const uint32_t b = pk[c] >> 16, rank = pk[c] & 0xFFFFu;
-        lp[c] = lstart[b] + rank;
-        dstmap[lp[c]] = gbase[b] + rank - dst_base;
-        sk[lp[c]] = kv[c];
-        sp[lp[c]] = pv[c];
-        sr[lp[c]] = rv[c];
-      }
-    }
-    __syncthreads();
-    if (!EXTRA && next_row0 < next_rend)
+    if (next_row0 < next_rend)
       shuffle_load<KeyT, PASS2>(keys, next_row0, next_rend, cm, reg_col, pw, rid_in, kv, pv, rv, kfirst, klast);
+  }
+}
 
-    // 4. write-out: consecutive threads store consecutive rows of one run
-    KeyT *kdst = (KeyT *)cm.dst[cm.key_index];
-    for (uint32_t i = threadIdx.x; i < rows; i += kFT) {
-      const uint32_t d = dstmap[i];
-      kdst[d] = sk[i];
-      if (pw == 8) ((uint64_t *)cm.dst[reg_col])[d] = sp[i];
-      if (pw == 4) ((uint32_t *)cm.dst[reg_col])[d] = (uint32_t)sp[i];
-      if (rid_out) rid_out[d] = sr[i];
-    }
-
-    // 5. any further column, one at a time through the payload stage
-    if (EXTRA) {
-      for (int j = 0; j < cm.n; j++) {
-        if (j == cm.key_index || j == reg_col) continue;
-        const int w = cm.width[j];
-        uint64_t v[kRPL];
-#pragma unroll
-        for (int c = 0; c < kRPL; c++) {
-          const uint32_t r = wrow0 + c * 32 + lane;
-          v[c] = 0;
-          if (r < rend) v[c] = w == 8 ? ((const uint64_t *)cm.src[j])[r] : ((const uint32_t *)cm.src[j])[r];
-        }
-        __syncthreads();
-#pragma unroll
-        for (int c = 0; c < kRPL; c++)
-          if (lp[c] != 0xFFFFFFFFu) sp[lp[c]] = v[c];
-        __syncthreads();
-        for (uint32_t i = threadIdx.x; i < rows; i += kFT) {
-          const uint32_t d = dstmap[i];
-          if (w == 8)
-            ((uint64_t *)cm.dst[j])[d] = sp[i];
-          else
-            ((uint32_t *)cm.dst[j])[d] = (uint32_t)sp[i];
-        }
-      }
-      if (next_row0 < next_rend)
-        shuffle_load<KeyT, PASS2>(keys, next_row0, next_rend, cm, reg_col, pw, rid_in, kv, pv, rv, kfirst, klast);
-    }
+// Clears both counter buffers of shuffle_one_tile (block-wide, no barrier).
+template <int NT>
+__device__ __forceinline__ void shuffle_clear_counters(unsigned char *smem) {
+  uint32_t *cnt = (uint32_t *)(smem + (size_t)shuffle_tile<NT>() * 24);
+  for (uint32_t i = threadIdx.x; i < 2 * shuffle_span<NT>(); i += NT) cnt[i] = 0;
 }
 
 }  // namespace
