@@ -442,7 +442,8 @@ def served_section(args, dev):
 
 def measured_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` from a committed ncu summary, if the
-    kernel source is unchanged since the capture (else None)."""
+    kernel's source files (comma-separated, hashed together) are unchanged
+    since the capture (else None)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     src = os.path.join(ROOT, "paper_2101_08878_gb300", "csrc")
@@ -454,7 +455,8 @@ def measured_traffic(kernel: str):
         kv = dict(x.split("=", 1) for x in r if "=" in x)
         if kv.get("kernel") != kernel:
             continue
-        h = hashlib.sha256(open(os.path.join(src, kv["file"]), "rb").read()).hexdigest()[:16]
+        blob = b"".join(open(os.path.join(src, f), "rb").read() for f in kv["file"].split(","))
+        h = hashlib.sha256(blob).hexdigest()[:16]
         if h != kv.get("src_sha"):
             return None
         return int(float(kv["bytes_per_unit"]) * N_LEFT)
