@@ -397,6 +397,7 @@ def merge_host(left_cols, right_cols, P: int, left_key: int = 0, right_key: int 
     dr = [c.to(dev, non_blocking=True) for c in right_cols]
     h2d = sum(c.numel() * c.element_size() for c in list(left_cols) + list(right_cols))
     res = mdj_merge(dl, dr, P, left_key, right_key)
+
     def host(t):
         h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
         h.copy_(t, non_blocking=True)

@@ -239,3 +239,19 @@ def test_merge_with_pipelined_scatter(monkeypatch):
     (lk, lp), (rk, rp) = datagen.match_fraction_tables(4_000_000, 1_000_000, 0.3, seed=31)
     got = _check([lk, lp], [rk, rp], 8)
     assert got["key"].size == 300_000
+
+
+def test_merge_host_end_to_end():
+    # host (pinned) tables in, host result out: same rows as the device merge
+    (lk, lp), (rk, rp) = datagen.match_fraction_tables(700_000, 900_000, 0.4, seed=21)
+    mdj = _mdj()
+    hl = [torch.from_numpy(lk).pin_memory(), torch.from_numpy(lp).pin_memory()]
+    hr = [torch.from_numpy(rk).pin_memory(), torch.from_numpy(rp).pin_memory()]
+    out, h2d, d2h = mdj.merge_host(hl, hr, 8)
+    assert h2d == 16 * (700_000 + 900_000)
+    assert out.nrows == math.floor(0.4 * 900_000) and not out.key.is_cuda
+    assert d2h == out.nrows * (8 + 4 + 4 + 8 + 8)
+    dev = mdj.mdj_merge(_dev([lk, lp]), _dev([rk, rp]), 8)
+    a = torch.sort((out.key << 32) | out.right_row.view(torch.int32).to(torch.int64)).values
+    b = torch.sort(((dev.key << 32) | dev.right_row.view(torch.int32).to(torch.int64)).cpu()).values
+    assert torch.equal(a, b)
