@@ -60,6 +60,24 @@ def test_results_identical_alone_and_in_the_mix():
     assert st["n"] == len(work) and st["p50_ms"] <= st["p99_ms"]
 
 
+def test_served_stream_matches_oracle():
+    # config 4 at reduced scale: 120 requests (P, key and payload widths
+    # drawn per request) arriving faster than one slot can serve, so groups
+    # form; every served result equals the oracle's merge row for row
+    import oracle
+    from joinhelp import assert_same_result, gpu_result_np
+    from paper_2101_08878_gb300.server import MergeServer, run_poisson
+    work = _workload(120, seed=11)
+    host = [([c.cpu().numpy() for c in l], [c.cpu().numpy() for c in r]) for l, r, _ in work]
+    arrivals = np.cumsum(np.random.default_rng(12).exponential(0.0002, len(work)))
+    server = MergeServer(DEV, slots=2)
+    reqs, _ = asyncio.run(asyncio.wait_for(run_poisson(server, work, arrivals), 300))
+    assert all(r.error is None for r in reqs), [r.error for r in reqs if r.error]
+    assert sum(server.group_sizes) == len(work) and max(server.group_sizes) > 1
+    for req, (hl, hr) in zip(reqs, host):
+        assert_same_result(gpu_result_np(req.result), oracle.merge_table(hl, hr))
+
+
 def test_admission_waits_for_memory_and_rejects_oversized():
     from paper_2101_08878_gb300.server import MergeServer, run_poisson
     work = _workload(6, seed=5)
