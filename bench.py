@@ -201,8 +201,10 @@ def alg_bytes_per_launch(kernel: str, n_side: int, n_left: int, n_right: int, m:
     payloads, 4-byte row ids); None for kernels outside the model."""
     per_side = {
         "hist": KEY,                                       # read keys
-        "scatter_stable": (KEY + PAY) + (KEY + PAY + RID),  # read row, write row + row id
-        "scatter_reserve": (KEY + PAY + RID) * 2,          # second level: read + write row and row id
+        "shuffle_pass1": (KEY + PAY) + (KEY + PAY + RID),  # read row, write row + row id
+        "shuffle_pass2": (KEY + PAY + RID) * 2,            # second level: read + write row and row id
+        "scatter_stable": (KEY + PAY) + (KEY + PAY + RID),  # the stable passes (MDJ_STABLE_SHUFFLE=1)
+        "scatter_reserve": (KEY + PAY + RID) * 2,
     }
     if kernel in per_side:
         return per_side[kernel] * n_side

@@ -18,8 +18,9 @@
  *    HOST memory.  Input columns are read-only and remain owned by the caller.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *    Every call is asynchronous on that stream, except mdj_join / mdj_merge /
- *    mdj_count_checksum, which read one small count back to the host (one
- *    stream synchronisation) before sizing their outputs.
+ *    mdj_count_checksum and the batch calls, which read small counts back to
+ *    the host (the number of work items, then the output row count: stream
+ *    synchronisations) to size their outputs.
  *  - Workspace and join outputs come from the caller's allocator (mdj_allocator);
  *    a NULL allocator means cudaMallocAsync / cudaFreeAsync on `stream`.
  *  - Keys are signed integers (MDJ_I32 or MDJ_I64); both sides of a join must use

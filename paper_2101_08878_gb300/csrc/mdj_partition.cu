@@ -920,7 +920,7 @@ int shuffle_pass(Workspace &ws, const KeyT *keys, uint32_t n, uint32_t grid, con
   int reg_col = -1;
   for (int j = 0; j < cm.n && reg_col < 0; j++)
     if (j != cm.key_index) reg_col = j;
-  TraceScope tr(PASS2 ? "scatter_reserve" : "scatter_stable", ws.stream());
+  TraceScope tr(PASS2 ? "shuffle_pass2" : "shuffle_pass1", ws.stream());
   shuffle_kernel<KeyT>(PASS2, cm.n > 2)<<<grid, NT, shuffle_smem_bytes<NT>(), ws.stream()>>>(
       keys, n, ntiles, bs, F, F2, cur, cm, reg_col, rid_in, rid_out);
   MDJ_LAUNCH_CHECK();
