@@ -339,7 +339,7 @@ def run_gpu(args):
 
 
 def batched_section(args, dev):
-    """Config 3: 256 independent partition-pair joins (n_L, n_R log-uniform in
+    """The batched workload: 256 independent partition-pair joins (n_L, n_R log-uniform in
     [1K, 4M], match fraction U[0.1, 0.9]) through mdj_join_batch (tuned) versus
     the plain path, one mdj_join call per pair.  Input rows/s of each."""
     import torch
@@ -394,7 +394,7 @@ def batched_section(args, dev):
 
 
 def served_section(args, dev):
-    """Config 4: Poisson arrivals of merge requests (P in {1, 8, 32}, n_L, n_R
+    """The served workload: Poisson arrivals of merge requests (P in {1, 8, 32}, n_L, n_R
     log-uniform in [1e4, 2e7], int32/int64 keys and float32/float64 payloads
     50/50, match fraction 0.3) over a device-resident pool of tables, served
     by MergeServer with continuous batching versus the plain per-request path

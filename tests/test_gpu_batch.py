@@ -114,7 +114,7 @@ def test_batch_invalid_arguments():
 
 
 @pytest.mark.slow
-def test_batch_config3_full_size():
+def test_batch_256_pairs_full_size():
     # 256 pairs, n_L, n_R log-uniform in [1K, 4M], match fraction U[0.1, 0.9]
     pairs = datagen.batch_pairs(256, 1_000, 4_000_000, seed=3)
     res, res_np, po, lo, ro = _run_batch(pairs)

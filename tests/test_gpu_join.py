@@ -147,7 +147,7 @@ def test_two_level_plan_fused_dtypes_and_duplicates(monkeypatch, kd, pd):
     _check([lk, lp], [rk, rp], 8)
 
 
-def test_config0_plain_merge_P1():
+def test_plain_merge_1M_P1():
     # plain inner merge, P = 1: 1M x 1M, unique left keys, match fraction 0.3
     (lk, lp), (rk, rp) = datagen.match_fraction_tables(1_000_000, 1_000_000, 0.3, seed=0)
     got = _check([lk, lp], [rk, rp], 1)

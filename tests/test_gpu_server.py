@@ -61,7 +61,7 @@ def test_results_identical_alone_and_in_the_mix():
 
 
 def test_served_stream_matches_oracle():
-    # config 4 at reduced scale: 120 requests (P, key and payload widths
+    # the served request stream at reduced scale: 120 requests (P, key and payload widths
     # drawn per request) arriving faster than one slot can serve, so groups
     # form; every served result equals the oracle's merge row for row
     import oracle
