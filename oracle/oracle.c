@@ -7,8 +7,8 @@
  * entry point and the CPU-baseline leg of the benchmark use it.  It shares no
  * code, header, table or constant with the CUDA path.
  *
- * The paper names the operation ("a merge operation is carried out for multiple
- * cuDF data frames", with "Shuffle: True, Fraction Match: 0.3") but prints no
+ * The paper's benchmark merges cuDF data frames after a shuffle (Sec. V-B,
+ * Fig. 8 settings "Shuffle: True, Fraction Match: 0.3") but prints no
  * algorithm, hash or output schema.  This file therefore writes out the plain
  * definitions of what the method computes:
  *

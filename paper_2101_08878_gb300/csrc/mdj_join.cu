@@ -1,5 +1,5 @@
 // The per-partition merge: an inner hash join of co-partitioned tables
-// (Sec. V-B: "a merge operation is carried out" after the shuffle).
+// (Sec. V-B: the benchmark merges the shuffled data frames).
 //
 // Both sides are bucketed with the same hash (partition p, then sub-bucket),
 // so equal keys share a bucket.  A work item is (bucket, chunk of at most `cap`
