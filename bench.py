@@ -291,6 +291,11 @@ def run_gpu(args):
                    "share": round(v[1] / max(sum(x[1] for x in prof.values()), 1e-9), 4)}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
 
+    # ---- the same merge through the streamed-output path, one window of all rows
+    stream_plain = None
+    if args.stream_windows > 0:
+        stream_plain = stream_whole(left, right, m_expect, ms_step, dev)
+
     # ---- end to end: host (pinned) inputs -> device -> merge -> host result
     e2e = None
     if args.e2e_steps > 0:
@@ -326,6 +331,10 @@ def run_gpu(args):
         "roofline": roofline, "step_roofline": step_roof, "kernels": kernels, "gpu_launches": launches,
         "e2e": e2e, "clocks": clk.summary(),
     }
+    if args.stream_windows > 0:
+        torch.cuda.empty_cache()
+        line["streamed"] = streamed_section(args, dev)
+        line["streamed"]["plain_workload_one_window"] = stream_plain
     if args.batch_pairs > 0:
         line["batched"] = batched_section(args, dev)
     if args.serve_requests > 0:
@@ -336,6 +345,106 @@ def run_gpu(args):
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def stream_whole(left, right, m_expect, merge_ms, dev):
+    """The bench workload through mdj_stream_open + one window of every row,
+    against mdj_merge: what the streamed path costs when the result fits."""
+    import torch
+    from paper_2101_08878_gb300 import mdj
+
+    def once():
+        t0 = time.perf_counter()
+        st = mdj.MergeStream(left, right, P)
+        t_open = time.perf_counter() - t0
+        assert st.total_rows == m_expect
+        buf = st.buffers(st.total_rows)
+        stream = torch.cuda.current_stream(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st.emit(0, st.total_rows, buf)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st.close()
+        return t_open * 1e3, e0.elapsed_time(e1)
+
+    once()
+    runs = [once() for _ in range(3)]
+    open_ms = statistics.median(r[0] for r in runs)
+    emit_ms = statistics.median(r[1] for r in runs)
+    return {"open_ms": round(open_ms, 3), "emit_ms": round(emit_ms, 3),
+            "total_ms": round(open_ms + emit_ms, 3), "merge_ms": round(merge_ms, 3),
+            "rows": m_expect, "note": "open is host-timed (it ends with the count read back); emit by CUDA events"}
+
+
+def zipf_device(n: int, n_values: int, s: float, gen, dev):
+    """n keys in [0, n_values), P(key = k-1) proportional to k^-s, by inverse CDF on the device."""
+    import torch
+    k = torch.arange(1, n_values + 1, dtype=torch.float64, device=dev)
+    cdf = torch.cumsum(k.pow(-s), 0)
+    cdf /= cdf[-1].clone()
+    u = torch.rand(n, generator=gen, dtype=torch.float64, device=dev)
+    return torch.searchsorted(cdf, u, right=True).clamp_(max=n_values - 1).to(torch.int64)
+
+
+def streamed_section(args, dev):
+    """The skewed many-to-many workload (Zipf(1.1) keys over 1e7 values on both
+    sides, 50M x 200M rows, P = 64; about 2.0e14 joined rows) through the
+    streamed-output path: mdj_stream_open once, then windows of 2^26 rows at
+    offsets spread over the whole result, each written by one emit kernel into
+    one reused 2.1 GB buffer.  Keys and payloads are drawn on the device
+    (seeded torch generator) with the distribution of the test generator."""
+    import torch
+    from paper_2101_08878_gb300 import mdj
+
+    n_l, n_r, nvals, P_z = 50_000_000, 200_000_000, 10_000_000, 64
+    g = torch.Generator(device=dev)
+    g.manual_seed(2)
+    L = [zipf_device(n_l, nvals, 1.1, g, dev), torch.rand(n_l, generator=g, dtype=torch.float64, device=dev)]
+    R = [zipf_device(n_r, nvals, 1.1, g, dev), torch.rand(n_r, generator=g, dtype=torch.float64, device=dev)]
+    torch.cuda.synchronize()
+    mdj.MergeStream(L, R, P_z).close()  # first launches of the stream kernels
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = mdj.MergeStream(L, R, P_z)
+    open_s = time.perf_counter() - t0
+    m = st.total_rows
+    W = 1 << 26
+    buf = st.buffers(W)
+    stream = torch.cuda.current_stream(dev)
+    k = args.stream_windows
+    offsets = [int(i * (m - W) // max(k - 1, 1)) for i in range(k)]
+    st.emit(offsets[0], W, buf)  # warm
+    ms = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for q0 in offsets:
+        e0.record(stream)
+        st.emit(q0, W, buf)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    # a row of every window is checked against its source rows
+    li = buf.left_row[-1].view(torch.int32).to(torch.int64)
+    ri = buf.right_row[-1].view(torch.int32).to(torch.int64)
+    assert int(L[0][li]) == int(R[0][ri]) == int(buf.key[-1])
+    st.close()
+    peak, _ = peaks()
+    med = statistics.median(ms)
+    per_row = OUT_ROW + RID + PAY  # written row + the grouped build side's row id and payload read
+    achieved = per_row * W / (med / 1e3) / 1e9
+    rate = W / (med / 1e3)
+    return {"workload": f"Zipf(1.1) over {nvals} values both sides, {n_l} x {n_r} rows, P={P_z}, int64 key + "
+                        "float64 payload (drawn on the device, seeded)",
+            "total_rows": m, "open_ms": round(open_s * 1e3, 2),
+            "open_input_rows_per_s": (n_l + n_r) / open_s,
+            "window_rows": W, "windows": k, "window_offsets": offsets, "ms_per_window": [round(x, 4) for x in ms],
+            "emit": {"value": rate, "unit": "output rows/s", "ms_per_window": round(med, 4),
+                     "roofline": {"bound": "hbm", "kernel": "stream_emit", "achieved": round(achieved, 1),
+                                  "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                                  "alg_bytes_per_row": per_row,
+                                  "note": "32 B written + 12 B grouped build side read per row; probe-side "
+                                          "and entry reads not counted"}},
+            "all_rows_estimate_s": round(m / rate, 1)}
 
 
 def batched_section(args, dev):
@@ -536,6 +645,8 @@ def main():
     ap.add_argument("--serve-batch-rows", type=int, default=80_000_000,
                     help="input rows per continuous-batching group at most (larger requests run alone)")
     ap.add_argument("--serve-pool", type=int, default=32, help="distinct table pairs the requests draw from")
+    ap.add_argument("--stream-windows", type=int, default=6,
+                    help="windows of the streamed-output section (0 skips it)")
     ap.add_argument("--rows", type=int, default=None,
                     help="rows per side (default 100M); smaller values are for profiling captures only")
     args = ap.parse_args()

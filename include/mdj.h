@@ -251,6 +251,70 @@ MDJ_API int mdj_merge_batch(const mdj_table *left, int32_t left_key, const uint6
                             const mdj_allocator *alloc, void *stream, mdj_result *out,
                             uint64_t *req_offsets);
 
+/*
+ * Streamed output: the join of mdj_merge written window by window into
+ * buffers the caller owns, for results too large to hold at once (the
+ * many-to-many merge of Sec. V-B with skewed keys, where one heavy key can
+ * produce more rows than device memory holds).  The paper's runtime moves a
+ * large message in bounded pieces (its 1 GB chunking of transfers, Sec. IV-B);
+ * this is the same idea applied to the merge's output.
+ *
+ * mdj_stream_open - the merge of mdj_merge (shuffle into P partitions, then
+ * every partition pair) up to its output: both tables are shuffled, in every
+ * partition pair the build (left) rows are grouped by key, and every probe
+ * (right) row learns its key's group.  That fixes an order on the join's
+ * rows: matching right rows in shuffled order, each followed through the left
+ * rows of its key.  Row q of that order is the same in every later window.
+ *   *out        : the handle (close it with mdj_stream_close)
+ *   *total_rows : the number of joined rows (exact, 64-bit)
+ * Skew is handled on either side with no special input: a key may have any
+ * number of rows on either side.  The handle holds on the device the shuffled
+ * right table (key, columns, uint32 row id), the grouped left row ids and
+ * columns, and 16 bytes per matching right row, until mdj_stream_close.
+ * The input tables must stay valid and unchanged until mdj_stream_close (with
+ * P = 1 and a small left table the right table is read in place).  The
+ * allocator struct is copied; its callbacks and ctx must stay valid until
+ * mdj_stream_close.  Synchronises `stream`; later calls on the handle run on
+ * that stream.  Errors: those of mdj_merge; on error *out is NULL.
+ */
+typedef struct mdj_stream mdj_stream;
+
+/* One window of output rows: device buffers owned by the caller, each with
+ * room for the window's rows.  A NULL pointer skips that column.
+ *   key, left_row, right_row, left_cols, right_cols : as in mdj_result (the
+ *   columns of each side are its non-key columns in table order). */
+typedef struct {
+    void *key;
+    uint32_t *left_row;
+    uint32_t *right_row;
+    void *left_cols[MDJ_MAX_COLS];
+    void *right_cols[MDJ_MAX_COLS];
+} mdj_window;
+
+MDJ_API int mdj_stream_open(const mdj_table *left, int32_t left_key, const mdj_table *right, int32_t right_key,
+                            uint32_t P, const mdj_allocator *alloc, void *stream, mdj_stream **out,
+                            uint64_t *total_rows);
+
+/* Writes rows [first_row, first_row + nrows) of the handle's order into
+ * out's buffers (element i of a buffer = row first_row + i).  Any window may
+ * be written, in any order, any number of times; each call is one kernel
+ * launch on the open stream and does not synchronise.  first_row + nrows
+ * must not exceed total_rows (else MDJ_ERR_INVALID_ARG); nrows = 0 is a no-op. */
+MDJ_API int mdj_stream_emit(mdj_stream *s, uint64_t first_row, uint64_t nrows, const mdj_window *out);
+
+/* The resumable cursor: writes the next min(max_rows, rows left) rows after
+ * the handle's cursor (initially 0) into out, reports them as
+ * [*first_row, *first_row + *nrows) and advances the cursor; *nrows = 0 once
+ * every row has been written. */
+MDJ_API int mdj_stream_next(mdj_stream *s, uint64_t max_rows, const mdj_window *out, uint64_t *first_row,
+                            uint64_t *nrows);
+
+/* total_rows of the handle (0 for NULL). */
+MDJ_API uint64_t mdj_stream_rows(const mdj_stream *s);
+
+/* Releases every device buffer of the handle (stream order) and the handle. */
+MDJ_API void mdj_stream_close(mdj_stream *s);
+
 /* Releases every array of *res with `alloc` (stream order) and zeroes *res. */
 MDJ_API void mdj_result_release(mdj_result *res, const mdj_allocator *alloc, void *stream);
 

@@ -35,7 +35,8 @@ _MDJ_TO_TORCH = {v: k for k, v in _TORCH_TO_MDJ.items()}
 
 EXPORTED = [
     "mdj_partition", "mdj_partition_noalloc", "mdj_join", "mdj_merge", "mdj_count_checksum", "mdj_join_batch",
-    "mdj_merge_batch",
+    "mdj_merge_batch", "mdj_stream_open", "mdj_stream_emit", "mdj_stream_next", "mdj_stream_rows",
+    "mdj_stream_close",
     "mdj_result_release",
     "mdj_status_string", "mdj_last_error", "mdj_version", "mdj_profile_enable", "mdj_profile_reset",
     "mdj_profile_collect", "mdj_profile_count", "mdj_profile_get",
@@ -72,6 +73,13 @@ class MdjResult(ctypes.Structure):
         ("n_right_cols", ctypes.c_int32), ("left_dtypes", ctypes.c_int32 * MDJ_MAX_COLS),
         ("right_dtypes", ctypes.c_int32 * MDJ_MAX_COLS), ("key", ctypes.c_void_p),
         ("left_row", ctypes.c_void_p), ("right_row", ctypes.c_void_p),
+        ("left_cols", ctypes.c_void_p * MDJ_MAX_COLS), ("right_cols", ctypes.c_void_p * MDJ_MAX_COLS),
+    ]
+
+
+class MdjWindow(ctypes.Structure):
+    _fields_ = [
+        ("key", ctypes.c_void_p), ("left_row", ctypes.c_void_p), ("right_row", ctypes.c_void_p),
         ("left_cols", ctypes.c_void_p * MDJ_MAX_COLS), ("right_cols", ctypes.c_void_p * MDJ_MAX_COLS),
     ]
 
@@ -115,6 +123,17 @@ def load(path: str = LIB_PATH):
         lib.mdj_merge_batch.restype = ctypes.c_int
         lib.mdj_merge_batch.argtypes = [P(MdjTable), i32, P(u64), P(MdjTable), i32, P(u64), i32, P(u32),
                                         P(MdjTuning), P(MdjAllocator), vp, P(MdjResult), P(u64)]
+        lib.mdj_stream_open.restype = ctypes.c_int
+        lib.mdj_stream_open.argtypes = [P(MdjTable), i32, P(MdjTable), i32, u32, P(MdjAllocator), vp, P(vp),
+                                        P(u64)]
+        lib.mdj_stream_emit.restype = ctypes.c_int
+        lib.mdj_stream_emit.argtypes = [vp, u64, u64, P(MdjWindow)]
+        lib.mdj_stream_next.restype = ctypes.c_int
+        lib.mdj_stream_next.argtypes = [vp, u64, P(MdjWindow), P(u64), P(u64)]
+        lib.mdj_stream_rows.restype = u64
+        lib.mdj_stream_rows.argtypes = [vp]
+        lib.mdj_stream_close.restype = None
+        lib.mdj_stream_close.argtypes = [vp]
         lib.mdj_result_release.restype = None
         lib.mdj_result_release.argtypes = [P(MdjResult), P(MdjAllocator), vp]
         lib.mdj_status_string.restype = ctypes.c_char_p
@@ -350,6 +369,113 @@ def mdj_merge_batch(left_cols: Sequence[torch.Tensor], right_cols: Sequence[torc
                              out_c)
     _check(rc, "mdj_merge_batch")
     return _adopt_result(res, alloc), [int(x) for x in out_c]
+
+
+class MergeStream:
+    """The merge of mdj_merge, written window by window (mdj_stream_* in mdj.h).
+
+    Opening runs the shuffle and groups the left rows by key; `total_rows`
+    is then exact, and rows [q0, q0 + n) of the fixed output order can be
+    written at any time into a window buffer.  The handle's device memory
+    comes from torch's caching allocator and is held until close().  The
+    input tensors must stay alive and unchanged until close()."""
+
+    def __init__(self, left_cols: Sequence[torch.Tensor], right_cols: Sequence[torch.Tensor], P: int,
+                 left_key: int = 0, right_key: int = 0):
+        lib = load()
+        self._lib = lib
+        self.device = left_cols[0].device
+        self._inputs = (list(left_cols), list(right_cols))
+        lt, lk = _table(left_cols)
+        rt, rk = _table(right_cols)
+        self._alloc = TorchAllocator(self.device)
+        self._h = ctypes.c_void_p()
+        total = ctypes.c_uint64(0)
+        rc = lib.mdj_stream_open(ctypes.byref(lt), left_key, ctypes.byref(rt), right_key, P,
+                                 ctypes.byref(self._alloc.struct), _stream_handle(self.device),
+                                 ctypes.byref(self._h), ctypes.byref(total))
+        _check(rc, "mdj_stream_open")
+        self.total_rows = int(total.value)
+        self.key_dtype = left_cols[left_key].dtype
+        self.left_dtypes = [c.dtype for j, c in enumerate(left_cols) if j != left_key]
+        self.right_dtypes = [c.dtype for j, c in enumerate(right_cols) if j != right_key]
+
+    def buffers(self, rows: int) -> JoinResult:
+        """A window buffer of `rows` rows (every column) on the handle's device."""
+        dev = self.device
+        return JoinResult(rows, torch.empty(rows, dtype=self.key_dtype, device=dev),
+                          torch.empty(rows, dtype=torch.uint32, device=dev),
+                          torch.empty(rows, dtype=torch.uint32, device=dev),
+                          [torch.empty(rows, dtype=d, device=dev) for d in self.left_dtypes],
+                          [torch.empty(rows, dtype=d, device=dev) for d in self.right_dtypes])
+
+    @staticmethod
+    def _window(buf: JoinResult, nrows: int) -> MdjWindow:
+        w = MdjWindow()
+        for name in ("key", "left_row", "right_row"):
+            t = getattr(buf, name)
+            if t is not None:
+                if t.numel() < nrows:
+                    raise ValueError(f"window buffer {name} holds {t.numel()} rows, {nrows} needed")
+                setattr(w, name, t.data_ptr() if nrows else None)
+        for side, arr in (("left_cols", w.left_cols), ("right_cols", w.right_cols)):
+            for j, t in enumerate(getattr(buf, side)):
+                if t is not None:
+                    if t.numel() < nrows:
+                        raise ValueError(f"window buffer {side}[{j}] holds {t.numel()} rows, {nrows} needed")
+                    arr[j] = t.data_ptr() if nrows else None
+        return w
+
+    def emit(self, first_row: int, nrows: int, buf: JoinResult) -> JoinResult:
+        """Rows [first_row, first_row + nrows) into `buf` (None entries are skipped);
+        returns views of the written rows."""
+        if self._h is None:
+            raise RuntimeError("stream is closed")
+        w = self._window(buf, nrows)
+        _check(self._lib.mdj_stream_emit(self._h, first_row, nrows, ctypes.byref(w)), "mdj_stream_emit")
+        return _view(buf, nrows)
+
+    def next(self, buf: JoinResult, max_rows: Optional[int] = None):
+        """The next window after the cursor (at most max_rows, default the buffer's
+        rows): (first_row, views); views.nrows == 0 at the end."""
+        if self._h is None:
+            raise RuntimeError("stream is closed")
+        cap = buf.nrows if max_rows is None else int(max_rows)
+        w = self._window(buf, min(cap, self.total_rows))
+        first, n = ctypes.c_uint64(0), ctypes.c_uint64(0)
+        _check(self._lib.mdj_stream_next(self._h, cap, ctypes.byref(w), ctypes.byref(first), ctypes.byref(n)),
+               "mdj_stream_next")
+        return int(first.value), _view(buf, int(n.value))
+
+    def windows(self, rows: int):
+        """Iterates (first_row, views) over the whole result through one buffer of
+        `rows` rows; each window is valid until the next iteration."""
+        buf = self.buffers(rows)
+        for q0 in range(0, self.total_rows, rows):
+            yield q0, self.emit(q0, min(rows, self.total_rows - q0), buf)
+
+    def close(self):
+        if self._h is not None:
+            self._lib.mdj_stream_close(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+
+def _view(buf: JoinResult, n: int) -> JoinResult:
+    cut = (lambda t: None if t is None else t[:n])
+    return JoinResult(n, cut(buf.key), cut(buf.left_row), cut(buf.right_row), [cut(t) for t in buf.left_cols],
+                      [cut(t) for t in buf.right_cols])
 
 
 def mdj_status_string(status: int) -> str:

@@ -77,3 +77,44 @@ def test_argument_checks_need_no_gpu(lib):
     assert lib.mdj_partition(ctypes.byref(bt), 0, 4, None, None, None, None, None) == -2
     many = MdjTable(cols, 17, 0)
     assert lib.mdj_join(ctypes.byref(many), 0, ctypes.byref(t), 0, None, None, ctypes.byref(res)) == -1
+
+
+def test_stream_argument_checks_need_no_gpu(lib):
+    from paper_2101_08878_gb300.mdj import MdjCol, MdjTable, MdjWindow
+    h = ctypes.c_void_p()
+    total = ctypes.c_uint64(7)
+    cols = (MdjCol * 1)()
+    cols[0].dtype = 2
+    t = MdjTable(cols, 1, 0)
+    # null tables, bad key index, P out of range, float key, key dtype mismatch
+    assert lib.mdj_stream_open(None, 0, ctypes.byref(t), 0, 8, None, None, ctypes.byref(h),
+                               ctypes.byref(total)) == -1
+    assert h.value is None and total.value == 0
+    assert lib.mdj_stream_open(ctypes.byref(t), 1, ctypes.byref(t), 0, 8, None, None, ctypes.byref(h),
+                               ctypes.byref(total)) == -1
+    assert lib.mdj_stream_open(ctypes.byref(t), 0, ctypes.byref(t), 0, 0, None, None, ctypes.byref(h),
+                               ctypes.byref(total)) == -1
+    assert lib.mdj_stream_open(ctypes.byref(t), 0, ctypes.byref(t), 0, 65537, None, None, ctypes.byref(h),
+                               ctypes.byref(total)) == -1
+    fcols = (MdjCol * 1)()
+    fcols[0].dtype = 4
+    ft = MdjTable(fcols, 1, 0)
+    assert lib.mdj_stream_open(ctypes.byref(ft), 0, ctypes.byref(ft), 0, 8, None, None, ctypes.byref(h),
+                               ctypes.byref(total)) == -2
+    icols = (MdjCol * 1)()
+    icols[0].dtype = 1
+    it = MdjTable(icols, 1, 0)
+    assert lib.mdj_stream_open(ctypes.byref(t), 0, ctypes.byref(it), 0, 8, None, None, ctypes.byref(h),
+                               ctypes.byref(total)) == -1
+    big = MdjTable(cols, 1, 1 << 32)
+    assert lib.mdj_stream_open(ctypes.byref(big), 0, ctypes.byref(t), 0, 8, None, None, ctypes.byref(h),
+                               ctypes.byref(total)) == -3
+    assert lib.mdj_stream_open(ctypes.byref(t), 0, ctypes.byref(t), 0, 8, None, None, None,
+                               ctypes.byref(total)) == -1
+    # calls on a missing handle
+    w = MdjWindow()
+    first, n = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    assert lib.mdj_stream_emit(None, 0, 0, ctypes.byref(w)) == -1
+    assert lib.mdj_stream_next(None, 10, ctypes.byref(w), ctypes.byref(first), ctypes.byref(n)) == -1
+    assert lib.mdj_stream_rows(None) == 0
+    lib.mdj_stream_close(None)
