@@ -115,9 +115,8 @@ struct HeavyUnit {
 struct GOut {
   uint32_t *grid;                  // grouped build side: input row ids
   void *gcols[MDJ_MAX_COLS];       // grouped build side: non-key columns
-  uint64_t *cnt;                   // per probe row: group size (0 = no match); [nR] = 0
+  uint32_t *cnt;                   // per probe row: group size (0 = no match)
   uint32_t *gbase;                 // per probe row: first grouped position of its group
-  uint32_t *matched;               // per probe row: cnt != 0; [nR] = 0
 };
 
 // In-table position and tag of a key: multiplicative hash of the key bits
@@ -141,9 +140,16 @@ __host__ __device__ __forceinline__ uint32_t small_logt(uint32_t nl) {
   return logt;
 }
 
+// Shared-memory layout of a group table (and of its saved copy): keys[kGCap],
+// slots[kGTab], base[kGCap + 1], then the block-scan scratch (33 words).
+template <typename KeyT>
+__host__ __device__ constexpr size_t group_slots_at() {
+  return (size_t)kGCap * sizeof(KeyT);
+}
+constexpr size_t kGBaseWords = kGCap + 1;
 template <typename KeyT>
 __host__ __device__ constexpr size_t group_smem_bytes() {
-  return (size_t)kGCap * sizeof(KeyT) + (size_t)kGTab * 4 + (size_t)(kGTab + 1) * 4 + 33 * 4;
+  return group_slots_at<KeyT>() + (size_t)kGTab * 4 + kGBaseWords * 4 + 33 * 4;
 }
 
 template <typename KeyT>
@@ -158,10 +164,22 @@ __device__ __forceinline__ void copy_col(void *dst, uint64_t di, const void *src
     ((uint32_t *)dst)[di] = ((const uint32_t *)src)[si];
 }
 
-// Probe rows [r0, r0 + nr) against a shared-memory group table (keys, slot
-// words tag << 16 | representative + 1, base = exclusive prefix of group
-// sizes over slots, base[T] = nl).  Four rows per thread are loaded before
-// any is probed.
+// Probe rows [r0, r0 + nr) against a shared-memory group table: keys, slot
+// words tag << 16 | representative + 1 (the build row that claimed the slot),
+// and base = exclusive prefix over build rows of the group sizes, each size
+// counted at its representative, so a group starts at base[rep] and has
+// base[rep + 1] - base[rep] rows.  Four rows per thread are loaded before any
+// is probed.
+template <typename KeyT>
+__device__ __forceinline__ void load_probe_batch(const KeyT *__restrict__ Rk, uint32_t r0, uint32_t nr, uint32_t i0,
+                                                 KeyT (&kv)[4]) {
+#pragma unroll
+  for (int u = 0; u < 4; u++) {
+    const uint32_t i = i0 + u * kGT + threadIdx.x;
+    kv[u] = i < nr ? Rk[r0 + i] : KeyT(0);
+  }
+}
+
 template <typename KeyT>
 __device__ __forceinline__ void probe_small(const KeyT *keys, const uint32_t *slots, const uint32_t *base, uint32_t logt,
                                             uint32_t lb, const KeyT *__restrict__ Rk, uint32_t r0, uint32_t nr,
@@ -169,43 +187,61 @@ __device__ __forceinline__ void probe_small(const KeyT *keys, const uint32_t *sl
   const uint32_t mask = (1u << logt) - 1;
   for (uint32_t i0 = 0; i0 < nr; i0 += 4 * kGT) {
     KeyT kv[4];
-#pragma unroll
-    for (int u = 0; u < 4; u++) {
-      const uint32_t i = i0 + u * kGT + threadIdx.x;
-      kv[u] = i < nr ? Rk[r0 + i] : KeyT(0);
-    }
+    load_probe_batch(Rk, r0, nr, i0, kv);
 #pragma unroll
     for (int u = 0; u < 4; u++) {
       const uint32_t i = i0 + u * kGT + threadIdx.x;
       if (i >= nr) continue;
       uint32_t s, tag;
       small_slot_tag(key_bits(kv[u]), logt, s, tag);
-      bool found = false;
+      uint32_t rep = 0xFFFFFFFFu;
       for (uint32_t p = 0; p <= mask; p++) {
         const uint32_t w = slots[s];
         if (w == 0) break;
         if ((w >> 16) == tag && keys[(w & 0xFFFFu) - 1] == kv[u]) {
-          found = true;
+          rep = (w & 0xFFFFu) - 1;
           break;
         }
         s = (s + 1) & mask;
       }
-      const uint32_t c = found ? base[s + 1] - base[s] : 0u;
-      o.cnt[r0 + i] = c;
-      o.gbase[r0 + i] = found ? lb + base[s] : 0u;
-      o.matched[r0 + i] = c != 0;
+      const bool found = rep != 0xFFFFFFFFu;
+      o.cnt[r0 + i] = found ? base[rep + 1] - base[rep] : 0u;
+      o.gbase[r0 + i] = found ? lb + base[rep] : 0u;
     }
   }
+}
+
+// One column of the build rows lb + threadIdx.x + k * kGT (k < kGRows, below
+// lb + nl) to grouped order: values to their local positions pos[k] in the
+// shared staging area (all loads first), then out to dst[lb ..) with
+// coalesced stores.  src NULL: the identity (row index).  Ends with a barrier.
+template <typename V>
+__device__ __forceinline__ void stage_column(V *__restrict__ dst, const V *__restrict__ src, uint32_t lb, uint32_t nl,
+                                             const uint32_t (&pos)[kGRows], unsigned char *stage_bytes) {
+  V *stage = (V *)stage_bytes;
+  V v[kGRows];
+#pragma unroll
+  for (int k = 0; k < kGRows; k++) {
+    const uint32_t i = threadIdx.x + k * kGT;
+    if (i < nl) v[k] = src ? src[lb + i] : (V)(lb + i);
+  }
+#pragma unroll
+  for (int k = 0; k < kGRows; k++)
+    if (threadIdx.x + k * kGT < nl) stage[pos[k]] = v[k];
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < nl; i += kGT) dst[lb + i] = stage[i];
+  __syncthreads();
 }
 
 // ------------------------------------------------------- light sub-buckets
 //
 // One unit per light sub-bucket (build side <= kGCap rows): build keys to
 // shared memory; one slot per distinct key (linear probing, compare-and-swap
-// on an empty slot), a build row's rank in its group from an atomicAdd on the
-// slot's count; block scan of the counts over slots = group starts; each
-// build row's input row id and columns are written at lb + start + rank; then
-// the first probe chunk is probed.  Units of an empty build side only write
+// on an empty slot; the row whose swap claimed the slot represents the group);
+// a build row's rank in its group from an atomicAdd on the count kept at its
+// representative; block scan of those counts over the build rows = group
+// starts; the first probe chunk is probed; each build row's input row id and
+// columns go to lb + start + rank.  Units of an empty build side only write
 // zero counts.
 template <typename KeyT>
 __global__ void __launch_bounds__(kGT, 2)
@@ -213,9 +249,9 @@ __global__ void __launch_bounds__(kGT, 2)
                   unsigned char *__restrict__ dumps) {
   extern __shared__ __align__(16) unsigned char smem[];
   KeyT *keys = (KeyT *)smem;
-  uint32_t *slots = (uint32_t *)(smem + (size_t)kGCap * sizeof(KeyT));
+  uint32_t *slots = (uint32_t *)(smem + group_slots_at<KeyT>());
   uint32_t *base = slots + kGTab;
-  uint32_t *scratch = base + kGTab + 1;
+  uint32_t *scratch = base + kGBaseWords;
   __shared__ uint32_t s_u;
   const KeyT *Lk = (const KeyT *)L.key;
   const KeyT *Rk = (const KeyT *)R.key;
@@ -231,15 +267,23 @@ __global__ void __launch_bounds__(kGT, 2)
       for (uint32_t r = U.r0 + threadIdx.x; r < U.r0 + U.nr; r += kGT) {
         o.cnt[r] = 0;
         o.gbase[r] = 0;
-        o.matched[r] = 0;
       }
       continue;
     }
     const uint32_t logt = small_logt(nl), T = 1u << logt, mask = T - 1;
-    for (uint32_t i = threadIdx.x; i < nl; i += kGT) keys[i] = Lk[lb + i];
-    for (uint32_t s = threadIdx.x; s <= T; s += kGT) {
-      if (s < T) slots[s] = 0;
-      base[s] = 0;
+    // every load of the build keys is issued before the first store
+    KeyT kr[kGRows];
+#pragma unroll
+    for (int k = 0; k < kGRows; k++) {
+      const uint32_t i = threadIdx.x + k * kGT;
+      kr[k] = i < nl ? Lk[lb + i] : KeyT(0);
+    }
+    for (uint32_t s = threadIdx.x; s < T; s += kGT) slots[s] = 0;
+    for (uint32_t i = threadIdx.x; i <= nl; i += kGT) base[i] = 0;
+#pragma unroll
+    for (int k = 0; k < kGRows; k++) {
+      const uint32_t i = threadIdx.x + k * kGT;
+      if (i < nl) keys[i] = kr[k];
     }
     __syncthreads();
     uint32_t sk[kGRows], rk[kGRows];
@@ -253,6 +297,7 @@ __global__ void __launch_bounds__(kGT, 2)
         uint32_t s, tag;
         small_slot_tag(key_bits(kk), logt, s, tag);
         const uint32_t w = (tag << 16) | (i + 1);
+        uint32_t rep = i;
         for (uint32_t p = 0; p <= mask; p++) {  // ends: 2 slots per row, so a free slot exists
           uint32_t cur = slots[s];
           if (cur == 0) {
@@ -260,37 +305,42 @@ __global__ void __launch_bounds__(kGT, 2)
             if (prev == 0) break;
             cur = prev;
           }
-          if ((cur >> 16) == tag && keys[(cur & 0xFFFFu) - 1] == kk) break;
+          if ((cur >> 16) == tag && keys[(cur & 0xFFFFu) - 1] == kk) {
+            rep = (cur & 0xFFFFu) - 1;
+            break;
+          }
           s = (s + 1) & mask;
         }
-        sk[k] = s;
-        rk[k] = atomicAdd(&base[s], 1u);
+        sk[k] = rep;
+        rk[k] = atomicAdd(&base[rep], 1u);
       }
     }
     __syncthreads();
-    block_scan_array(base, T + 1, scratch);
-#pragma unroll
-    for (int k = 0; k < kGRows; k++) {
-      const uint32_t i = threadIdx.x + k * kGT;
-      if (i < nl) {
-        const uint32_t pos = lb + base[sk[k]] + rk[k];
-        o.grid[pos] = L.rid ? L.rid[lb + i] : lb + i;
-        for (int c = 0; c < L.ncols; c++) copy_col(o.gcols[c], pos, L.cols[c], lb + i, L.width[c]);
-      }
-    }
+    block_scan_array(base, nl + 1, scratch);
     if (U.dump >= 0) {  // later probe chunks of this sub-bucket reload this exact table
       unsigned char *d = dumps + (size_t)U.dump * dump_stride<KeyT>();
       KeyT *dk = (KeyT *)d;
-      uint32_t *ds = (uint32_t *)(d + (size_t)kGCap * sizeof(KeyT));
+      uint32_t *ds = (uint32_t *)(d + group_slots_at<KeyT>());
       uint32_t *db = ds + kGTab;
       for (uint32_t i = threadIdx.x; i < nl; i += kGT) dk[i] = keys[i];
-      for (uint32_t s = threadIdx.x; s <= T; s += kGT) {
-        if (s < T) ds[s] = slots[s];
-        db[s] = base[s];
-      }
+      for (uint32_t s = threadIdx.x; s < T; s += kGT) ds[s] = slots[s];
+      for (uint32_t i = threadIdx.x; i <= nl; i += kGT) db[i] = base[i];
     }
     probe_small<KeyT>(keys, slots, base, logt, lb, Rk, U.r0, U.nr, o);
+    // grouped order: each build row's position in the group order of the
+    // sub-bucket; keys and slots are dead after the probe, so their space
+    // stages one column at a time and the column leaves with coalesced stores
+#pragma unroll
+    for (int k = 0; k < kGRows; k++) sk[k] = base[sk[k]] + rk[k];
     __syncthreads();
+    stage_column<uint32_t>(o.grid, L.rid, lb, nl, sk, smem);
+#pragma unroll 1
+    for (int c = 0; c < L.ncols; c++) {
+      if (L.width[c] == 8)
+        stage_column<uint64_t>((uint64_t *)o.gcols[c], (const uint64_t *)L.cols[c], lb, nl, sk, smem);
+      else
+        stage_column<uint32_t>((uint32_t *)o.gcols[c], (const uint32_t *)L.cols[c], lb, nl, sk, smem);
+    }
   }
 }
 
@@ -301,7 +351,7 @@ __global__ void __launch_bounds__(kGT, 2)
                    const unsigned char *__restrict__ dumps) {
   extern __shared__ __align__(16) unsigned char smem[];
   KeyT *keys = (KeyT *)smem;
-  uint32_t *slots = (uint32_t *)(smem + (size_t)kGCap * sizeof(KeyT));
+  uint32_t *slots = (uint32_t *)(smem + group_slots_at<KeyT>());
   uint32_t *base = slots + kGTab;
   const KeyT *Rk = (const KeyT *)R.key;
   for (uint32_t u = blockIdx.x; u < nunits; u += gridDim.x) {
@@ -310,13 +360,11 @@ __global__ void __launch_bounds__(kGT, 2)
     const uint32_t logt = small_logt(nl), T = 1u << logt;
     const unsigned char *d = dumps + (size_t)U.dump * dump_stride<KeyT>();
     const KeyT *dk = (const KeyT *)d;
-    const uint32_t *ds = (const uint32_t *)(d + (size_t)kGCap * sizeof(KeyT));
+    const uint32_t *ds = (const uint32_t *)(d + group_slots_at<KeyT>());
     const uint32_t *db = ds + kGTab;
     for (uint32_t i = threadIdx.x; i < nl; i += kGT) keys[i] = dk[i];
-    for (uint32_t s = threadIdx.x; s <= T; s += kGT) {
-      if (s < T) slots[s] = ds[s];
-      base[s] = db[s];
-    }
+    for (uint32_t s = threadIdx.x; s < T; s += kGT) slots[s] = ds[s];
+    for (uint32_t i = threadIdx.x; i <= nl; i += kGT) base[i] = db[i];
     __syncthreads();
     probe_small<KeyT>(keys, slots, base, logt, lb, Rk, U.r0, U.nr, o);
     __syncthreads();
@@ -417,28 +465,114 @@ __global__ void __launch_bounds__(kHT)
       const uint32_t c = found ? hbase[H.ts0 + s + 1] - hbase[H.ts0 + s] : 0u;
       o.cnt[r] = c;
       o.gbase[r] = found ? H.lb + (hbase[H.ts0 + s] - H.hr0) : 0u;
-      o.matched[r] = c != 0;
     }
   }
 }
 
 // ------------------------------------------------------------- entries
+//
+// Matching probe rows, in shuffled order, become entries (first output row,
+// probe row, group start); moff[nm] = total rows.  Reduce, scan, rescan:
+// k_entry_sums sums each chunk of kCChunk probe rows (rows and entries),
+// the chunk sums are scanned, and k_entry_write rescans its chunk from the
+// counts and writes the chunk's entries at its base.  Within a block both
+// sums travel in one 64-bit scan, packed rows << 13 | entries (a chunk has at
+// most 4096 entries and fewer than 2^44 rows).
+constexpr int kCT = 512;
+constexpr int kCRows = 8;
+constexpr uint32_t kCChunk = kCT * kCRows;
+static_assert(kCChunk <= 8191, "entries of a chunk fit the packed low 13 bits");
 
-// Matching probe rows, in shuffled order: entry midx[r] = (first output row,
-// probe row, group start); moff[nm] = total rows.
-__global__ void k_compact(const uint64_t *__restrict__ off, const uint32_t *__restrict__ midx,
-                          const uint32_t *__restrict__ gbase, uint32_t nR, uint64_t *__restrict__ moff,
-                          uint32_t *__restrict__ mr, uint32_t *__restrict__ mg) {
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x; r < nR; r += stride) {
-    const uint32_t e = midx[r];
-    if (midx[r + 1] != e) {
-      moff[e] = off[r];
-      mr[e] = (uint32_t)r;
-      mg[e] = gbase[r];
-    }
+__device__ __forceinline__ void load_counts(const uint32_t *__restrict__ cnt, uint32_t nR, uint32_t r0,
+                                            uint32_t (&v)[kCRows]) {
+  if (r0 + kCRows <= nR) {
+    const uint4 a = *(const uint4 *)(cnt + r0), b = *(const uint4 *)(cnt + r0 + 4);
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < kCRows; k++) v[k] = r0 + k < nR ? cnt[r0 + k] : 0u;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) moff[midx[nR]] = off[nR];
+}
+
+__device__ __forceinline__ uint64_t packed_sum(const uint32_t (&v)[kCRows]) {
+  uint64_t rows = 0;
+  uint32_t ents = 0;
+#pragma unroll
+  for (int k = 0; k < kCRows; k++) {
+    rows += v[k];
+    ents += v[k] != 0;
+  }
+  return (rows << 13) | ents;
+}
+
+// chunk c: rows[c], ents[c] (nchunks + 1 entries each; the last stays 0)
+__global__ void __launch_bounds__(kCT)
+    k_entry_sums(const uint32_t *__restrict__ cnt, uint32_t nR, uint64_t *__restrict__ rows,
+                 uint32_t *__restrict__ ents) {
+  __shared__ uint64_t scratch[33];
+  const uint32_t r0 = blockIdx.x * kCChunk + threadIdx.x * kCRows;
+  uint32_t v[kCRows];
+  load_counts(cnt, nR, r0, v);
+  uint64_t tot;
+  block_exclusive_scan<uint64_t>(packed_sum(v), scratch, &tot);
+  if (threadIdx.x == 0) {
+    rows[blockIdx.x] = tot >> 13;
+    ents[blockIdx.x] = (uint32_t)(tot & 8191);
+  }
+}
+
+// rows / ents: exclusive prefixes over chunks (index nchunks = totals).  The
+// chunk's entries are staged in shared memory one array at a time and leave
+// with coalesced stores.
+__global__ void __launch_bounds__(kCT)
+    k_entry_write(const uint32_t *__restrict__ cnt, const uint32_t *__restrict__ gbase, uint32_t nR, uint32_t nchunks,
+                  const uint64_t *__restrict__ rows, const uint32_t *__restrict__ ents, uint64_t *__restrict__ moff,
+                  uint32_t *__restrict__ mr, uint32_t *__restrict__ mg) {
+  __shared__ uint64_t scratch[33];
+  __shared__ uint64_t stage[kCChunk];
+  uint32_t *stage32 = (uint32_t *)stage;
+  const uint32_t r0 = blockIdx.x * kCChunk + threadIdx.x * kCRows;
+  uint32_t v[kCRows];
+  load_counts(cnt, nR, r0, v);
+  uint32_t g[kCRows];
+#pragma unroll
+  for (int k = 0; k < kCRows; k++) g[k] = v[k] ? gbase[r0 + k] : 0u;
+  uint64_t tot;
+  const uint64_t ex = block_exclusive_scan<uint64_t>(packed_sum(v), scratch, &tot);
+  const uint64_t rbase = rows[blockIdx.x];
+  const uint32_t ebase = ents[blockIdx.x], n = (uint32_t)(tot & 8191);
+  const uint32_t e0 = (uint32_t)(ex & 8191);
+  {
+    uint64_t at = rbase + (ex >> 13);
+    uint32_t e = e0;
+#pragma unroll
+    for (int k = 0; k < kCRows; k++)
+      if (v[k]) {
+        stage[e++] = at;
+        at += v[k];
+      }
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < n; i += kCT) moff[ebase + i] = stage[i];
+  __syncthreads();
+  {
+    uint32_t e = e0;
+#pragma unroll
+    for (int k = 0; k < kCRows; k++)
+      if (v[k]) stage32[e++] = r0 + k;
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < n; i += kCT) mr[ebase + i] = stage32[i];
+  __syncthreads();
+  {
+    uint32_t e = e0;
+#pragma unroll
+    for (int k = 0; k < kCRows; k++)
+      if (v[k]) stage32[e++] = g[k];
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < n; i += kCT) mg[ebase + i] = stage32[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) moff[ents[nchunks]] = rows[nchunks];
 }
 
 // ------------------------------------------------------------------ emit
@@ -691,14 +825,11 @@ int group_and_index(Workspace &tmp, mdj_stream *h, const Side &L, const Side &R,
   if (!o.grid) return MDJ_ERR_OOM;
   for (int c = 0; c < L.ncols; c++)
     if (!(o.gcols[c] = keep.get((size_t)nL * L.widths[c]))) return MDJ_ERR_OOM;
-  o.cnt = (uint64_t *)tmp.get((size_t)(nR + 1) * 8);
+  o.cnt = (uint32_t *)tmp.get((size_t)nR * 4);
   o.gbase = (uint32_t *)tmp.get((size_t)nR * 4);
-  o.matched = (uint32_t *)tmp.get((size_t)(nR + 1) * 4);
-  int *err = (int *)tmp.get(16);  // set by a global-table kernel if a probe sequence ran out
-  if (!o.cnt || !o.gbase || !o.matched || !err) return MDJ_ERR_OOM;
+  int *err = (int *)tmp.get(16);  // [0]: a global-table probe sequence ran out
+  if (!o.cnt || !o.gbase || !err) return MDJ_ERR_OOM;
   MDJ_CUDA_TRY(cudaMemsetAsync(err, 0, 16, s));
-  MDJ_CUDA_TRY(cudaMemsetAsync(o.cnt + nR, 0, 8, s));
-  MDJ_CUDA_TRY(cudaMemsetAsync(o.matched + nR, 0, 4, s));
 
   int rc = MDJ_OK;
   LightUnit *d_first = upload(tmp, un.first, &rc);
@@ -760,31 +891,41 @@ int group_and_index(Workspace &tmp, mdj_stream *h, const Side &L, const Side &R,
     }
     MDJ_LAUNCH_CHECK();
   }
-  // output offsets of the probe rows, entry indices of the matching ones
-  MDJ_TRY(exclusive_scan_u64(tmp, o.cnt, o.cnt, (size_t)nR + 1));
-  MDJ_TRY(exclusive_scan_u32(tmp, o.matched, o.matched, (size_t)nR + 1));
+  // entries of the matching probe rows, with their first output rows
   EmitSrc &S = h->src;
   uint64_t *moff = (uint64_t *)keep.get((size_t)(nR + 1) * 8);
   uint32_t *mr = (uint32_t *)keep.get((size_t)nR * 4);
   uint32_t *mg = (uint32_t *)keep.get((size_t)nR * 4);
-  if (!moff || !mr || !mg) return MDJ_ERR_OOM;
+  const uint32_t nchunks = (uint32_t)(((size_t)nR + kCChunk - 1) / kCChunk);
+  uint64_t *crows = (uint64_t *)tmp.get((size_t)(nchunks + 1) * 8);
+  uint32_t *cents = (uint32_t *)tmp.get((size_t)(nchunks + 1) * 4);
+  if (!moff || !mr || !mg || !crows || !cents) return MDJ_ERR_OOM;
+  MDJ_CUDA_TRY(cudaMemsetAsync(crows + nchunks, 0, 8, s));
+  MDJ_CUDA_TRY(cudaMemsetAsync(cents + nchunks, 0, 4, s));
+  {
+    TraceScope tr("stream_entry_sums", s);
+    k_entry_sums<<<nchunks, kCT, 0, s>>>(o.cnt, nR, crows, cents);
+  }
+  MDJ_LAUNCH_CHECK();
+  MDJ_TRY(exclusive_scan_u64(tmp, crows, crows, (size_t)nchunks + 1));
+  MDJ_TRY(exclusive_scan_u32(tmp, cents, cents, (size_t)nchunks + 1));
   {
     TraceScope tr("stream_entries", s);
-    k_compact<<<grid_for(((size_t)nR + 255) / 256, 8), 256, 0, s>>>(o.cnt, o.matched, o.gbase, nR, moff, mr, mg);
+    k_entry_write<<<nchunks, kCT, 0, s>>>(o.cnt, o.gbase, nR, nchunks, crows, cents, moff, mr, mg);
   }
   MDJ_LAUNCH_CHECK();
   uint64_t total = 0;
   uint32_t nm = 0;
-  int herr = 0, pflag[2] = {0, 0};
-  MDJ_CUDA_TRY(cudaMemcpyAsync(&total, o.cnt + nR, 8, cudaMemcpyDeviceToHost, s));
-  MDJ_CUDA_TRY(cudaMemcpyAsync(&nm, o.matched + nR, 4, cudaMemcpyDeviceToHost, s));
-  MDJ_CUDA_TRY(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, s));
+  int herr[4] = {0, 0, 0, 0}, pflag[2] = {0, 0};
+  MDJ_CUDA_TRY(cudaMemcpyAsync(&total, crows + nchunks, 8, cudaMemcpyDeviceToHost, s));
+  MDJ_CUDA_TRY(cudaMemcpyAsync(&nm, cents + nchunks, 4, cudaMemcpyDeviceToHost, s));
+  MDJ_CUDA_TRY(cudaMemcpyAsync(herr, err, 16, cudaMemcpyDeviceToHost, s));
   // a shuffle pass that gave up on a bounded copy wait (opt-in bulk-copy scatter)
   if (tmp.flag_word_if_any()) MDJ_CUDA_TRY(cudaMemcpyAsync(&pflag[0], tmp.flag_word_if_any(), 4, cudaMemcpyDeviceToHost, s));
   if (keep.flag_word_if_any()) MDJ_CUDA_TRY(cudaMemcpyAsync(&pflag[1], keep.flag_word_if_any(), 4, cudaMemcpyDeviceToHost, s));
   MDJ_CUDA_TRY(cudaStreamSynchronize(s));
   if (pflag[0] || pflag[1]) return MDJ_ERR_DEVICE_TIMEOUT;
-  if (herr) return MDJ_ERR_INTERNAL;
+  if (herr[0]) return MDJ_ERR_INTERNAL;
   h->total = total;
   S.moff = moff;
   S.mr = mr;
