@@ -335,6 +335,9 @@ def run_gpu(args):
         torch.cuda.empty_cache()
         line["streamed"] = streamed_section(args, dev)
         line["streamed"]["plain_workload_one_window"] = stream_plain
+    if args.transpose_steps > 0:
+        torch.cuda.empty_cache()
+        line["transpose_sum"] = transpose_section(args, dev)
     if args.batch_pairs > 0:
         line["batched"] = batched_section(args, dev)
     if args.serve_requests > 0:
@@ -397,7 +400,8 @@ def streamed_section(args, dev):
     import torch
     from paper_2101_08878_gb300 import mdj
 
-    n_l, n_r, nvals, P_z = 50_000_000, 200_000_000, 10_000_000, 64
+    n_l, nvals, P_z = args.stream_left, 10_000_000, 64
+    n_r = 4 * n_l
     g = torch.Generator(device=dev)
     g.manual_seed(2)
     L = [zipf_device(n_l, nvals, 1.1, g, dev), torch.rand(n_l, generator=g, dtype=torch.float64, device=dev)]
@@ -409,7 +413,7 @@ def streamed_section(args, dev):
     st = mdj.MergeStream(L, R, P_z)
     open_s = time.perf_counter() - t0
     m = st.total_rows
-    W = 1 << 26
+    W = min(1 << 26, m)
     buf = st.buffers(W)
     stream = torch.cuda.current_stream(dev)
     k = args.stream_windows
@@ -445,6 +449,58 @@ def streamed_section(args, dev):
                                   "note": "32 B written + 12 B grouped build side read per row; probe-side "
                                           "and entry reads not counted"}},
             "all_rows_estimate_s": round(m / rate, 1)}
+
+
+def transpose_section(args, dev):
+    """The paper's other application benchmark, y = x + x.T on a float64
+    array: 16K x 16K (Fig. 7) and 20E3 x 20E3 (Fig. 9(a)), x drawn U[0,1) on
+    the device (seeded).  One step = one mdj_transpose_add call; algorithmic
+    bytes = 16 per element (x read once, y written once); arrays of 2-3 GB
+    are far larger than L2.  The CPU oracle (numpy x + x.T, one thread) is
+    timed on a 4096 x 4096 sample."""
+    import torch
+    from paper_2101_08878_gb300 import mdj
+    import oracle
+
+    peak, _ = peaks()
+    stream = torch.cuda.current_stream(dev)
+    sizes = []
+    for n in (16384, 20000):
+        g = torch.Generator(device=dev)
+        g.manual_seed(n)
+        x = torch.rand((n, n), generator=g, dtype=torch.float64, device=dev)
+        y = torch.empty_like(x)
+        for _ in range(3):
+            mdj.transpose_add(x, y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.transpose_steps):
+            mdj.transpose_add(x, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.transpose_steps
+        i, j = 12345 % n, n - 7
+        assert float(y[i, j]) == float(x[i, j]) + float(x[j, i])
+        alg = 16 * n * n
+        achieved = alg / (ms / 1e3) / 1e9
+        sizes.append({"n": n, "ms_per_step": round(ms, 4), "elements_per_s": n * n / (ms / 1e3),
+                      "roofline": {"bound": "hbm", "kernel": "transpose_add", "achieved": round(achieved, 1),
+                                   "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                                   "alg_bytes_per_launch": alg}})
+        del x, y
+        torch.cuda.empty_cache()
+    oracle.build()
+    xs = np.random.default_rng(0).random((4096, 4096))
+    oracle.transpose_add(xs)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        oracle.transpose_add(xs)
+    cpu_s = (time.perf_counter() - t0) / 3
+    return {"workload": "y = x + x.T, float64, 16384^2 and 20000^2 (x U[0,1) drawn on the device, seeded)",
+            "steps": args.transpose_steps, "sizes": sizes,
+            "cpu_baseline": {"value": 4096 * 4096 / cpu_s, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                             "sample": "numpy x + x.T on a 4096 x 4096 float64 array, one thread"}}
 
 
 def batched_section(args, dev):
@@ -645,8 +701,13 @@ def main():
     ap.add_argument("--serve-batch-rows", type=int, default=80_000_000,
                     help="input rows per continuous-batching group at most (larger requests run alone)")
     ap.add_argument("--serve-pool", type=int, default=32, help="distinct table pairs the requests draw from")
+    ap.add_argument("--transpose-steps", type=int, default=10,
+                    help="timed calls per size of the transpose-sum section (0 skips it)")
     ap.add_argument("--stream-windows", type=int, default=6,
                     help="windows of the streamed-output section (0 skips it)")
+    ap.add_argument("--stream-left", type=int, default=50_000_000,
+                    help="left rows of the streamed-output section (right = 4x); smaller values are for "
+                         "profiling captures only")
     ap.add_argument("--rows", type=int, default=None,
                     help="rows per side (default 100M); smaller values are for profiling captures only")
     args = ap.parse_args()

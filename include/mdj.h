@@ -263,8 +263,11 @@ MDJ_API int mdj_merge_batch(const mdj_table *left, int32_t left_key, const uint6
  * every partition pair) up to its output: both tables are shuffled, in every
  * partition pair the build (left) rows are grouped by key, and every probe
  * (right) row learns its key's group.  That fixes an order on the join's
- * rows: matching right rows in shuffled order, each followed through the left
- * rows of its key.  Row q of that order is the same in every later window.
+ * rows: right rows in shuffled order (the matching ones, or all with
+ * MDJ_RIGHT / MDJ_OUTER), each followed through the left rows of its key,
+ * then (MDJ_LEFT / MDJ_OUTER) the left rows no right row matched, grouped by
+ * key.  Row q of that order is the same in every later window.
+ *   how         : an mdj_how (else MDJ_ERR_INVALID_ARG)
  *   *out        : the handle (close it with mdj_stream_close)
  *   *total_rows : the number of joined rows (exact, 64-bit)
  * Skew is handled on either side with no special input: a key may have any
@@ -279,6 +282,15 @@ MDJ_API int mdj_merge_batch(const mdj_table *left, int32_t left_key, const uint6
  */
 typedef struct mdj_stream mdj_stream;
 
+/* Which rows a streamed join keeps (the usual merge variants):
+ *   MDJ_INNER : matching pairs only
+ *   MDJ_LEFT  : also every left row without a match, once, with no right row
+ *   MDJ_RIGHT : also every right row without a match, once, with no left row
+ *   MDJ_OUTER : both
+ * A missing side has row id 0xFFFFFFFF (UINT32_MAX) and all-zero bits in its
+ * columns; the key is the present side's. */
+typedef enum { MDJ_INNER = 0, MDJ_LEFT = 1, MDJ_RIGHT = 2, MDJ_OUTER = 3 } mdj_how;
+
 /* One window of output rows: device buffers owned by the caller, each with
  * room for the window's rows.  A NULL pointer skips that column.
  *   key, left_row, right_row, left_cols, right_cols : as in mdj_result (the
@@ -292,7 +304,7 @@ typedef struct {
 } mdj_window;
 
 MDJ_API int mdj_stream_open(const mdj_table *left, int32_t left_key, const mdj_table *right, int32_t right_key,
-                            uint32_t P, const mdj_allocator *alloc, void *stream, mdj_stream **out,
+                            uint32_t P, int32_t how, const mdj_allocator *alloc, void *stream, mdj_stream **out,
                             uint64_t *total_rows);
 
 /* Writes rows [first_row, first_row + nrows) of the handle's order into
@@ -314,6 +326,25 @@ MDJ_API uint64_t mdj_stream_rows(const mdj_stream *s);
 
 /* Releases every device buffer of the handle (stream order) and the handle. */
 MDJ_API void mdj_stream_close(mdj_stream *s);
+
+/*
+ * mdj_transpose_add - the paper's second application benchmark, the sum of an
+ * array and its transpose (Sec. V-B "Sum of cuPy Array and its Transpose",
+ * Fig. 7: 16K x 16K; Sec. V-C, Fig. 9(a): 20E3 x 20E3).  y = x + x^T for an
+ * n x n row-major matrix: y[i][j] = x[i][j] + x[j][i].  In the paper the
+ * array is split into chunks held by different Dask workers, so each output
+ * chunk needs the mirrored chunk from another worker; on one GPU that is a
+ * read of the mirrored tile.
+ *   x, y  : device pointers to n * n elements of `dtype`, aligned to the
+ *           element size; y may equal x (in place) but may not otherwise
+ *           overlap it (MDJ_ERR_INVALID_ARG)
+ *   dtype : MDJ_F64 / MDJ_F32 (one IEEE addition per element, so y is exact
+ *           and symmetric), MDJ_I64 / MDJ_U64 / MDJ_I32 / MDJ_U32 (addition
+ *           modulo 2^64 / 2^32)
+ * n = 0 is a no-op; n >= 2^32 gives MDJ_ERR_TOO_LARGE.  Asynchronous on
+ * `stream`; allocates nothing.
+ */
+MDJ_API int mdj_transpose_add(const void *x, void *y, uint64_t n, int32_t dtype, void *stream);
 
 /* Releases every array of *res with `alloc` (stream order) and zeroes *res. */
 MDJ_API void mdj_result_release(mdj_result *res, const mdj_allocator *alloc, void *stream);

@@ -9,7 +9,10 @@ The arithmetic lives in ``oracle.c`` (plain C, compiled with gcc into
 independent nested-loop join (``brute_force``) used to pin the C sort-merge on
 tiny inputs.  What each function computes is the plain definition of the
 operation named in Sec. V-B ("cuDF Merge", Fig. 8 and Fig. 9(b,c)) of the
-paper: a hash-partitioned shuffle followed by an inner equi-join.
+paper: a hash-partitioned shuffle followed by an inner equi-join.  The
+paper's other application benchmark, the sum of an array and its transpose
+(Sec. V-B, Fig. 7; Sec. V-C, Fig. 9(a)), is ``transpose_add``: its plain
+numpy definition.
 """
 from __future__ import annotations
 
@@ -166,6 +169,39 @@ def merge_table(left_cols, right_cols, key_col_l: int = 0, key_col_r: int = 0):
     }
 
 
+NO_ROW = 0xFFFFFFFF  # row id of the missing side of an outer-join row
+
+
+def merge_table_how(left_cols, right_cols, how: str, key_col_l: int = 0, key_col_r: int = 0):
+    """The merge variants, canonical order (key, left_row, right_row; NO_ROW last).
+
+    "inner" is merge_table.  "left" adds every left row whose key no right row
+    has, once, with no right row; "right" adds every right row whose key no
+    left row has, once, with no left row; "outer" adds both.  A missing side
+    has row id NO_ROW and all-zero bits in its columns; the key is the present
+    side's.
+    """
+    if how not in ("inner", "left", "right", "outer"):
+        raise ValueError(f"unknown join type {how!r}")
+    inner = merge_table(left_cols, right_cols, key_col_l, key_col_r)
+    lk = np.asarray(left_cols[key_col_l])
+    rk = np.asarray(right_cols[key_col_r])
+    lcols = [np.asarray(c) for j, c in enumerate(left_cols) if j != key_col_l]
+    rcols = [np.asarray(c) for j, c in enumerate(right_cols) if j != key_col_r]
+    ul = np.nonzero(~np.isin(lk, rk))[0] if how in ("left", "outer") else np.empty(0, np.int64)
+    ur = np.nonzero(~np.isin(rk, lk))[0] if how in ("right", "outer") else np.empty(0, np.int64)
+    none_l = np.full(ul.size, NO_ROW, np.uint32)
+    none_r = np.full(ur.size, NO_ROW, np.uint32)
+    key = np.concatenate([inner["key"], lk[ul], rk[ur]])
+    lrow = np.concatenate([inner["left_row"], ul.astype(np.uint32), none_r])
+    rrow = np.concatenate([inner["right_row"], none_l, ur.astype(np.uint32)])
+    left_out = [np.concatenate([a, c[ul], np.zeros(ur.size, c.dtype)]) for a, c in zip(inner["left_cols"], lcols)]
+    right_out = [np.concatenate([a, np.zeros(ul.size, c.dtype), c[ur]]) for a, c in zip(inner["right_cols"], rcols)]
+    order = np.lexsort((rrow, lrow, key))
+    return {"key": key[order], "left_row": lrow[order], "right_row": rrow[order],
+            "left_cols": [c[order] for c in left_out], "right_cols": [c[order] for c in right_out]}
+
+
 def brute_force(lkeys, rkeys):
     """Nested-loop inner join (independent of the C code) for tiny inputs.
 
@@ -222,3 +258,15 @@ def count_checksum_dense(lkeys, lpay, rkeys, rpay, key_range: int):
     if rc != 0:
         raise ValueError("oracle_count_checksum_dense failed (key outside [0, key_range)?)")
     return cnt.value, chk.value
+
+
+# ------------------------------------------------------- transpose-sum
+
+def transpose_add(x):
+    """y = x + x.T (Sec. V-B "Sum of cuPy Array and its Transpose"): one
+    addition per element in the array's own dtype (IEEE for floats, modulo
+    2^bits for integers, as numpy adds arrays)."""
+    x = np.asarray(x)
+    if x.ndim != 2 or x.shape[0] != x.shape[1]:
+        raise ValueError("x must be a square matrix")
+    return x + x.T

@@ -56,6 +56,7 @@ struct EmitSrc {
   int32_t rwidth[MDJ_MAX_COLS];
   int32_t nrc;
   const uint32_t *grid;  // grouped build rows' input row ids
+  const void *gkey;      // grouped build keys (joins that keep unmatched left rows), else NULL
   const void *gcols[MDJ_MAX_COLS];
   int32_t lwidth[MDJ_MAX_COLS];
   int32_t nlc;
@@ -112,11 +113,17 @@ struct HeavyUnit {
   uint32_t h, i0, n;  // build units: local rows [i0, i0 + n); probe units: probe rows [i0, i0 + n)
 };
 
+constexpr uint32_t kNone = 0xFFFFFFFFu;  // no row on this side (outer joins)
+
 struct GOut {
   uint32_t *grid;                  // grouped build side: input row ids
   void *gcols[MDJ_MAX_COLS];       // grouped build side: non-key columns
   uint32_t *cnt;                   // per probe row: group size (0 = no match)
   uint32_t *gbase;                 // per probe row: first grouped position of its group
+  // joins that keep unmatched left rows (else NULL):
+  void *gkey;                      // grouped build side: keys
+  uint32_t *gsize;                 // group size at each group's first grouped position, 0 elsewhere
+  uint32_t *hit;                   // 1 at the first grouped position of every group a probe row found
 };
 
 // In-table position and tag of a key: multiplicative hash of the key bits
@@ -207,27 +214,32 @@ __device__ __forceinline__ void probe_small(const KeyT *keys, const uint32_t *sl
       const bool found = rep != 0xFFFFFFFFu;
       o.cnt[r0 + i] = found ? base[rep + 1] - base[rep] : 0u;
       o.gbase[r0 + i] = found ? lb + base[rep] : 0u;
+      if (found && o.hit) o.hit[lb + base[rep]] = 1;
     }
   }
 }
 
 // One column of the build rows lb + threadIdx.x + k * kGT (k < kGRows, below
 // lb + nl) to grouped order: values to their local positions pos[k] in the
-// shared staging area (all loads first), then out to dst[lb ..) with
-// coalesced stores.  src NULL: the identity (row index).  Ends with a barrier.
+// shared staging area (four loads in flight at a time), then out to
+// dst[lb ..) with coalesced stores.  src NULL: the identity (row index).
+// Ends with a barrier.
 template <typename V>
 __device__ __forceinline__ void stage_column(V *__restrict__ dst, const V *__restrict__ src, uint32_t lb, uint32_t nl,
                                              const uint32_t (&pos)[kGRows], unsigned char *stage_bytes) {
   V *stage = (V *)stage_bytes;
-  V v[kGRows];
 #pragma unroll
-  for (int k = 0; k < kGRows; k++) {
-    const uint32_t i = threadIdx.x + k * kGT;
-    if (i < nl) v[k] = src ? src[lb + i] : (V)(lb + i);
+  for (int h = 0; h < kGRows; h += 4) {  // four loads in flight per thread
+    V v[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const uint32_t i = threadIdx.x + (h + k) * kGT;
+      if (i < nl) v[k] = src ? src[lb + i] : (V)(lb + i);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+      if (threadIdx.x + (h + k) * kGT < nl) stage[pos[h + k]] = v[k];
   }
-#pragma unroll
-  for (int k = 0; k < kGRows; k++)
-    if (threadIdx.x + k * kGT < nl) stage[pos[k]] = v[k];
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < nl; i += kGT) dst[lb + i] = stage[i];
   __syncthreads();
@@ -245,8 +257,9 @@ __device__ __forceinline__ void stage_column(V *__restrict__ dst, const V *__res
 // zero counts.
 template <typename KeyT>
 __global__ void __launch_bounds__(kGT, 2)
-    k_group_light(GSide L, GSide R, const LightUnit *__restrict__ units, uint32_t nunits, uint32_t *ticket, GOut o,
-                  unsigned char *__restrict__ dumps) {
+    k_group_light(const __grid_constant__ GSide L, const __grid_constant__ GSide R,
+                  const LightUnit *__restrict__ units, uint32_t nunits, uint32_t *ticket,
+                  const __grid_constant__ GOut o, unsigned char *__restrict__ dumps) {
   extern __shared__ __align__(16) unsigned char smem[];
   KeyT *keys = (KeyT *)smem;
   uint32_t *slots = (uint32_t *)(smem + group_slots_at<KeyT>());
@@ -286,12 +299,13 @@ __global__ void __launch_bounds__(kGT, 2)
       if (i < nl) keys[i] = kr[k];
     }
     __syncthreads();
-    uint32_t sk[kGRows], rk[kGRows];
+    // per build row: representative << 16 | rank in its group (both < kGCap),
+    // later its grouped position
+    uint32_t pr[kGRows];
 #pragma unroll
     for (int k = 0; k < kGRows; k++) {
       const uint32_t i = threadIdx.x + k * kGT;
-      sk[k] = 0;
-      rk[k] = 0;
+      pr[k] = 0;
       if (i < nl) {
         const KeyT kk = keys[i];
         uint32_t s, tag;
@@ -311,8 +325,7 @@ __global__ void __launch_bounds__(kGT, 2)
           }
           s = (s + 1) & mask;
         }
-        sk[k] = rep;
-        rk[k] = atomicAdd(&base[rep], 1u);
+        pr[k] = (rep << 16) | atomicAdd(&base[rep], 1u);
       }
     }
     __syncthreads();
@@ -331,15 +344,25 @@ __global__ void __launch_bounds__(kGT, 2)
     // sub-bucket; keys and slots are dead after the probe, so their space
     // stages one column at a time and the column leaves with coalesced stores
 #pragma unroll
-    for (int k = 0; k < kGRows; k++) sk[k] = base[sk[k]] + rk[k];
+    for (int k = 0; k < kGRows; k++) {
+      const uint32_t rep = pr[k] >> 16, rank = pr[k] & 0xFFFFu;
+      if (o.gsize && rank == 0 && threadIdx.x + k * kGT < nl) o.gsize[lb + base[rep]] = base[rep + 1] - base[rep];
+      pr[k] = base[rep] + rank;
+    }
     __syncthreads();
-    stage_column<uint32_t>(o.grid, L.rid, lb, nl, sk, smem);
+    stage_column<uint32_t>(o.grid, L.rid, lb, nl, pr, smem);
+    if (o.gkey) {
+      if (sizeof(KeyT) == 8)
+        stage_column<uint64_t>((uint64_t *)o.gkey, (const uint64_t *)L.key, lb, nl, pr, smem);
+      else
+        stage_column<uint32_t>((uint32_t *)o.gkey, (const uint32_t *)L.key, lb, nl, pr, smem);
+    }
 #pragma unroll 1
     for (int c = 0; c < L.ncols; c++) {
       if (L.width[c] == 8)
-        stage_column<uint64_t>((uint64_t *)o.gcols[c], (const uint64_t *)L.cols[c], lb, nl, sk, smem);
+        stage_column<uint64_t>((uint64_t *)o.gcols[c], (const uint64_t *)L.cols[c], lb, nl, pr, smem);
       else
-        stage_column<uint32_t>((uint32_t *)o.gcols[c], (const uint32_t *)L.cols[c], lb, nl, sk, smem);
+        stage_column<uint32_t>((uint32_t *)o.gcols[c], (const uint32_t *)L.cols[c], lb, nl, pr, smem);
     }
   }
 }
@@ -347,7 +370,8 @@ __global__ void __launch_bounds__(kGT, 2)
 // Later probe chunks of light sub-buckets: reload the saved table, probe.
 template <typename KeyT>
 __global__ void __launch_bounds__(kGT, 2)
-    k_group_chunks(GSide L, GSide R, const LightUnit *__restrict__ units, uint32_t nunits, GOut o,
+    k_group_chunks(const __grid_constant__ GSide L, const __grid_constant__ GSide R,
+                   const LightUnit *__restrict__ units, uint32_t nunits, const __grid_constant__ GOut o,
                    const unsigned char *__restrict__ dumps) {
   extern __shared__ __align__(16) unsigned char smem[];
   KeyT *keys = (KeyT *)smem;
@@ -424,17 +448,21 @@ __global__ void __launch_bounds__(kHT)
 
 // hbase = exclusive scan of hcnt over all regions, so a region starts at hr0.
 __global__ void __launch_bounds__(kHT)
-    k_heavy_scatter(const HeavyDesc *__restrict__ hd, const HeavyUnit *__restrict__ units, uint32_t nunits, GSide L,
-                    const uint32_t *__restrict__ hbase, const uint32_t *__restrict__ hs,
-                    const uint32_t *__restrict__ hrank, GOut o) {
+    k_heavy_scatter(const HeavyDesc *__restrict__ hd, const HeavyUnit *__restrict__ units, uint32_t nunits,
+                    const __grid_constant__ GSide L, int key_width, const uint32_t *__restrict__ hbase,
+                    const uint32_t *__restrict__ hs, const uint32_t *__restrict__ hrank,
+                    const __grid_constant__ GOut o) {
   for (uint32_t u = blockIdx.x; u < nunits; u += gridDim.x) {
     const HeavyUnit U = units[u];
     const HeavyDesc H = hd[U.h];
     for (uint32_t i = U.i0 + threadIdx.x; i < U.i0 + U.n; i += kHT) {
-      const uint32_t pos = H.lb + (hbase[H.ts0 + hs[H.hr0 + i]] - H.hr0) + hrank[H.hr0 + i];
+      const uint32_t s = H.ts0 + hs[H.hr0 + i], rank = hrank[H.hr0 + i];
+      const uint32_t pos = H.lb + (hbase[s] - H.hr0) + rank;
       const uint32_t src = H.lb + i;
       o.grid[pos] = L.rid ? L.rid[src] : src;
       for (int c = 0; c < L.ncols; c++) copy_col(o.gcols[c], pos, L.cols[c], src, L.width[c]);
+      if (o.gsize && rank == 0) o.gsize[pos] = hbase[s + 1] - hbase[s];
+      if (o.gkey) copy_col(o.gkey, pos, L.key, src, key_width);
     }
   }
 }
@@ -465,32 +493,61 @@ __global__ void __launch_bounds__(kHT)
       const uint32_t c = found ? hbase[H.ts0 + s + 1] - hbase[H.ts0 + s] : 0u;
       o.cnt[r] = c;
       o.gbase[r] = found ? H.lb + (hbase[H.ts0 + s] - H.hr0) : 0u;
+      if (found && o.hit) o.hit[H.lb + (hbase[H.ts0 + s] - H.hr0)] = 1;
     }
   }
 }
 
 // ------------------------------------------------------------- entries
 //
-// Matching probe rows, in shuffled order, become entries (first output row,
-// probe row, group start); moff[nm] = total rows.  Reduce, scan, rescan:
-// k_entry_sums sums each chunk of kCChunk probe rows (rows and entries),
-// the chunk sums are scanned, and k_entry_write rescans its chunk from the
-// counts and writes the chunk's entries at its base.  Within a block both
-// sums travel in one 64-bit scan, packed rows << 13 | entries (a chunk has at
-// most 4096 entries and fewer than 2^44 rows).
+// Entries (first output row, probe row, group start) in output order:
+//   pass 1, over probe rows in shuffled order: every matching row (inner,
+//     left), or every row, an unmatched one as a one-row entry with no group
+//     (right, outer);
+//   pass 2 (left, outer), over grouped build positions: every group no probe
+//     row found, as an entry with no probe row and the group's size.
+// Reduce, scan, rescan: k_entry_sums sums each chunk of kCChunk rows (rows
+// and entries), the chunk sums are scanned, and k_entry_write rescans its
+// chunk and writes the chunk's entries at its base (after pass 1's totals in
+// pass 2).  Within a block both sums travel in one 64-bit scan, packed
+// rows << 13 | entries (a chunk has at most 4096 entries and fewer than 2^44
+// rows).
 constexpr int kCT = 512;
 constexpr int kCRows = 8;
 constexpr uint32_t kCChunk = kCT * kCRows;
 static_assert(kCChunk <= 8191, "entries of a chunk fit the packed low 13 bits");
 
-__device__ __forceinline__ void load_counts(const uint32_t *__restrict__ cnt, uint32_t nR, uint32_t r0,
-                                            uint32_t (&v)[kCRows]) {
-  if (r0 + kCRows <= nR) {
-    const uint4 a = *(const uint4 *)(cnt + r0), b = *(const uint4 *)(cnt + r0 + 4);
-    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+enum { SRC_PROBE = 0, SRC_PROBE_ALL = 1, SRC_UNMATCHED_GROUPS = 2 };
+struct EntrySrc {
+  const uint32_t *cnt;  // probe passes: group size per probe row; group pass: size at group starts
+  const uint32_t *aux;  // probe passes: group start per probe row; group pass: hit flags
+  uint32_t n;
+  int mode;
+};
+
+__device__ __forceinline__ void load8(const uint32_t *__restrict__ a, uint32_t n, uint32_t r0, uint32_t (&v)[kCRows]) {
+  if (r0 + kCRows <= n) {
+    const uint4 x = *(const uint4 *)(a + r0), y = *(const uint4 *)(a + r0 + 4);
+    v[0] = x.x, v[1] = x.y, v[2] = x.z, v[3] = x.w, v[4] = y.x, v[5] = y.y, v[6] = y.z, v[7] = y.w;
   } else {
 #pragma unroll
-    for (int k = 0; k < kCRows; k++) v[k] = r0 + k < nR ? cnt[r0 + k] : 0u;
+    for (int k = 0; k < kCRows; k++) v[k] = r0 + k < n ? a[r0 + k] : 0u;
+  }
+}
+
+// Output rows of rows r0 .. r0 + 7 of the pass (0 = no entry).
+__device__ __forceinline__ void entry_rows(const EntrySrc &S, uint32_t r0, uint32_t (&v)[kCRows]) {
+  load8(S.cnt, S.n, r0, v);
+  if (S.mode == SRC_PROBE_ALL) {
+#pragma unroll
+    for (int k = 0; k < kCRows; k++)
+      if (r0 + k < S.n && v[k] == 0) v[k] = 1;
+  } else if (S.mode == SRC_UNMATCHED_GROUPS) {
+    uint32_t h[kCRows];
+    load8(S.aux, S.n, r0, h);
+#pragma unroll
+    for (int k = 0; k < kCRows; k++)
+      if (h[k]) v[k] = 0;
   }
 }
 
@@ -507,12 +564,11 @@ __device__ __forceinline__ uint64_t packed_sum(const uint32_t (&v)[kCRows]) {
 
 // chunk c: rows[c], ents[c] (nchunks + 1 entries each; the last stays 0)
 __global__ void __launch_bounds__(kCT)
-    k_entry_sums(const uint32_t *__restrict__ cnt, uint32_t nR, uint64_t *__restrict__ rows,
-                 uint32_t *__restrict__ ents) {
+    k_entry_sums(EntrySrc S, uint64_t *__restrict__ rows, uint32_t *__restrict__ ents) {
   __shared__ uint64_t scratch[33];
   const uint32_t r0 = blockIdx.x * kCChunk + threadIdx.x * kCRows;
   uint32_t v[kCRows];
-  load_counts(cnt, nR, r0, v);
+  entry_rows(S, r0, v);
   uint64_t tot;
   block_exclusive_scan<uint64_t>(packed_sum(v), scratch, &tot);
   if (threadIdx.x == 0) {
@@ -521,26 +577,30 @@ __global__ void __launch_bounds__(kCT)
   }
 }
 
-// rows / ents: exclusive prefixes over chunks (index nchunks = totals).  The
-// chunk's entries are staged in shared memory one array at a time and leave
-// with coalesced stores.
+// rows / ents: exclusive prefixes over chunks; rows0 / ents0: where the pass
+// starts (pass 1's totals, or NULL for 0).  The chunk's entries are staged in
+// shared memory one array at a time and leave with coalesced stores.
 __global__ void __launch_bounds__(kCT)
-    k_entry_write(const uint32_t *__restrict__ cnt, const uint32_t *__restrict__ gbase, uint32_t nR, uint32_t nchunks,
-                  const uint64_t *__restrict__ rows, const uint32_t *__restrict__ ents, uint64_t *__restrict__ moff,
+    k_entry_write(EntrySrc S, const uint64_t *__restrict__ rows, const uint32_t *__restrict__ ents,
+                  const uint64_t *__restrict__ rows0, const uint32_t *__restrict__ ents0, uint64_t *__restrict__ moff,
                   uint32_t *__restrict__ mr, uint32_t *__restrict__ mg) {
   __shared__ uint64_t scratch[33];
   __shared__ uint64_t stage[kCChunk];
   uint32_t *stage32 = (uint32_t *)stage;
   const uint32_t r0 = blockIdx.x * kCChunk + threadIdx.x * kCRows;
   uint32_t v[kCRows];
-  load_counts(cnt, nR, r0, v);
-  uint32_t g[kCRows];
+  entry_rows(S, r0, v);
+  uint32_t g[kCRows], r[kCRows];
+  const bool probe = S.mode != SRC_UNMATCHED_GROUPS;
 #pragma unroll
-  for (int k = 0; k < kCRows; k++) g[k] = v[k] ? gbase[r0 + k] : 0u;
+  for (int k = 0; k < kCRows; k++) {
+    r[k] = probe ? r0 + k : kNone;
+    g[k] = probe ? (v[k] && r0 + k < S.n && S.cnt[r0 + k] ? S.aux[r0 + k] : kNone) : r0 + k;
+  }
   uint64_t tot;
   const uint64_t ex = block_exclusive_scan<uint64_t>(packed_sum(v), scratch, &tot);
-  const uint64_t rbase = rows[blockIdx.x];
-  const uint32_t ebase = ents[blockIdx.x], n = (uint32_t)(tot & 8191);
+  const uint64_t rbase = rows[blockIdx.x] + (rows0 ? *rows0 : 0ull);
+  const uint32_t ebase = ents[blockIdx.x] + (ents0 ? *ents0 : 0u), n = (uint32_t)(tot & 8191);
   const uint32_t e0 = (uint32_t)(ex & 8191);
   {
     uint64_t at = rbase + (ex >> 13);
@@ -559,7 +619,7 @@ __global__ void __launch_bounds__(kCT)
     uint32_t e = e0;
 #pragma unroll
     for (int k = 0; k < kCRows; k++)
-      if (v[k]) stage32[e++] = r0 + k;
+      if (v[k]) stage32[e++] = r[k];
   }
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < n; i += kCT) mr[ebase + i] = stage32[i];
@@ -572,7 +632,6 @@ __global__ void __launch_bounds__(kCT)
   }
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < n; i += kCT) mg[ebase + i] = stage32[i];
-  if (blockIdx.x == 0 && threadIdx.x == 0) moff[ents[nchunks]] = rows[nchunks];
 }
 
 // ------------------------------------------------------------------ emit
@@ -586,16 +645,17 @@ __global__ void __launch_bounds__(kCT)
 // resolves its kERows rows first, then moves one column at a time, kEBatch
 // rows at once: kEBatch independent loads, then kEBatch stores.  Output rows
 // of a warp are consecutive, so every store is coalesced.
+// idx kNone (no row on that side of an outer join) writes `fill`.
 template <typename V>
 __device__ __forceinline__ void gather_rows(V *dst, const V *src, const uint32_t (&idx)[kERows], uint64_t q0,
-                                            uint32_t nrow) {
+                                            uint32_t nrow, V fill) {
   V *d = dst + q0;
 #pragma unroll
   for (int h = 0; h < kERows; h += kEBatch) {
     V v[kEBatch];
 #pragma unroll
     for (int k = 0; k < kEBatch; k++)
-      if ((uint32_t)(h + k) < nrow) v[k] = src[idx[h + k]];
+      if ((uint32_t)(h + k) < nrow) v[k] = idx[h + k] != kNone ? src[idx[h + k]] : fill;
 #pragma unroll
     for (int k = 0; k < kEBatch; k++)
       if ((uint32_t)(h + k) < nrow) d[(h + k) * kET] = v[k];
@@ -605,9 +665,27 @@ __device__ __forceinline__ void gather_rows(V *dst, const V *src, const uint32_t
 __device__ __forceinline__ void gather_col(void *dst, const void *src, int width, const uint32_t (&idx)[kERows],
                                            uint64_t q0, uint32_t nrow) {
   if (width == 8)
-    gather_rows<uint64_t>((uint64_t *)dst, (const uint64_t *)src, idx, q0, nrow);
+    gather_rows<uint64_t>((uint64_t *)dst, (const uint64_t *)src, idx, q0, nrow, 0ull);
   else
-    gather_rows<uint32_t>((uint32_t *)dst, (const uint32_t *)src, idx, q0, nrow);
+    gather_rows<uint32_t>((uint32_t *)dst, (const uint32_t *)src, idx, q0, nrow, 0u);
+}
+
+// The key of each row: the probe row's, or the grouped build row's when the
+// row has no probe side.
+template <typename KeyT>
+__device__ __forceinline__ void gather_keys(KeyT *dst, const KeyT *rk, const KeyT *gk, const uint32_t (&ri)[kERows],
+                                            const uint32_t (&li)[kERows], uint64_t q0, uint32_t nrow) {
+  KeyT *d = dst + q0;
+#pragma unroll
+  for (int h = 0; h < kERows; h += kEBatch) {
+    KeyT v[kEBatch];
+#pragma unroll
+    for (int k = 0; k < kEBatch; k++)
+      if ((uint32_t)(h + k) < nrow) v[k] = ri[h + k] != kNone ? rk[ri[h + k]] : gk[li[h + k]];
+#pragma unroll
+    for (int k = 0; k < kEBatch; k++)
+      if ((uint32_t)(h + k) < nrow) d[(h + k) * kET] = v[k];
+  }
 }
 
 template <typename KeyT>
@@ -657,12 +735,12 @@ __global__ void __launch_bounds__(kET, 3)
     const uint32_t nrow = mine < o1 ? (uint32_t)((o1 - mine + kET - 1) / kET) : 0u;
     uint32_t ri[kERows], li[kERows];
     if (s_off[1] >= o1) {  // one entry: one probe row against a run of its group
-      const uint32_t r = s_r[0];
-      const uint32_t g = s_g[0] + (uint32_t)(mine - s_off[0]);
+      const uint32_t r = s_r[0], g0 = s_g[0];
+      const uint32_t g = g0 + (uint32_t)(mine - s_off[0]);
 #pragma unroll
       for (int k = 0; k < kERows; k++) {
         ri[k] = r;
-        li[k] = g + k * kET;
+        li[k] = g0 == kNone ? kNone : g + k * kET;
       }
     } else {
       uint32_t j = 0;
@@ -681,16 +759,16 @@ __global__ void __launch_bounds__(kET, 3)
               hi = mid;
           }
           ri[k] = s_r[j];
-          li[k] = s_g[j] + (uint32_t)(o - s_off[j]);
+          li[k] = s_g[j] == kNone ? kNone : s_g[j] + (uint32_t)(o - s_off[j]);
         }
       }
     }
     const uint64_t q0 = mine - first;
-    if (D.key) gather_rows<KeyT>((KeyT *)D.key, (const KeyT *)S.rkey, ri, q0, nrow);
-    if (D.lrow) gather_rows<uint32_t>(D.lrow, S.grid, li, q0, nrow);
+    if (D.key) gather_keys<KeyT>((KeyT *)D.key, (const KeyT *)S.rkey, (const KeyT *)S.gkey, ri, li, q0, nrow);
+    if (D.lrow) gather_rows<uint32_t>(D.lrow, S.grid, li, q0, nrow, kNone);
     if (D.rrow) {
       if (S.rrid) {
-        gather_rows<uint32_t>(D.rrow, S.rrid, ri, q0, nrow);
+        gather_rows<uint32_t>(D.rrow, S.rrid, ri, q0, nrow, kNone);
       } else {
         uint32_t *d = D.rrow + q0;
 #pragma unroll
@@ -758,16 +836,19 @@ struct Units {
   uint64_t hslots = 0, hrows = 0;
 };
 
-void plan_units(const std::vector<uint32_t> &offL, const std::vector<uint32_t> &offR, uint32_t nb, Units *u) {
+// keep_left: every build row is grouped (its unmatched groups become rows),
+// even in sub-buckets without probe rows.
+void plan_units(const std::vector<uint32_t> &offL, const std::vector<uint32_t> &offR, uint32_t nb, bool keep_left,
+                Units *u) {
   for (uint32_t b = 0; b < nb; b++) {
     const uint32_t nl = offL[b + 1] - offL[b], nr = offR[b + 1] - offR[b];
-    if (nr == 0) continue;  // no probe row: nothing of this sub-bucket is ever read
+    if (nr == 0 && !(keep_left && nl > 0)) continue;  // nothing of this sub-bucket is ever read
     if (nl == 0) {
       for (uint32_t c0 = 0; c0 < nr; c0 += kProbeChunk)
         u->first.push_back({b, offR[b] + c0, std::min(kProbeChunk, nr - c0), -1});
       continue;
     }
-    if (nl <= kGCap) {
+    if (nl <= kGCap) {  // nr may be 0 (keep_left): the unit groups and probes nothing
       const int32_t dump = nr > kProbeChunk ? (int32_t)u->ndump++ : -1;
       u->first.push_back({b, offR[b], std::min(kProbeChunk, nr), dump});
       for (uint32_t c0 = kProbeChunk; c0 < nr; c0 += kProbeChunk)
@@ -804,9 +885,41 @@ unsigned grid_for(uint64_t units, int per_sm) {
   return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(units, most));
 }
 
+// One pass of the entries: sums per chunk, scan, rescan and write.  rows0 /
+// ents0: where the pass starts (NULL: 0).  Leaves the pass's totals at
+// crows[nchunks], cents[nchunks].
+int entries_pass(Workspace &tmp, const EntrySrc &src, const uint64_t *rows0, const uint32_t *ents0, uint64_t *moff,
+                 uint32_t *mr, uint32_t *mg, uint64_t **crows_out, uint32_t **cents_out, uint32_t *nchunks_out) {
+  cudaStream_t s = tmp.stream();
+  const uint32_t nchunks = (uint32_t)(((size_t)src.n + kCChunk - 1) / kCChunk);
+  uint64_t *crows = (uint64_t *)tmp.get((size_t)(nchunks + 1) * 8);
+  uint32_t *cents = (uint32_t *)tmp.get((size_t)(nchunks + 1) * 4);
+  if (!crows || !cents) return MDJ_ERR_OOM;
+  MDJ_CUDA_TRY(cudaMemsetAsync(crows + nchunks, 0, 8, s));
+  MDJ_CUDA_TRY(cudaMemsetAsync(cents + nchunks, 0, 4, s));
+  if (nchunks) {
+    TraceScope tr("stream_entry_sums", s);
+    k_entry_sums<<<nchunks, kCT, 0, s>>>(src, crows, cents);
+  }
+  MDJ_LAUNCH_CHECK();
+  MDJ_TRY(exclusive_scan_u64(tmp, crows, crows, (size_t)nchunks + 1));
+  MDJ_TRY(exclusive_scan_u32(tmp, cents, cents, (size_t)nchunks + 1));
+  if (nchunks) {
+    TraceScope tr("stream_entries", s);
+    k_entry_write<<<nchunks, kCT, 0, s>>>(src, crows, cents, rows0, ents0, moff, mr, mg);
+  }
+  MDJ_LAUNCH_CHECK();
+  *crows_out = crows;
+  *cents_out = cents;
+  *nchunks_out = nchunks;
+  return MDJ_OK;
+}
+
 // Groups the build side, probes, and builds the entries into the handle.
 template <typename KeyT>
-int group_and_index(Workspace &tmp, mdj_stream *h, const Side &L, const Side &R, uint32_t nb) {
+int group_and_index(Workspace &tmp, mdj_stream *h, const Side &L, const Side &R, uint32_t nb, int32_t how) {
+  const bool keep_left = how == MDJ_LEFT || how == MDJ_OUTER;
+  const bool keep_right = how == MDJ_RIGHT || how == MDJ_OUTER;
   Workspace &keep = *h->ws;
   cudaStream_t s = tmp.stream();
   const uint32_t nL = (uint32_t)L.nrows, nR = (uint32_t)R.nrows;
@@ -815,7 +928,7 @@ int group_and_index(Workspace &tmp, mdj_stream *h, const Side &L, const Side &R,
   MDJ_CUDA_TRY(cudaMemcpyAsync(offR.data(), R.off, (size_t)(nb + 1) * 4, cudaMemcpyDeviceToHost, s));
   MDJ_CUDA_TRY(cudaStreamSynchronize(s));
   Units un;
-  plan_units(offL, offR, nb, &un);
+  plan_units(offL, offR, nb, keep_left, &un);
   if (un.hslots >= (1ull << 32) - 1) return MDJ_ERR_TOO_LARGE;
 
   // the grouped build side lives as long as the handle
@@ -830,6 +943,14 @@ int group_and_index(Workspace &tmp, mdj_stream *h, const Side &L, const Side &R,
   int *err = (int *)tmp.get(16);  // [0]: a global-table probe sequence ran out
   if (!o.cnt || !o.gbase || !err) return MDJ_ERR_OOM;
   MDJ_CUDA_TRY(cudaMemsetAsync(err, 0, 16, s));
+  if (keep_left) {
+    o.gkey = keep.get((size_t)nL * sizeof(KeyT));
+    o.gsize = (uint32_t *)tmp.get((size_t)nL * 4);
+    o.hit = (uint32_t *)tmp.get((size_t)nL * 4);
+    if (!o.gkey || !o.gsize || !o.hit) return MDJ_ERR_OOM;
+    MDJ_CUDA_TRY(cudaMemsetAsync(o.gsize, 0, (size_t)nL * 4, s));
+    MDJ_CUDA_TRY(cudaMemsetAsync(o.hit, 0, (size_t)nL * 4, s));
+  }
 
   int rc = MDJ_OK;
   LightUnit *d_first = upload(tmp, un.first, &rc);
@@ -882,43 +1003,39 @@ int group_and_index(Workspace &tmp, mdj_stream *h, const Side &L, const Side &R,
     {
       TraceScope tr("stream_heavy_scatter", s);
       k_heavy_scatter<<<grid_for(un.hbuild.size(), 8), kHT, 0, s>>>(d_heavy, d_hbuild, (uint32_t)un.hbuild.size(),
-                                                                      gL, hcnt, hs, hrank, o);
+                                                                      gL, (int)sizeof(KeyT), hcnt, hs, hrank, o);
     }
-    {
+    if (!un.hprobe.empty()) {
       TraceScope tr("stream_heavy_probe", s);
       k_heavy_probe<KeyT><<<grid_for(un.hprobe.size(), 8), kHT, 0, s>>>(
           d_heavy, d_hprobe, (uint32_t)un.hprobe.size(), Lk, (const KeyT *)R.key, hslot, hcnt, o, err);
     }
     MDJ_LAUNCH_CHECK();
   }
-  // entries of the matching probe rows, with their first output rows
+  // entries: the probe rows (matching ones, or all), then the unmatched groups
   EmitSrc &S = h->src;
-  uint64_t *moff = (uint64_t *)keep.get((size_t)(nR + 1) * 8);
-  uint32_t *mr = (uint32_t *)keep.get((size_t)nR * 4);
-  uint32_t *mg = (uint32_t *)keep.get((size_t)nR * 4);
-  const uint32_t nchunks = (uint32_t)(((size_t)nR + kCChunk - 1) / kCChunk);
-  uint64_t *crows = (uint64_t *)tmp.get((size_t)(nchunks + 1) * 8);
-  uint32_t *cents = (uint32_t *)tmp.get((size_t)(nchunks + 1) * 4);
-  if (!moff || !mr || !mg || !crows || !cents) return MDJ_ERR_OOM;
-  MDJ_CUDA_TRY(cudaMemsetAsync(crows + nchunks, 0, 8, s));
-  MDJ_CUDA_TRY(cudaMemsetAsync(cents + nchunks, 0, 4, s));
-  {
-    TraceScope tr("stream_entry_sums", s);
-    k_entry_sums<<<nchunks, kCT, 0, s>>>(o.cnt, nR, crows, cents);
+  const size_t cap = (size_t)nR + (keep_left ? nL : 0);
+  uint64_t *moff = (uint64_t *)keep.get((cap + 1) * 8);
+  uint32_t *mr = (uint32_t *)keep.get(cap * 4);
+  uint32_t *mg = (uint32_t *)keep.get(cap * 4);
+  if (!moff || !mr || !mg) return MDJ_ERR_OOM;
+  const EntrySrc probe_src = {o.cnt, o.gbase, nR, keep_right ? SRC_PROBE_ALL : SRC_PROBE};
+  uint64_t *crows1, *crows2 = nullptr;
+  uint32_t *cents1, *cents2 = nullptr, c1, c2 = 0;
+  MDJ_TRY(entries_pass(tmp, probe_src, nullptr, nullptr, moff, mr, mg, &crows1, &cents1, &c1));
+  if (keep_left) {
+    const EntrySrc group_src = {o.gsize, o.hit, nL, SRC_UNMATCHED_GROUPS};
+    MDJ_TRY(entries_pass(tmp, group_src, crows1 + c1, cents1 + c1, moff, mr, mg, &crows2, &cents2, &c2));
   }
-  MDJ_LAUNCH_CHECK();
-  MDJ_TRY(exclusive_scan_u64(tmp, crows, crows, (size_t)nchunks + 1));
-  MDJ_TRY(exclusive_scan_u32(tmp, cents, cents, (size_t)nchunks + 1));
-  {
-    TraceScope tr("stream_entries", s);
-    k_entry_write<<<nchunks, kCT, 0, s>>>(o.cnt, o.gbase, nR, nchunks, crows, cents, moff, mr, mg);
-  }
-  MDJ_LAUNCH_CHECK();
-  uint64_t total = 0;
-  uint32_t nm = 0;
+  uint64_t t1 = 0, t2 = 0;
+  uint32_t n1 = 0, n2 = 0;
   int herr[4] = {0, 0, 0, 0}, pflag[2] = {0, 0};
-  MDJ_CUDA_TRY(cudaMemcpyAsync(&total, crows + nchunks, 8, cudaMemcpyDeviceToHost, s));
-  MDJ_CUDA_TRY(cudaMemcpyAsync(&nm, cents + nchunks, 4, cudaMemcpyDeviceToHost, s));
+  MDJ_CUDA_TRY(cudaMemcpyAsync(&t1, crows1 + c1, 8, cudaMemcpyDeviceToHost, s));
+  MDJ_CUDA_TRY(cudaMemcpyAsync(&n1, cents1 + c1, 4, cudaMemcpyDeviceToHost, s));
+  if (keep_left) {
+    MDJ_CUDA_TRY(cudaMemcpyAsync(&t2, crows2 + c2, 8, cudaMemcpyDeviceToHost, s));
+    MDJ_CUDA_TRY(cudaMemcpyAsync(&n2, cents2 + c2, 4, cudaMemcpyDeviceToHost, s));
+  }
   MDJ_CUDA_TRY(cudaMemcpyAsync(herr, err, 16, cudaMemcpyDeviceToHost, s));
   // a shuffle pass that gave up on a bounded copy wait (opt-in bulk-copy scatter)
   if (tmp.flag_word_if_any()) MDJ_CUDA_TRY(cudaMemcpyAsync(&pflag[0], tmp.flag_word_if_any(), 4, cudaMemcpyDeviceToHost, s));
@@ -926,6 +1043,11 @@ int group_and_index(Workspace &tmp, mdj_stream *h, const Side &L, const Side &R,
   MDJ_CUDA_TRY(cudaStreamSynchronize(s));
   if (pflag[0] || pflag[1]) return MDJ_ERR_DEVICE_TIMEOUT;
   if (herr[0]) return MDJ_ERR_INTERNAL;
+  const uint64_t total = t1 + t2;
+  const uint32_t nm = n1 + n2;
+  // the search sentinel after the last entry: moff[nm] = total rows
+  MDJ_CUDA_TRY(cudaMemcpyAsync(moff + nm, &total, 8, cudaMemcpyHostToDevice, s));
+  MDJ_CUDA_TRY(cudaStreamSynchronize(s));
   h->total = total;
   S.moff = moff;
   S.mr = mr;
@@ -939,6 +1061,7 @@ int group_and_index(Workspace &tmp, mdj_stream *h, const Side &L, const Side &R,
     S.rwidth[c] = R.widths[c];
   }
   S.grid = o.grid;
+  S.gkey = o.gkey;
   S.nlc = L.ncols;
   for (int c = 0; c < L.ncols; c++) {
     S.gcols[c] = o.gcols[c];
@@ -947,7 +1070,7 @@ int group_and_index(Workspace &tmp, mdj_stream *h, const Side &L, const Side &R,
   return MDJ_OK;
 }
 
-int stream_open(const mdj_table *left, int32_t lk, const mdj_table *right, int32_t rk, uint32_t P,
+int stream_open(const mdj_table *left, int32_t lk, const mdj_table *right, int32_t rk, uint32_t P, int32_t how,
                 const mdj_allocator *alloc, void *stream, mdj_stream **out, uint64_t *total_rows) {
   if (!out || !total_rows) return MDJ_ERR_INVALID_ARG;
   *out = nullptr;
@@ -955,6 +1078,7 @@ int stream_open(const mdj_table *left, int32_t lk, const mdj_table *right, int32
   MDJ_TRY(validate(left, lk));
   MDJ_TRY(validate(right, rk));
   if (P < 1 || P > MDJ_MAX_PARTITIONS) return MDJ_ERR_INVALID_ARG;
+  if (how < MDJ_INNER || how > MDJ_OUTER) return MDJ_ERR_INVALID_ARG;
   if (left->cols[lk].dtype != right->cols[rk].dtype) return MDJ_ERR_INVALID_ARG;
   mdj_stream *h = new (std::nothrow) mdj_stream;
   if (!h) return MDJ_ERR_OOM;
@@ -978,9 +1102,12 @@ int stream_open(const mdj_table *left, int32_t lk, const mdj_table *right, int32
     Side L, R;
     rc = partition_side(tmp, left, lk, plan, &L);        // released when open returns
     if (rc == MDJ_OK) rc = partition_side(*h->ws, right, rk, plan, &R);  // read by every window
-    if (rc == MDJ_OK && left->nrows > 0 && right->nrows > 0)
-      rc = h->key_dtype == MDJ_I64 ? group_and_index<int64_t>(tmp, h, L, R, plan.nbuckets)
-                                   : group_and_index<int32_t>(tmp, h, L, R, plan.nbuckets);
+    const bool rows_possible = (left->nrows > 0 && right->nrows > 0) ||
+                               (left->nrows > 0 && (how == MDJ_LEFT || how == MDJ_OUTER)) ||
+                               (right->nrows > 0 && (how == MDJ_RIGHT || how == MDJ_OUTER));
+    if (rc == MDJ_OK && rows_possible)
+      rc = h->key_dtype == MDJ_I64 ? group_and_index<int64_t>(tmp, h, L, R, plan.nbuckets, how)
+                                   : group_and_index<int32_t>(tmp, h, L, R, plan.nbuckets, how);
   }
   if (rc != MDJ_OK) {
     delete h->ws;
@@ -1022,8 +1149,8 @@ int stream_emit(mdj_stream *h, uint64_t first, uint64_t rows, const mdj_window *
 extern "C" {
 
 int mdj_stream_open(const mdj_table *left, int32_t left_key, const mdj_table *right, int32_t right_key, uint32_t P,
-                    const mdj_allocator *alloc, void *stream, mdj_stream **out, uint64_t *total_rows) {
-  return mdj::stream_open(left, left_key, right, right_key, P, alloc, stream, out, total_rows);
+                    int32_t how, const mdj_allocator *alloc, void *stream, mdj_stream **out, uint64_t *total_rows) {
+  return mdj::stream_open(left, left_key, right, right_key, P, how, alloc, stream, out, total_rows);
 }
 
 int mdj_stream_emit(mdj_stream *s, uint64_t first_row, uint64_t nrows, const mdj_window *out) {

@@ -26,6 +26,8 @@ STATUS = {
     -4: "MDJ_ERR_OOM", -5: "MDJ_ERR_CUDA", -6: "MDJ_ERR_DEVICE_TIMEOUT", -7: "MDJ_ERR_INTERNAL",
 }
 MDJ_I32, MDJ_I64, MDJ_F32, MDJ_F64, MDJ_U32, MDJ_U64 = 1, 2, 3, 4, 5, 6
+HOW = {"inner": 0, "left": 1, "right": 2, "outer": 3}   # mdj_how
+NO_ROW = 0xFFFFFFFF  # row id of the missing side of an outer-join row
 
 _TORCH_TO_MDJ = {
     torch.int32: MDJ_I32, torch.int64: MDJ_I64, torch.float32: MDJ_F32, torch.float64: MDJ_F64,
@@ -36,7 +38,7 @@ _MDJ_TO_TORCH = {v: k for k, v in _TORCH_TO_MDJ.items()}
 EXPORTED = [
     "mdj_partition", "mdj_partition_noalloc", "mdj_join", "mdj_merge", "mdj_count_checksum", "mdj_join_batch",
     "mdj_merge_batch", "mdj_stream_open", "mdj_stream_emit", "mdj_stream_next", "mdj_stream_rows",
-    "mdj_stream_close",
+    "mdj_stream_close", "mdj_transpose_add",
     "mdj_result_release",
     "mdj_status_string", "mdj_last_error", "mdj_version", "mdj_profile_enable", "mdj_profile_reset",
     "mdj_profile_collect", "mdj_profile_count", "mdj_profile_get",
@@ -124,7 +126,7 @@ def load(path: str = LIB_PATH):
         lib.mdj_merge_batch.argtypes = [P(MdjTable), i32, P(u64), P(MdjTable), i32, P(u64), i32, P(u32),
                                         P(MdjTuning), P(MdjAllocator), vp, P(MdjResult), P(u64)]
         lib.mdj_stream_open.restype = ctypes.c_int
-        lib.mdj_stream_open.argtypes = [P(MdjTable), i32, P(MdjTable), i32, u32, P(MdjAllocator), vp, P(vp),
+        lib.mdj_stream_open.argtypes = [P(MdjTable), i32, P(MdjTable), i32, u32, i32, P(MdjAllocator), vp, P(vp),
                                         P(u64)]
         lib.mdj_stream_emit.restype = ctypes.c_int
         lib.mdj_stream_emit.argtypes = [vp, u64, u64, P(MdjWindow)]
@@ -134,6 +136,8 @@ def load(path: str = LIB_PATH):
         lib.mdj_stream_rows.argtypes = [vp]
         lib.mdj_stream_close.restype = None
         lib.mdj_stream_close.argtypes = [vp]
+        lib.mdj_transpose_add.restype = ctypes.c_int
+        lib.mdj_transpose_add.argtypes = [vp, vp, u64, i32, vp]
         lib.mdj_result_release.restype = None
         lib.mdj_result_release.argtypes = [P(MdjResult), P(MdjAllocator), vp]
         lib.mdj_status_string.restype = ctypes.c_char_p
@@ -376,12 +380,16 @@ class MergeStream:
 
     Opening runs the shuffle and groups the left rows by key; `total_rows`
     is then exact, and rows [q0, q0 + n) of the fixed output order can be
-    written at any time into a window buffer.  The handle's device memory
-    comes from torch's caching allocator and is held until close().  The
-    input tensors must stay alive and unchanged until close()."""
+    written at any time into a window buffer.  `how` is "inner", "left",
+    "right" or "outer"; a row's missing side has row id NO_ROW and zero bits
+    in its columns.  The handle's device memory comes from torch's caching
+    allocator and is held until close().  The input tensors must stay alive
+    and unchanged until close()."""
 
     def __init__(self, left_cols: Sequence[torch.Tensor], right_cols: Sequence[torch.Tensor], P: int,
-                 left_key: int = 0, right_key: int = 0):
+                 left_key: int = 0, right_key: int = 0, how: str = "inner"):
+        if how not in HOW:
+            raise ValueError(f"how must be one of {sorted(HOW)}")
         lib = load()
         self._lib = lib
         self.device = left_cols[0].device
@@ -391,7 +399,7 @@ class MergeStream:
         self._alloc = TorchAllocator(self.device)
         self._h = ctypes.c_void_p()
         total = ctypes.c_uint64(0)
-        rc = lib.mdj_stream_open(ctypes.byref(lt), left_key, ctypes.byref(rt), right_key, P,
+        rc = lib.mdj_stream_open(ctypes.byref(lt), left_key, ctypes.byref(rt), right_key, P, HOW[how],
                                  ctypes.byref(self._alloc.struct), _stream_handle(self.device),
                                  ctypes.byref(self._h), ctypes.byref(total))
         _check(rc, "mdj_stream_open")
@@ -472,10 +480,40 @@ class MergeStream:
             pass
 
 
+def merge(left_cols: Sequence[torch.Tensor], right_cols: Sequence[torch.Tensor], P: int, how: str = "inner",
+          left_key: int = 0, right_key: int = 0) -> JoinResult:
+    """The merge with a join type: "inner" is mdj_merge; "left", "right" and
+    "outer" run the streamed path and write every row in one window."""
+    if how == "inner":
+        return mdj_merge(left_cols, right_cols, P, left_key, right_key)
+    with MergeStream(left_cols, right_cols, P, left_key, right_key, how) as st:
+        buf = st.buffers(st.total_rows)
+        if st.total_rows:
+            st.emit(0, st.total_rows, buf)
+        return buf
+
+
 def _view(buf: JoinResult, n: int) -> JoinResult:
     cut = (lambda t: None if t is None else t[:n])
     return JoinResult(n, cut(buf.key), cut(buf.left_row), cut(buf.right_row), [cut(t) for t in buf.left_cols],
                       [cut(t) for t in buf.right_cols])
+
+
+def transpose_add(x: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """y = x + x.T for a square, contiguous CUDA matrix (mdj_transpose_add in mdj.h).
+    `out` may be x itself (in place) or None (a new tensor)."""
+    lib = load()
+    if not x.is_cuda or x.dim() != 2 or x.shape[0] != x.shape[1] or not x.is_contiguous():
+        raise ValueError("x must be a square, contiguous CUDA matrix")
+    if x.dtype not in _TORCH_TO_MDJ:
+        raise TypeError(f"unsupported dtype {x.dtype}")
+    y = torch.empty_like(x) if out is None else out
+    if y.shape != x.shape or y.dtype != x.dtype or not y.is_contiguous() or y.device != x.device:
+        raise ValueError("out must match x in shape, dtype and device and be contiguous")
+    n = x.shape[0]
+    _check(lib.mdj_transpose_add(x.data_ptr() if n else None, y.data_ptr() if n else None, n,
+                                 _TORCH_TO_MDJ[x.dtype], _stream_handle(x.device)), "mdj_transpose_add")
+    return y
 
 
 def mdj_status_string(status: int) -> str:

@@ -87,30 +87,34 @@ def test_stream_argument_checks_need_no_gpu(lib):
     cols[0].dtype = 2
     t = MdjTable(cols, 1, 0)
     # null tables, bad key index, P out of range, float key, key dtype mismatch
-    assert lib.mdj_stream_open(None, 0, ctypes.byref(t), 0, 8, None, None, ctypes.byref(h),
+    assert lib.mdj_stream_open(None, 0, ctypes.byref(t), 0, 8, 0, None, None, ctypes.byref(h),
                                ctypes.byref(total)) == -1
     assert h.value is None and total.value == 0
-    assert lib.mdj_stream_open(ctypes.byref(t), 1, ctypes.byref(t), 0, 8, None, None, ctypes.byref(h),
+    assert lib.mdj_stream_open(ctypes.byref(t), 1, ctypes.byref(t), 0, 8, 0, None, None, ctypes.byref(h),
                                ctypes.byref(total)) == -1
-    assert lib.mdj_stream_open(ctypes.byref(t), 0, ctypes.byref(t), 0, 0, None, None, ctypes.byref(h),
+    assert lib.mdj_stream_open(ctypes.byref(t), 0, ctypes.byref(t), 0, 0, 0, None, None, ctypes.byref(h),
                                ctypes.byref(total)) == -1
-    assert lib.mdj_stream_open(ctypes.byref(t), 0, ctypes.byref(t), 0, 65537, None, None, ctypes.byref(h),
+    assert lib.mdj_stream_open(ctypes.byref(t), 0, ctypes.byref(t), 0, 65537, 0, None, None, ctypes.byref(h),
                                ctypes.byref(total)) == -1
     fcols = (MdjCol * 1)()
     fcols[0].dtype = 4
     ft = MdjTable(fcols, 1, 0)
-    assert lib.mdj_stream_open(ctypes.byref(ft), 0, ctypes.byref(ft), 0, 8, None, None, ctypes.byref(h),
+    assert lib.mdj_stream_open(ctypes.byref(ft), 0, ctypes.byref(ft), 0, 8, 0, None, None, ctypes.byref(h),
                                ctypes.byref(total)) == -2
     icols = (MdjCol * 1)()
     icols[0].dtype = 1
     it = MdjTable(icols, 1, 0)
-    assert lib.mdj_stream_open(ctypes.byref(t), 0, ctypes.byref(it), 0, 8, None, None, ctypes.byref(h),
+    assert lib.mdj_stream_open(ctypes.byref(t), 0, ctypes.byref(it), 0, 8, 0, None, None, ctypes.byref(h),
                                ctypes.byref(total)) == -1
     big = MdjTable(cols, 1, 1 << 32)
-    assert lib.mdj_stream_open(ctypes.byref(big), 0, ctypes.byref(t), 0, 8, None, None, ctypes.byref(h),
+    assert lib.mdj_stream_open(ctypes.byref(big), 0, ctypes.byref(t), 0, 8, 0, None, None, ctypes.byref(h),
                                ctypes.byref(total)) == -3
-    assert lib.mdj_stream_open(ctypes.byref(t), 0, ctypes.byref(t), 0, 8, None, None, None,
+    assert lib.mdj_stream_open(ctypes.byref(t), 0, ctypes.byref(t), 0, 8, 0, None, None, None,
                                ctypes.byref(total)) == -1
+    # join type outside mdj_how
+    for how in (-1, 4):
+        assert lib.mdj_stream_open(ctypes.byref(t), 0, ctypes.byref(t), 0, 8, how, None, None, ctypes.byref(h),
+                                   ctypes.byref(total)) == -1
     # calls on a missing handle
     w = MdjWindow()
     first, n = ctypes.c_uint64(0), ctypes.c_uint64(0)
@@ -118,3 +122,14 @@ def test_stream_argument_checks_need_no_gpu(lib):
     assert lib.mdj_stream_next(None, 10, ctypes.byref(w), ctypes.byref(first), ctypes.byref(n)) == -1
     assert lib.mdj_stream_rows(None) == 0
     lib.mdj_stream_close(None)
+
+
+def test_transpose_add_argument_checks_need_no_gpu(lib):
+    # n = 0 is a no-op; null pointers, unknown dtypes, n >= 2^32 and partial
+    # overlap are rejected before any CUDA call
+    assert lib.mdj_transpose_add(None, None, 0, 4, None) == 0
+    assert lib.mdj_transpose_add(None, None, 5, 4, None) == -1
+    assert lib.mdj_transpose_add(None, None, 5, 99, None) == -2
+    assert lib.mdj_transpose_add(4096, 8192, 1 << 32, 4, None) == -3
+    assert lib.mdj_transpose_add(4096, 4096 + 64, 8, 4, None) == -1
+    assert lib.mdj_transpose_add(4097, 4097, 8, 4, None) == -1

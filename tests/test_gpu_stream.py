@@ -46,9 +46,9 @@ def _host(v, mdj):
                           [cp(t) for t in v.right_cols])
 
 
-def _stream_all(left, right, P, window, lk=0, rk=0):
+def _stream_all(left, right, P, window, lk=0, rk=0, how="inner"):
     mdj = _mdj()
-    with mdj.MergeStream(_dev(left), _dev(right), P, lk, rk) as st:
+    with mdj.MergeStream(_dev(left), _dev(right), P, lk, rk, how) as st:
         parts = [_host(v, mdj) for _, v in st.windows(window)]
         total = st.total_rows
     torch.cuda.synchronize()
@@ -57,9 +57,9 @@ def _stream_all(left, right, P, window, lk=0, rk=0):
     return total, _concat(parts, mdj)
 
 
-def _check(left, right, P, window, lk=0, rk=0):
-    want = oracle.merge_table(left, right, lk, rk)
-    total, got = _stream_all(left, right, P, window, lk, rk)
+def _check(left, right, P, window, lk=0, rk=0, how="inner"):
+    want = oracle.merge_table_how(left, right, how, lk, rk)
+    total, got = _stream_all(left, right, P, window, lk, rk, how)
     assert total == want["key"].size
     if total:
         assert_same_result(gpu_result_np(got), want)
@@ -233,3 +233,76 @@ def test_stream_skewed_full_size_windows():
             assert torch.equal(v.right_cols[0].view(torch.int64), R[1].view(torch.int64)[ri])
             pair = torch.sort(li * 200_000_000 + ri).values
             assert torch.unique_consecutive(pair).numel() == rows
+
+
+# ------------------------------------------------ merge variants (outer joins)
+
+OUTER = ["left", "right", "outer"]
+
+
+@pytest.mark.parametrize("how", OUTER)
+@pytest.mark.parametrize("P", [1, 8])
+def test_outer_unique_build_keys(how, P):
+    left, right = datagen.match_fraction_tables(150_000, 200_000, 0.3, seed=41)
+    _check(list(left), list(right), P, window=50_001, how=how)
+
+
+@pytest.mark.parametrize("how", OUTER)
+def test_outer_duplicate_keys(how):
+    # overlapping but different key ranges: unmatched rows on both sides
+    rng = np.random.default_rng(42)
+    lk = rng.integers(0, 40_000, 120_000).astype(np.int64)
+    rk = rng.integers(20_000, 70_000, 90_000).astype(np.int64)
+    _check([lk, rng.random(lk.size)], [rk, rng.random(rk.size)], 8, window=77_777, how=how)
+
+
+@pytest.mark.parametrize("how", OUTER)
+def test_outer_heavy_keys(how):
+    left, right = _skewed_tables(43)
+    rng = np.random.default_rng(44)
+    # plus left-only and right-only keys, one of them heavy on each side
+    left[0] = np.concatenate([left[0], np.full(5000, -3), rng.integers(10**9, 2 * 10**9, 3000)])
+    left[1] = np.concatenate([left[1], rng.random(8000)])
+    right[0] = np.concatenate([right[0], np.full(7000, -5), rng.integers(3 * 10**9, 4 * 10**9, 3000)])
+    right[1] = np.concatenate([right[1], rng.random(10_000)])
+    _check(left, right, 8, window=2_000_003, how=how)
+
+
+@pytest.mark.parametrize("how", OUTER)
+def test_outer_int32_several_columns(how):
+    (lk, lp), (rk, rp) = datagen.random_tables(40_000, 60_000, 100_000, seed=45, key_dtype=np.int32,
+                                               pay_dtype=np.float32)
+    rng = np.random.default_rng(46)
+    lx = rng.integers(0, 2**62, lk.size, dtype=np.int64)
+    _check([lk, lp, lx], [rp, rk], 4, window=9_999, lk=0, rk=1, how=how)
+
+
+@pytest.mark.parametrize("how", ["inner"] + OUTER)
+@pytest.mark.parametrize("nl,nr", [(0, 3000), (3000, 0), (0, 0)])
+def test_outer_empty_side(how, nl, nr):
+    left, right = datagen.match_fraction_tables(max(nl, 1), max(nr, 1), 0.3, seed=47)
+    left = [c[:nl] for c in left]
+    right = [c[:nr] for c in right]
+    want = oracle.merge_table_how(left, right, how)
+    total, got = _stream_all(left, right, 8, 1000, how=how)
+    assert total == want["key"].size
+    if total:
+        assert_same_result(gpu_result_np(got), want)
+
+
+@pytest.mark.parametrize("how", OUTER)
+def test_outer_small_unpartitioned(how):
+    left, right = datagen.random_tables(2_000, 3_000, 4_000, seed=48)
+    _check(list(left), list(right), 1, window=333, how=how)
+
+
+def test_merge_how_one_call():
+    mdj = _mdj()
+    rng = np.random.default_rng(49)
+    lk = rng.integers(0, 5000, 20_000).astype(np.int64)
+    rk = rng.integers(2500, 7500, 20_000).astype(np.int64)
+    left, right = [lk, rng.random(lk.size)], [rk, rng.random(rk.size)]
+    res = mdj.merge(_dev(left), _dev(right), 8, how="outer")
+    torch.cuda.synchronize()
+    want = oracle.merge_table_how(left, right, "outer")
+    assert_same_result(gpu_result_np(res), want)

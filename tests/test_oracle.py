@@ -253,3 +253,113 @@ def test_zipf_skew_matches_closed_form():
     rng = np.random.default_rng(5)
     keys = datagen.zipf_keys(rng, 2_000_000, 10_000_000, 1.1)
     assert abs(np.mean(keys == 0) - p[0]) < 5 * np.sqrt(p[0] * (1 - p[0]) / 2_000_000)
+
+
+# ------------------------------------------------ transpose-sum (Fig. 7, 9(a))
+
+def _loop_transpose_add(x):
+    n = x.shape[0]
+    y = np.empty_like(x)
+    for i in range(n):
+        for j in range(n):
+            y[i, j] = x[i, j] + x[j, i]
+    return y
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32, np.int64, np.int32])
+def test_transpose_add_equals_element_loop(dtype):
+    rng = np.random.default_rng(11)
+    x = (rng.standard_normal((9, 9)) * 1000).astype(dtype)
+    assert np.array_equal(oracle.transpose_add(x), _loop_transpose_add(x))
+
+
+def test_transpose_add_symmetric_and_antisymmetric_inputs():
+    # y = x + x^T is symmetric bit for bit (IEEE addition commutes); a
+    # symmetric x gives exactly 2x, an antisymmetric x (u - u^T) exactly 0
+    rng = np.random.default_rng(12)
+    u = rng.random((37, 37))
+    y = oracle.transpose_add(u)
+    assert np.array_equal(y.view(np.uint64), y.T.view(np.uint64))
+    s = u + u.T
+    assert np.array_equal(oracle.transpose_add(s), 2 * s)
+    a = u - u.T
+    assert np.array_equal(oracle.transpose_add(a), np.zeros_like(a))
+    assert np.array_equal(np.diag(oracle.transpose_add(u)), 2 * np.diag(u))
+
+
+def test_transpose_add_integer_wraparound():
+    x = np.array([[2**63 - 1, 5], [-7, 0]], dtype=np.int64)
+    y = oracle.transpose_add(x)
+    assert y[0, 0] == -2 and y[0, 1] == -2 and y[1, 0] == -2 and y[1, 1] == 0
+    x32 = np.array([[2**31 - 1, 1], [1, -2**31]], dtype=np.int32)
+    assert oracle.transpose_add(x32)[0, 0] == -2 and oracle.transpose_add(x32)[1, 1] == 0
+
+
+def test_transpose_sum_sizes_of_the_paper():
+    # 16K x 16K (Fig. 7) and 20E3 x 20E3 (Fig. 9(a)) float64 arrays
+    assert 16384 * 16384 * 8 == 2 * 2**30
+    assert 20_000 * 20_000 * 8 == 3_200_000_000
+    with pytest.raises(ValueError):
+        oracle.transpose_add(np.zeros((2, 3)))
+
+
+# ------------------------------------------------ merge variants (outer joins)
+
+def _loop_outer(lk, lp, rk, rp, how):
+    """Nested loops, written from the definition: every matching pair; then
+    each left row without a match (left, outer) and each right row without a
+    match (right, outer), once, with the other side missing."""
+    rows = []
+    for i in range(lk.size):
+        found = False
+        for j in range(rk.size):
+            if lk[i] == rk[j]:
+                rows.append((int(lk[i]), i, j, lp[i], rp[j]))
+                found = True
+        if not found and how in ("left", "outer"):
+            rows.append((int(lk[i]), i, oracle.NO_ROW, lp[i], 0.0))
+    if how in ("right", "outer"):
+        for j in range(rk.size):
+            if not any(lk[i] == rk[j] for i in range(lk.size)):
+                rows.append((int(rk[j]), oracle.NO_ROW, j, 0.0, rp[j]))
+    rows.sort(key=lambda t: (t[0], t[1], t[2]))
+    return rows
+
+
+@pytest.mark.parametrize("how", ["inner", "left", "right", "outer"])
+def test_merge_variants_equal_nested_loops(how):
+    rng = np.random.default_rng(21)
+    lk = rng.integers(0, 40, 120).astype(np.int64)
+    rk = rng.integers(20, 70, 90).astype(np.int64)
+    lp, rp = rng.random(lk.size), rng.random(rk.size)
+    got = oracle.merge_table_how([lk, lp], [rk, rp], how)
+    want = _loop_outer(lk, lp, rk, rp, how)
+    assert got["key"].size == len(want)
+    assert [int(x) for x in got["key"]] == [t[0] for t in want]
+    assert [int(x) for x in got["left_row"]] == [t[1] for t in want]
+    assert [int(x) for x in got["right_row"]] == [t[2] for t in want]
+    assert np.array_equal(got["left_cols"][0], np.array([t[3] for t in want]))
+    assert np.array_equal(got["right_cols"][0], np.array([t[4] for t in want]))
+
+
+def test_merge_variant_row_counts():
+    # left join: each left row max(1, matches); right join likewise; outer =
+    # inner + unmatched on both sides; missing sides carry zero bits
+    rng = np.random.default_rng(22)
+    lk = rng.integers(0, 500, 3000).astype(np.int32)
+    rk = rng.integers(250, 900, 2000).astype(np.int32)
+    lp, rp = rng.random(lk.size).astype(np.float32), rng.random(rk.size).astype(np.float32)
+    lc = np.bincount(lk, minlength=900)
+    rc = np.bincount(rk, minlength=900)
+    inner = int(np.sum(lc * rc))
+    left = oracle.merge_table_how([lk, lp], [rk, rp], "left")
+    right = oracle.merge_table_how([lk, lp], [rk, rp], "right")
+    outer = oracle.merge_table_how([lk, lp], [rk, rp], "outer")
+    assert left["key"].size == int(np.sum(np.maximum(1, rc[lk])))
+    assert right["key"].size == int(np.sum(np.maximum(1, lc[rk])))
+    assert outer["key"].size == inner + int(np.sum(rc[lk] == 0)) + int(np.sum(lc[rk] == 0))
+    miss = outer["right_row"] == oracle.NO_ROW
+    assert np.all(outer["right_cols"][0][miss].view(np.uint32) == 0)
+    assert np.all(lk[outer["left_row"][miss]] == outer["key"][miss])
+    assert np.array_equal(oracle.merge_table_how([lk, lp], [rk, rp], "inner")["key"],
+                          oracle.merge_table([lk, lp], [rk, rp])["key"])
