@@ -296,6 +296,11 @@ def run_gpu(args):
     if args.stream_windows > 0:
         stream_plain = stream_whole(left, right, m_expect, ms_step, dev)
 
+    # ---- the same tables merged from host memory under a 1 GiB device budget
+    host_tables = None
+    if args.host_budget_mib > 0:
+        host_tables = host_tables_section(args, dev, (lk, lp), (rk, rp), m_expect)
+
     # ---- end to end: host (pinned) inputs -> device -> merge -> host result
     e2e = None
     if args.e2e_steps > 0:
@@ -331,6 +336,8 @@ def run_gpu(args):
         "roofline": roofline, "step_roofline": step_roof, "kernels": kernels, "gpu_launches": launches,
         "e2e": e2e, "clocks": clk.summary(),
     }
+    if host_tables is not None:
+        line["host_tables"] = host_tables
     if args.stream_windows > 0:
         torch.cuda.empty_cache()
         line["streamed"] = streamed_section(args, dev)
@@ -350,17 +357,49 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def host_tables_section(args, dev, left_np, right_np, m_expect):
+    """The bench tables held in host memory (3.2 GB, pageable) and merged
+    through mdj_merge_host with a device budget smaller than the tables:
+    chunked hash partition into host buckets, then one stream per bucket pair,
+    each window handed to a sink that counts rows (nothing is kept).  Wall
+    time of one call after one warm-up call on a 1/10 sample."""
+    import torch
+    from paper_2101_08878_gb300 import mdj
+
+    budget = args.host_budget_mib << 20
+    L = [torch.from_numpy(c) for c in left_np]
+    R = [torch.from_numpy(c) for c in right_np]
+    seen = [0]
+
+    def count(first_row, piece):
+        seen[0] += piece.nrows
+
+    k = len(L[0]) // 10
+    mdj.merge_host_chunked([c[:k] for c in L], [c[:k] for c in R], P, budget, on_piece=count, device=dev)
+    seen[0] = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    total, _ = mdj.merge_host_chunked(L, R, P, budget, on_piece=count, device=dev)
+    wall = time.perf_counter() - t0
+    assert total == seen[0] == m_expect, (total, seen[0])
+    in_bytes = sum(c.numel() * c.element_size() for c in L + R)
+    return {"workload": "the bench tables in pageable host memory, inner merge, sink counts rows",
+            "device_budget_bytes": budget, "input_bytes": in_bytes, "rows": total, "wall_s": round(wall, 3),
+            "value": (len(L[0]) + len(R[0])) / wall, "unit": "input rows/s"}
+
+
 def stream_whole(left, right, m_expect, merge_ms, dev):
     """The bench workload through mdj_stream_open + one window of every row,
     against mdj_merge: what the streamed path costs when the result fits."""
     import torch
     from paper_2101_08878_gb300 import mdj
 
-    def once():
+    def once(how="inner"):
         t0 = time.perf_counter()
-        st = mdj.MergeStream(left, right, P)
+        st = mdj.MergeStream(left, right, P, how=how)
         t_open = time.perf_counter() - t0
-        assert st.total_rows == m_expect
+        assert how != "inner" or st.total_rows == m_expect
+        rows = st.total_rows
         buf = st.buffers(st.total_rows)
         stream = torch.cuda.current_stream(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -369,15 +408,19 @@ def stream_whole(left, right, m_expect, merge_ms, dev):
         e1.record(stream)
         torch.cuda.synchronize()
         st.close()
-        return t_open * 1e3, e0.elapsed_time(e1)
+        del buf
+        return t_open * 1e3, e0.elapsed_time(e1), rows
 
     once()
     runs = [once() for _ in range(3)]
     open_ms = statistics.median(r[0] for r in runs)
     emit_ms = statistics.median(r[1] for r in runs)
+    once("outer")
+    o_open, o_emit, o_rows = once("outer")
     return {"open_ms": round(open_ms, 3), "emit_ms": round(emit_ms, 3),
             "total_ms": round(open_ms + emit_ms, 3), "merge_ms": round(merge_ms, 3),
-            "rows": m_expect, "note": "open is host-timed (it ends with the count read back); emit by CUDA events"}
+            "rows": m_expect, "note": "open is host-timed (it ends with the count read back); emit by CUDA events",
+            "outer_join": {"rows": o_rows, "open_ms": round(o_open, 3), "emit_ms": round(o_emit, 3)}}
 
 
 def zipf_device(n: int, n_values: int, s: float, gen, dev):
@@ -701,6 +744,8 @@ def main():
     ap.add_argument("--serve-batch-rows", type=int, default=80_000_000,
                     help="input rows per continuous-batching group at most (larger requests run alone)")
     ap.add_argument("--serve-pool", type=int, default=32, help="distinct table pairs the requests draw from")
+    ap.add_argument("--host-budget-mib", type=int, default=1024,
+                    help="device budget of the host-tables section in MiB (0 skips it)")
     ap.add_argument("--transpose-steps", type=int, default=10,
                     help="timed calls per size of the transpose-sum section (0 skips it)")
     ap.add_argument("--stream-windows", type=int, default=6,

@@ -62,7 +62,8 @@ typedef enum {
     MDJ_ERR_OOM = -4,               /* the allocator returned NULL */
     MDJ_ERR_CUDA = -5,              /* a CUDA runtime call failed */
     MDJ_ERR_DEVICE_TIMEOUT = -6,    /* a bounded device-side wait gave up */
-    MDJ_ERR_INTERNAL = -7           /* a device-side consistency check failed */
+    MDJ_ERR_INTERNAL = -7,          /* a device-side consistency check failed */
+    MDJ_ERR_ABORTED = -8            /* a caller's sink asked to stop (mdj_merge_host) */
 } mdj_status;
 
 typedef enum {
@@ -326,6 +327,41 @@ MDJ_API uint64_t mdj_stream_rows(const mdj_stream *s);
 
 /* Releases every device buffer of the handle (stream order) and the handle. */
 MDJ_API void mdj_stream_close(mdj_stream *s);
+
+/*
+ * mdj_merge_host - the merge of HOST-resident tables that need not fit device
+ * memory.  The paper's runtime sends messages above MPI's 2 GB count limit as
+ * 1 GB chunks (Sec. IV-B); here the tables themselves pass through the device
+ * in pieces bounded by `device_budget`:
+ *   1. each table goes to the device in chunks; every chunk is hash
+ *      partitioned into B buckets (bucket = h mod B, as mdj_partition) and the
+ *      buckets return to host memory with the rows' input row ids;
+ *   2. for each bucket b, both tables' bucket b go to the device, their merge
+ *      is opened as a stream (mdj_stream_open with P and `how`), and its rows
+ *      are written window by window; each window's row ids are mapped back to
+ *      the input tables and the window is handed to `sink`.
+ *   left, right   : tables whose column pointers are HOST pointers (pageable
+ *                   or pinned), read only
+ *   device_budget : bytes of device memory the call sizes its pieces for
+ *                   (>= 64 MiB, else MDJ_ERR_INVALID_ARG): B, the chunk rows
+ *                   and the window rows follow from it
+ *   sink          : called once per window with a result whose arrays are
+ *                   DEVICE pointers valid only during the call (copy what you
+ *                   keep); first_row counts the rows handed over before it.
+ *                   Returning non-zero stops the merge with MDJ_ERR_ABORTED.
+ *   *total_rows   : rows handed to the sink
+ * Row ids index the input tables; a missing side (outer joins) is
+ * 0xFFFFFFFF as in mdj_stream_open.  Rows arrive bucket by bucket, each
+ * bucket in its stream order.  All rows of one key share a bucket, so a key
+ * whose rows exceed about a sixth of the budget gives MDJ_ERR_OOM.  Host
+ * memory for the buckets (the tables' size again, plus 4 bytes per row) is
+ * the library's own.  Synchronises `stream`.
+ */
+typedef int (*mdj_sink)(const mdj_result *piece, uint64_t first_row, void *ctx);
+
+MDJ_API int mdj_merge_host(const mdj_table *left, int32_t left_key, const mdj_table *right, int32_t right_key,
+                           uint32_t P, int32_t how, uint64_t device_budget, mdj_sink sink, void *sink_ctx,
+                           const mdj_allocator *alloc, void *stream, uint64_t *total_rows);
 
 /*
  * mdj_transpose_add - the paper's second application benchmark, the sum of an

@@ -248,6 +248,7 @@ const char *mdj_status_string(int status) {
     case MDJ_ERR_CUDA: return "CUDA runtime error";
     case MDJ_ERR_DEVICE_TIMEOUT: return "bounded device-side wait expired";
     case MDJ_ERR_INTERNAL: return "internal consistency check failed";
+    case MDJ_ERR_ABORTED: return "stopped by the caller's sink";
     default: return "unknown status";
   }
 }

@@ -23,6 +23,12 @@
 // sides of any size are split into chunks over many blocks (a light
 // sub-bucket's table is saved once and reloaded by its other chunks, so every
 // chunk sees the same table).
+//
+// Merge variants: a right or outer join makes every probe row an entry (an
+// unmatched one a single row with no left side); a left or outer join also
+// records each group's size and whether any probe row found it, and appends
+// one entry per group nobody found (no right side).  A missing side is row id
+// kNone (0xFFFFFFFF) with zero bits in its columns.
 #include <string.h>
 
 #include <algorithm>

@@ -24,6 +24,7 @@ MDJ_OK = 0
 STATUS = {
     0: "MDJ_OK", -1: "MDJ_ERR_INVALID_ARG", -2: "MDJ_ERR_UNSUPPORTED_DTYPE", -3: "MDJ_ERR_TOO_LARGE",
     -4: "MDJ_ERR_OOM", -5: "MDJ_ERR_CUDA", -6: "MDJ_ERR_DEVICE_TIMEOUT", -7: "MDJ_ERR_INTERNAL",
+    -8: "MDJ_ERR_ABORTED",
 }
 MDJ_I32, MDJ_I64, MDJ_F32, MDJ_F64, MDJ_U32, MDJ_U64 = 1, 2, 3, 4, 5, 6
 HOW = {"inner": 0, "left": 1, "right": 2, "outer": 3}   # mdj_how
@@ -38,7 +39,7 @@ _MDJ_TO_TORCH = {v: k for k, v in _TORCH_TO_MDJ.items()}
 EXPORTED = [
     "mdj_partition", "mdj_partition_noalloc", "mdj_join", "mdj_merge", "mdj_count_checksum", "mdj_join_batch",
     "mdj_merge_batch", "mdj_stream_open", "mdj_stream_emit", "mdj_stream_next", "mdj_stream_rows",
-    "mdj_stream_close", "mdj_transpose_add",
+    "mdj_stream_close", "mdj_transpose_add", "mdj_merge_host",
     "mdj_result_release",
     "mdj_status_string", "mdj_last_error", "mdj_version", "mdj_profile_enable", "mdj_profile_reset",
     "mdj_profile_collect", "mdj_profile_count", "mdj_profile_get",
@@ -84,6 +85,9 @@ class MdjWindow(ctypes.Structure):
         ("key", ctypes.c_void_p), ("left_row", ctypes.c_void_p), ("right_row", ctypes.c_void_p),
         ("left_cols", ctypes.c_void_p * MDJ_MAX_COLS), ("right_cols", ctypes.c_void_p * MDJ_MAX_COLS),
     ]
+
+
+SINK_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(MdjResult), ctypes.c_uint64, ctypes.c_void_p)
 
 
 class MdjTuning(ctypes.Structure):
@@ -136,6 +140,9 @@ def load(path: str = LIB_PATH):
         lib.mdj_stream_rows.argtypes = [vp]
         lib.mdj_stream_close.restype = None
         lib.mdj_stream_close.argtypes = [vp]
+        lib.mdj_merge_host.restype = ctypes.c_int
+        lib.mdj_merge_host.argtypes = [P(MdjTable), i32, P(MdjTable), i32, u32, i32, u64, SINK_FN, vp,
+                                       P(MdjAllocator), vp, P(u64)]
         lib.mdj_transpose_add.restype = ctypes.c_int
         lib.mdj_transpose_add.argtypes = [vp, vp, u64, i32, vp]
         lib.mdj_result_release.restype = None
@@ -497,6 +504,95 @@ def _view(buf: JoinResult, n: int) -> JoinResult:
     cut = (lambda t: None if t is None else t[:n])
     return JoinResult(n, cut(buf.key), cut(buf.left_row), cut(buf.right_row), [cut(t) for t in buf.left_cols],
                       [cut(t) for t in buf.right_cols])
+
+
+class _DeviceArray:
+    """A borrowed device array, seen by torch through __cuda_array_interface__."""
+
+    _TYPESTR = {torch.int32: "<i4", torch.int64: "<i8", torch.float32: "<f4", torch.float64: "<f8",
+                torch.uint32: "<u4", torch.uint64: "<u8"}
+
+    def __init__(self, ptr: int, n: int, dtype: torch.dtype):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": self._TYPESTR[dtype], "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+def _host_table(cols: Sequence[torch.Tensor]):
+    if not 1 <= len(cols) <= MDJ_MAX_COLS:
+        raise ValueError(f"a table needs 1..{MDJ_MAX_COLS} columns")
+    n = cols[0].numel()
+    arr = (MdjCol * len(cols))()
+    for j, c in enumerate(cols):
+        if c.is_cuda or c.dim() != 1 or c.numel() != n or not c.is_contiguous():
+            raise ValueError("columns must be contiguous 1-D host tensors of equal length")
+        if c.dtype not in _TORCH_TO_MDJ:
+            raise TypeError(f"unsupported column dtype {c.dtype}")
+        arr[j].data = c.data_ptr() if n else None
+        arr[j].dtype = _TORCH_TO_MDJ[c.dtype]
+    return MdjTable(arr, len(cols), n), arr
+
+
+def merge_host_chunked(left_cols: Sequence[torch.Tensor], right_cols: Sequence[torch.Tensor], P: int,
+                       device_budget: int, how: str = "inner", left_key: int = 0, right_key: int = 0,
+                       on_piece=None, device: Optional[torch.device] = None):
+    """The merge of host (CPU) tables that need not fit device memory
+    (mdj_merge_host in mdj.h).  on_piece(first_row, JoinResult) receives each
+    window as device tensors valid only during the call; by default the
+    windows are copied to the host and returned as one JoinResult of CPU
+    tensors.  Returns (total rows, that JoinResult or None)."""
+    if how not in HOW:
+        raise ValueError(f"how must be one of {sorted(HOW)}")
+    lib = load()
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    lt, lk_keep = _host_table(left_cols)
+    rt, rk_keep = _host_table(right_cols)
+    parts = []
+    failure = []
+
+    def collect(first_row, res):
+        parts.append(JoinResult(res.nrows, res.key.cpu(), res.left_row.cpu(), res.right_row.cpu(),
+                                [c.cpu() for c in res.left_cols], [c.cpu() for c in res.right_cols]))
+
+    consume = on_piece or collect
+
+    def sink(piece_p, first_row, ctx):
+        try:
+            pc = piece_p.contents
+            n = int(pc.nrows)
+            view = (lambda ptr, dt: torch.as_tensor(_DeviceArray(ptr, n, dt), device=dev))
+            res = JoinResult(n, view(pc.key, _MDJ_TO_TORCH[pc.key_dtype]), view(pc.left_row, torch.uint32),
+                             view(pc.right_row, torch.uint32),
+                             [view(pc.left_cols[j], _MDJ_TO_TORCH[pc.left_dtypes[j]]) for j in range(pc.n_left_cols)],
+                             [view(pc.right_cols[j], _MDJ_TO_TORCH[pc.right_dtypes[j]])
+                              for j in range(pc.n_right_cols)])
+            consume(int(first_row), res)
+            return 0
+        except Exception as e:  # noqa: BLE001 - reported after the call returns
+            failure.append(e)
+            return 1
+
+    cb = SINK_FN(sink)
+    alloc = TorchAllocator(dev)
+    total = ctypes.c_uint64(0)
+    rc = lib.mdj_merge_host(ctypes.byref(lt), left_key, ctypes.byref(rt), right_key, P, HOW[how], int(device_budget),
+                            cb, None, ctypes.byref(alloc.struct), _stream_handle(dev), ctypes.byref(total))
+    if failure:
+        raise failure[0]
+    _check(rc, "mdj_merge_host")
+    if on_piece is not None:
+        return int(total.value), None
+    if not parts:
+        kd = left_cols[left_key].dtype
+        empty = (lambda dt: torch.empty(0, dtype=dt))
+        return 0, JoinResult(0, empty(kd), empty(torch.uint32), empty(torch.uint32),
+                             [empty(c.dtype) for j, c in enumerate(left_cols) if j != left_key],
+                             [empty(c.dtype) for j, c in enumerate(right_cols) if j != right_key])
+    cat = torch.cat
+    out = JoinResult(int(total.value), cat([p.key for p in parts]), cat([p.left_row for p in parts]),
+                     cat([p.right_row for p in parts]),
+                     [cat([p.left_cols[j] for p in parts]) for j in range(len(parts[0].left_cols))],
+                     [cat([p.right_cols[j] for p in parts]) for j in range(len(parts[0].right_cols))])
+    return int(total.value), out
 
 
 def transpose_add(x: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:

@@ -133,3 +133,31 @@ def test_transpose_add_argument_checks_need_no_gpu(lib):
     assert lib.mdj_transpose_add(4096, 8192, 1 << 32, 4, None) == -3
     assert lib.mdj_transpose_add(4096, 4096 + 64, 8, 4, None) == -1
     assert lib.mdj_transpose_add(4097, 4097, 8, 4, None) == -1
+
+
+def test_merge_host_argument_checks_need_no_gpu(lib):
+    from paper_2101_08878_gb300.mdj import SINK_FN, MdjCol, MdjTable
+    sink = SINK_FN(lambda piece, first, ctx: 0)
+    total = ctypes.c_uint64(9)
+    cols = (MdjCol * 1)()
+    cols[0].dtype = 2
+    t = MdjTable(cols, 1, 0)
+    big_budget = 1 << 30
+    # a budget below 64 MiB, a missing sink, a bad join type, P = 0, float keys, too many rows
+    assert lib.mdj_merge_host(ctypes.byref(t), 0, ctypes.byref(t), 0, 8, 0, 1 << 20, sink, None, None, None,
+                              ctypes.byref(total)) == -1
+    assert lib.mdj_merge_host(ctypes.byref(t), 0, ctypes.byref(t), 0, 8, 0, big_budget, SINK_FN(), None, None,
+                              None, ctypes.byref(total)) == -1
+    assert lib.mdj_merge_host(ctypes.byref(t), 0, ctypes.byref(t), 0, 8, 7, big_budget, sink, None, None, None,
+                              ctypes.byref(total)) == -1
+    assert lib.mdj_merge_host(ctypes.byref(t), 0, ctypes.byref(t), 0, 0, 0, big_budget, sink, None, None, None,
+                              ctypes.byref(total)) == -1
+    fcols = (MdjCol * 1)()
+    fcols[0].dtype = 4
+    ft = MdjTable(fcols, 1, 0)
+    assert lib.mdj_merge_host(ctypes.byref(ft), 0, ctypes.byref(ft), 0, 8, 0, big_budget, sink, None, None, None,
+                              ctypes.byref(total)) == -2
+    big = MdjTable(cols, 1, 1 << 32)
+    assert lib.mdj_merge_host(ctypes.byref(big), 0, ctypes.byref(t), 0, 8, 0, big_budget, sink, None, None, None,
+                              ctypes.byref(total)) == -3
+    assert lib.mdj_status_string(-8) == b"stopped by the caller's sink"
