@@ -329,6 +329,25 @@ MDJ_API uint64_t mdj_stream_rows(const mdj_stream *s);
 MDJ_API void mdj_stream_close(mdj_stream *s);
 
 /*
+ * mdj_merge_multi - the merge of mdj_merge on several key columns (a merge
+ * variant: the key is the tuple of columns left_keys[a] = right_keys[a],
+ * a < nkeys).  Inner join: every pair (l, r) whose tuples are equal column by
+ * column.  Each tuple is hashed to a 64-bit surrogate, the surrogates are
+ * merged as mdj_merge does (P partitions), and every candidate row's two
+ * tuples are then compared, so hash collisions never reach the result.
+ *   left_keys, right_keys : host arrays of nkeys distinct column indices
+ *                           (1 <= nkeys <= 8); key columns are I32 / I64 /
+ *                           U32 / U64, equal dtypes pairwise, compared as bits
+ * The result has no `key` array (NULL, key_dtype 0): left_cols holds the left
+ * key columns in left_keys order, then the left table's other columns in
+ * table order; right_cols holds the right table's non-key columns.  Tables
+ * may have at most MDJ_MAX_COLS - 1 columns.  Synchronises `stream`.
+ */
+MDJ_API int mdj_merge_multi(const mdj_table *left, const int32_t *left_keys, const mdj_table *right,
+                            const int32_t *right_keys, int32_t nkeys, uint32_t P, const mdj_allocator *alloc,
+                            void *stream, mdj_result *out);
+
+/*
  * mdj_merge_host - the merge of HOST-resident tables that need not fit device
  * memory.  The paper's runtime sends messages above MPI's 2 GB count limit as
  * 1 GB chunks (Sec. IV-B); here the tables themselves pass through the device

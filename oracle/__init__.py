@@ -202,6 +202,21 @@ def merge_table_how(left_cols, right_cols, how: str, key_col_l: int = 0, key_col
             "left_cols": [c[order] for c in left_out], "right_cols": [c[order] for c in right_out]}
 
 
+def merge_multi(left_cols, right_cols, left_keys, right_keys):
+    """Inner merge on key tuples (left_keys[a] = right_keys[a] for every a):
+    row pairs (lrow, rrow) in (lrow, rrow) order.  The tuples of both tables
+    are numbered by np.unique over their rows (equal tuples, equal number),
+    then the numbers are merged by merge_pairs."""
+    lt = np.stack([np.asarray(left_cols[k]).astype(np.int64) for k in left_keys], axis=1)
+    rt = np.stack([np.asarray(right_cols[k]).astype(np.int64) for k in right_keys], axis=1)
+    both = np.concatenate([lt, rt], axis=0) if lt.size + rt.size else np.zeros((0, len(left_keys)), np.int64)
+    _, ids = np.unique(both, axis=0, return_inverse=True)
+    ids = ids.reshape(-1).astype(np.int64)
+    lrow, rrow = merge_pairs(ids[:lt.shape[0]], ids[lt.shape[0]:])
+    order = np.lexsort((rrow, lrow))
+    return lrow[order], rrow[order]
+
+
 def brute_force(lkeys, rkeys):
     """Nested-loop inner join (independent of the C code) for tiny inputs.
 

@@ -161,3 +161,28 @@ def test_merge_host_argument_checks_need_no_gpu(lib):
     assert lib.mdj_merge_host(ctypes.byref(big), 0, ctypes.byref(t), 0, 8, 0, big_budget, sink, None, None, None,
                               ctypes.byref(total)) == -3
     assert lib.mdj_status_string(-8) == b"stopped by the caller's sink"
+
+
+def test_merge_multi_argument_checks_need_no_gpu(lib):
+    from paper_2101_08878_gb300.mdj import MdjCol, MdjResult, MdjTable
+    res = MdjResult()
+    cols = (MdjCol * 2)()
+    cols[0].dtype = 2
+    cols[1].dtype = 1
+    t = MdjTable(cols, 2, 0)
+    k2 = (ctypes.c_int32 * 2)(0, 1)
+    dup = (ctypes.c_int32 * 2)(0, 0)
+    out_of_range = (ctypes.c_int32 * 2)(0, 5)
+    assert lib.mdj_merge_multi(ctypes.byref(t), k2, ctypes.byref(t), k2, 0, 8, None, None, ctypes.byref(res)) == -1
+    assert lib.mdj_merge_multi(ctypes.byref(t), k2, ctypes.byref(t), k2, 9, 8, None, None, ctypes.byref(res)) == -1
+    assert lib.mdj_merge_multi(ctypes.byref(t), dup, ctypes.byref(t), k2, 2, 8, None, None, ctypes.byref(res)) == -1
+    assert lib.mdj_merge_multi(ctypes.byref(t), k2, ctypes.byref(t), out_of_range, 2, 8, None, None,
+                               ctypes.byref(res)) == -1
+    swapped = (ctypes.c_int32 * 2)(1, 0)  # I64 against I32
+    assert lib.mdj_merge_multi(ctypes.byref(t), k2, ctypes.byref(t), swapped, 2, 8, None, None,
+                               ctypes.byref(res)) == -1
+    fcols = (MdjCol * 2)()
+    fcols[0].dtype = 4
+    fcols[1].dtype = 1
+    ft = MdjTable(fcols, 2, 0)
+    assert lib.mdj_merge_multi(ctypes.byref(ft), k2, ctypes.byref(ft), k2, 2, 8, None, None, ctypes.byref(res)) == -2

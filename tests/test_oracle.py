@@ -363,3 +363,30 @@ def test_merge_variant_row_counts():
     assert np.all(lk[outer["left_row"][miss]] == outer["key"][miss])
     assert np.array_equal(oracle.merge_table_how([lk, lp], [rk, rp], "inner")["key"],
                           oracle.merge_table([lk, lp], [rk, rp])["key"])
+
+
+# ------------------------------------------------ several key columns
+
+def test_merge_multi_equals_nested_loops():
+    rng = np.random.default_rng(61)
+    a = rng.integers(0, 6, 200).astype(np.int64)
+    b = rng.integers(0, 5, 200).astype(np.int32)
+    c = rng.integers(0, 6, 150).astype(np.int64)
+    d = rng.integers(0, 5, 150).astype(np.int32)
+    lrow, rrow = oracle.merge_multi([a, b], [d, c], [0, 1], [1, 0])
+    want = sorted((i, j) for i in range(a.size) for j in range(c.size) if a[i] == c[j] and b[i] == d[j])
+    assert list(zip(lrow.tolist(), rrow.tolist())) == want
+    # one key column: the plain merge's pairs
+    l1, r1 = oracle.merge_multi([a], [c], [0], [0])
+    pl, pr = oracle.merge_pairs(a, c)
+    assert sorted(zip(l1.tolist(), r1.tolist())) == sorted(zip(pl.tolist(), pr.tolist()))
+
+
+def test_merge_multi_is_not_a_merge_on_the_first_column():
+    # tuples equal on the first column only must not join
+    # (the first column alone would join (0,0) (0,1) (1,0) (1,1) (2,2))
+    a = np.array([1, 1, 2], np.int64)
+    b = np.array([5, 6, 5], np.int64)
+    rb = np.array([6, 5, 9], np.int64)
+    lrow, rrow = oracle.merge_multi([a, b], [a, rb], [0, 1], [0, 1])
+    assert list(zip(lrow.tolist(), rrow.tolist())) == [(0, 1), (1, 0)]
