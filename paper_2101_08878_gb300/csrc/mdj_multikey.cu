@@ -190,20 +190,15 @@ int merge_multi_impl(const mdj_table *left, const int32_t *lkeys, const mdj_tabl
   for (int j = 0; j < cand.n_left_cols; j++) r.left_dtypes[j] = cand.left_dtypes[j];
   r.n_right_cols = cand.n_right_cols - nkeys;
   for (int j = 0; j < r.n_right_cols; j++) r.right_dtypes[j] = cand.right_dtypes[nkeys + j];
-  auto give_back = [&](void *p) {
-    if (p && alloc && alloc->release)
-      alloc->release(p, alloc->ctx, stream);
-    else if (p && !(alloc && alloc->alloc))
-      cudaFreeAsync(p, s);
-  };
   if (host_dropped == 0) {  // every candidate stands: keep its buffers
     r.nrows = m;
     r.left_row = cand.left_row;
     r.right_row = cand.right_row;
     for (int j = 0; j < r.n_left_cols; j++) r.left_cols[j] = cand.left_cols[j];
     for (int j = 0; j < r.n_right_cols; j++) r.right_cols[j] = cand.right_cols[nkeys + j];
-    give_back(cand.key);
-    for (int a = 0; a < nkeys; a++) give_back(cand.right_cols[a]);
+    if (cand.key) ws.release_caller(cand.key);
+    for (int a = 0; a < nkeys; a++)
+      if (cand.right_cols[a]) ws.release_caller(cand.right_cols[a]);
     *out = r;
     return MDJ_OK;
   }

@@ -306,3 +306,39 @@ def test_merge_how_one_call():
     torch.cuda.synchronize()
     want = oracle.merge_table_how(left, right, "outer")
     assert_same_result(gpu_result_np(res), want)
+
+
+# ------------------------------------------------ edge cases of the stream
+
+@pytest.mark.parametrize("how", ["inner", "outer"])
+def test_stream_all_keys_equal(how):
+    # one key on both sides: one group of 5000 build rows (the global-memory
+    # path) against 3000 probe rows, 15M rows in windows
+    rng = np.random.default_rng(81)
+    lk = np.full(5000, 42, np.int64)
+    rk = np.full(3000, 42, np.int64)
+    assert _check([lk, rng.random(5000)], [rk, rng.random(3000)], 8, window=4_000_000, how=how) == 15_000_000
+
+
+def test_stream_extreme_keys_and_nan_payloads():
+    rng = np.random.default_rng(82)
+    ext = np.array([np.iinfo(np.int64).min, np.iinfo(np.int64).max, -1, 0], np.int64)
+    lk = np.concatenate([ext, rng.integers(-5, 5, 2000)]).astype(np.int64)
+    rk = np.concatenate([ext[::-1], ext, rng.integers(-5, 5, 3000)]).astype(np.int64)
+    nan_bits = np.array([0x7FF8000000000001, 0xFFF0000000000001, 0x7FF4000000000000], np.uint64)
+    lp = rng.random(lk.size)
+    rp = rng.random(rk.size)
+    lp.view(np.uint64)[:3] = nan_bits
+    rp.view(np.uint64)[-3:] = nan_bits
+    for how in ("inner", "left", "right", "outer"):
+        _check([lk, lp], [rk, rp], 8, window=50_000, how=how)
+
+
+@pytest.mark.parametrize("nl,nr,P", [(1, 1, 1), (1, 1, 64), (3, 2, 1024), (2, 5, 2048)])
+def test_stream_tiny_tables_and_more_partitions_than_rows(nl, nr, P):
+    lk = np.arange(nl, dtype=np.int64) % 2
+    rk = np.arange(nr, dtype=np.int64) % 2
+    left = [lk, np.arange(nl, dtype=np.float64)]
+    right = [rk, np.arange(nr, dtype=np.float64)]
+    for how in ("inner", "outer"):
+        _check(left, right, P, window=1, how=how)
