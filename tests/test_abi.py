@@ -186,3 +186,20 @@ def test_merge_multi_argument_checks_need_no_gpu(lib):
     fcols[1].dtype = 1
     ft = MdjTable(fcols, 2, 0)
     assert lib.mdj_merge_multi(ctypes.byref(ft), k2, ctypes.byref(ft), k2, 2, 8, None, None, ctypes.byref(res)) == -2
+
+
+def test_binding_rejects_bad_arguments_before_device_work(lib):
+    import torch
+    from paper_2101_08878_gb300 import mdj
+    k = torch.arange(10, dtype=torch.int64)
+    p = torch.zeros(10, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        mdj.MergeStream([k, p], [k, p], 8, how="sideways")
+    with pytest.raises(ValueError):
+        mdj.merge_host_chunked([k, p], [k, p], 8, 1 << 30, how="sideways")
+    with pytest.raises(ValueError):
+        mdj.transpose_add(torch.zeros((4, 4), dtype=torch.float64))   # not a CUDA tensor
+    with pytest.raises(ValueError):
+        mdj.mdj_merge_multi([k, p], [k, p], [0], [0], 8)              # not CUDA tensors
+    assert mdj.HOW == {"inner": 0, "left": 1, "right": 2, "outer": 3}
+    assert mdj.NO_ROW == 0xFFFFFFFF
