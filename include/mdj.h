@@ -274,7 +274,9 @@ MDJ_API int mdj_merge_batch(const mdj_table *left, int32_t left_key, const uint6
  * Skew is handled on either side with no special input: a key may have any
  * number of rows on either side.  The handle holds on the device the shuffled
  * right table (key, columns, uint32 row id), the grouped left row ids and
- * columns, and 16 bytes per matching right row, until mdj_stream_close.
+ * columns (and keys, for MDJ_LEFT / MDJ_OUTER), and 16 bytes per right row
+ * plus, for MDJ_LEFT / MDJ_OUTER, 16 bytes per left row, until
+ * mdj_stream_close.
  * The input tables must stay valid and unchanged until mdj_stream_close (with
  * P = 1 and a small left table the right table is read in place).  The
  * allocator struct is copied; its callbacks and ctx must stay valid until
