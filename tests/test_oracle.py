@@ -51,6 +51,96 @@ def test_fmix64_avalanche():
     assert worst < 0.06, worst
 
 
+_M64 = (1 << 64) - 1
+
+
+def _rotl64(x, r):
+    return ((x << r) | (x >> (64 - r))) & _M64
+
+
+def _murmur3_x64_128(data: bytes, seed: int, fin) -> bytes:
+    """MurmurHash3_x64_128 (Appleby's published algorithm, restated here):
+    16-byte blocks mixed into two 64-bit lanes, the tail, the length, and
+    `fin` (the 64-bit finalizer) applied to both lanes."""
+    c1, c2 = 0x87C37B91114253D5, 0x4CF5AD432745937F
+    h1 = h2 = seed & 0xFFFFFFFF
+    n = len(data)
+    nblocks = n // 16
+    for i in range(nblocks):
+        k1 = int.from_bytes(data[16 * i:16 * i + 8], "little")
+        k2 = int.from_bytes(data[16 * i + 8:16 * i + 16], "little")
+        k1 = _rotl64((k1 * c1) & _M64, 31) * c2 & _M64
+        h1 ^= k1
+        h1 = (_rotl64(h1, 27) + h2) & _M64
+        h1 = (h1 * 5 + 0x52DCE729) & _M64
+        k2 = _rotl64((k2 * c2) & _M64, 33) * c1 & _M64
+        h2 ^= k2
+        h2 = (_rotl64(h2, 31) + h1) & _M64
+        h2 = (h2 * 5 + 0x38495AB5) & _M64
+    tail = data[16 * nblocks:]
+    if len(tail) > 8:
+        k2 = int.from_bytes(tail[8:], "little")
+        h2 ^= _rotl64((k2 * c2) & _M64, 33) * c1 & _M64
+    if tail:
+        k1 = int.from_bytes(tail[:8], "little")
+        h1 ^= _rotl64((k1 * c1) & _M64, 31) * c2 & _M64
+    h1 ^= n
+    h2 ^= n
+    h1 = (h1 + h2) & _M64
+    h2 = (h2 + h1) & _M64
+    h1, h2 = fin(h1), fin(h2)
+    h1 = (h1 + h2) & _M64
+    h2 = (h2 + h1) & _M64
+    return h1.to_bytes(8, "little") + h2.to_bytes(8, "little")
+
+
+def _smhasher_verification(fin) -> int:
+    # SMHasher's verification value: hash the keys {}, {0}, {0,1}, ...,
+    # {0..254} with seed 256 - length, hash the 256 concatenated results with
+    # seed 0, and read the first four bytes as a little-endian integer.
+    key = bytes(range(256))
+    hashes = b"".join(_murmur3_x64_128(key[:i], 256 - i, fin) for i in range(256))
+    return int.from_bytes(_murmur3_x64_128(hashes, 0, fin)[:4], "little")
+
+
+def _oracle_fin(h: int) -> int:
+    return int(oracle.fmix64(np.array([h], dtype=np.uint64))[0])
+
+
+def test_fmix64_is_murmur3_finalizer_known_answer():
+    # SMHasher publishes 0x6384BA69 as the verification value of
+    # MurmurHash3_x64_128, whose finalizer is fmix64.  With the oracle's
+    # fmix64 as the finalizer the whole hash must reproduce it; this pins the
+    # exact multipliers and shifts, which the partition rule rests on.
+    assert _smhasher_verification(_oracle_fin) == 0x6384BA69
+
+
+def _fmix_variant(m1, m2, s1, s2, s3):
+    def fin(h):
+        h ^= h >> s1
+        h = (h * m1) & _M64
+        h ^= h >> s2
+        h = (h * m2) & _M64
+        h ^= h >> s3
+        return h
+    return fin
+
+
+@pytest.mark.parametrize("variant", [
+    (0xC4CEB9FE1A85EC53, 0xFF51AFD7ED558CCD, 33, 33, 33),   # multipliers swapped
+    (0xFF51AFD7ED558CCD, 0xC4CEB9FE1A85EC53, 31, 33, 33),   # first shift 31
+    (0xFF51AFD7ED558CCD, 0xC4CEB9FE1A85EC53, 33, 33, 32),   # last shift 32
+    (0xFF51AFD7ED558CCD, 0xC4CEB9FE1A85EC55, 33, 33, 33),   # one multiplier bit off
+])
+def test_known_answer_rejects_plausible_finalizer_mistakes(variant):
+    # The same known answer fails for finalizers with one plausible mistake
+    # (these pass the zero, bijection and avalanche tests above).
+    assert _smhasher_verification(_fmix_variant(*variant)) != 0x6384BA69
+    x = np.random.default_rng(5).integers(0, 2**64 - 1, 300, dtype=np.uint64, endpoint=True)
+    mutated = np.array([_fmix_variant(*variant)(int(v)) for v in x], dtype=np.uint64)
+    assert not np.array_equal(oracle.fmix64(x), mutated)
+
+
 def test_partition_ids_sign_extend_int32():
     # int32 and int64 columns holding equal values must hash to equal partitions.
     v = np.array([-5, -1, 0, 1, 7, 2**31 - 1, -(2**31)], dtype=np.int64)
