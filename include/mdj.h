@@ -155,7 +155,8 @@ MDJ_API int mdj_partition(const mdj_table *in, int32_t key_col, uint32_t P,
  *   out_offsets), without the allocator.
  *   Limits: 1 <= P <= 1024, and the working set must fit the 16 MiB array:
  *   P * T + ceil(P * T / 4096) + P + 1 <= 4194304 words, T = ceil(nrows / 4096)
- *   (e.g. up to 16.7M rows at P = 1024, any nrows < 2^32 at P = 8).  Larger
+ *   (e.g. up to 16,764,928 rows at P = 1024, 2,146,951,168 rows at P = 8, and
+ *   any nrows < 2^32 at P <= 2).  Larger
  *   inputs return MDJ_ERR_TOO_LARGE before any work; P > 1024 returns
  *   MDJ_ERR_INVALID_ARG.
  *   The array (16 MiB of device memory) is held on every GPU that loads the
@@ -171,8 +172,8 @@ MDJ_API int mdj_partition_noalloc(const mdj_table *in, int32_t key_col, uint32_t
                                   int64_t *out_offsets, void *stream);
 
 /*
- * mdj_join - the per-partition merge (Sec. V-B: "a merge operation is carried
- * out" on the co-located partitions).  Inner equi-join of `left` (build side)
+ * mdj_join - the per-partition merge of the co-located partitions (the cuDF
+ * merge step of Sec. V-B, after the shuffle).  Inner equi-join of `left` (build side)
  * and `right` (probe side) on left column `left_key` = right column
  * `right_key`, with no shuffle.  Internally the rows are bucketed by hash so
  * every hash table lives in one SM's shared memory; a count pass sizes the
@@ -358,7 +359,9 @@ MDJ_API int mdj_merge_multi(const mdj_table *left, const int32_t *left_keys, con
  *      partitioned into B buckets (bucket = h mod B, as mdj_partition) and the
  *      buckets return to host memory with the rows' input row ids;
  *   2. for each bucket b, both tables' bucket b go to the device, their merge
- *      is opened as a stream (mdj_stream_open with P and `how`), and its rows
+ *      is opened as a stream (mdj_stream_open with P and `how`; with one
+ *      partition when P is a power of two no larger than B, since every row
+ *      of the bucket would then share one partition), and its rows
  *      are written window by window; each window's row ids are mapped back to
  *      the input tables and the window is handed to `sink`.
  *   left, right   : tables whose column pointers are HOST pointers (pageable

@@ -196,6 +196,12 @@ int merge_host_impl(const mdj_table *left, int32_t lk, const mdj_table *right, i
   }
 
   const bool keep_left = how == MDJ_LEFT || how == MDJ_OUTER, keep_right = how == MDJ_RIGHT || how == MDJ_OUTER;
+  // Every row of bucket b has h mod B = b.  For a power-of-two P <= B that
+  // fixes h mod P = b mod P too, so all of a bucket's rows would fall in one of
+  // its P partitions; such buckets are merged with one partition instead (the
+  // merge's own sub-buckets come from the high hash bits, so the work still
+  // spreads over the device).  The joined rows do not depend on P.
+  const uint32_t Pb = ((P & (P - 1)) == 0 && (uint64_t)P <= B) ? 1u : P;
   uint64_t produced = 0;
   for (uint32_t b = 0; b < B; b++) {
     const uint64_t nl = hl.rid[b].size(), nr = hr.rid[b].size();
@@ -208,7 +214,7 @@ int merge_host_impl(const mdj_table *left, int32_t lk, const mdj_table *right, i
     MDJ_TRY(bucket_to_device(ws, right, hr, b, rc, &rt, &rrid));
     mdj_stream *h = nullptr;
     uint64_t m = 0;
-    MDJ_TRY(mdj_stream_open(&lt, lk, &rt, rk, P, how, alloc, stream, &h, &m));
+    MDJ_TRY(mdj_stream_open(&lt, lk, &rt, rk, Pb, how, alloc, stream, &h, &m));
     int rc2 = MDJ_OK;
     for (uint64_t q0 = 0; q0 < m && rc2 == MDJ_OK; q0 += window) {
       const uint64_t n = std::min(window, m - q0);

@@ -11,6 +11,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "mdj.h"
@@ -108,6 +109,15 @@ __device__ __forceinline__ BucketSpec make_spec_dev(uint32_t P) {
 
 // ------------------------------------------------------------ primitives
 
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Device time in nanoseconds (bounds every device-side wait).
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -202,10 +212,6 @@ class Workspace {
   void release_all();
   cudaStream_t stream() const { return stream_; }
   const mdj_allocator *allocator() const { return alloc_; }
-  // A zeroed device int owned by this workspace (kernels set it to report a
-  // bounded wait that ran out); NULL if it cannot be allocated.
-  int *flag_word();
-  int *flag_word_if_any() const { return flag_; }
 
  private:
   void *raw_alloc(size_t bytes);
@@ -213,7 +219,6 @@ class Workspace {
   const mdj_allocator *alloc_;
   cudaStream_t stream_;
   std::vector<void *> owned_;
-  int *flag_ = nullptr;
   unsigned char *arena_ = nullptr;  // current chunk
   size_t arena_used_ = 0;
   static constexpr size_t kArenaMax = 1u << 20;
@@ -231,6 +236,28 @@ struct TraceScope {
 
 int num_sms();
 int cuda_status(cudaError_t e);  // MDJ_OK or MDJ_ERR_CUDA (and records the text)
+
+// Set-up that must run once on every device that uses it, with that device
+// current (for example cudaFuncSetAttribute, which applies to the current
+// device only).  Thread-safe: concurrent first calls on one device run `fn`
+// once; a failed `fn` is retried by the next call.
+constexpr int kMaxDevicesOnce = 64;
+struct PerDeviceOnce {
+  std::mutex mu;
+  bool done[kMaxDevicesOnce] = {};
+};
+template <typename Fn>
+int once_per_device(PerDeviceOnce &once, Fn &&fn) {
+  int dev = 0;
+  const cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (dev < 0 || dev >= kMaxDevicesOnce) return MDJ_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(once.mu);
+  if (once.done[dev]) return MDJ_OK;
+  const int rc = fn();
+  if (rc == MDJ_OK) once.done[dev] = true;
+  return rc;
+}
 
 // ------------------------------------------------------------- side buffers
 
@@ -270,20 +297,6 @@ Plan make_plan(uint64_t n_build, uint32_t P, uint32_t cap, bool force_partition)
 // freshly allocated workspace buffers; fills `out` (offsets per final bucket).
 int partition_side(Workspace &ws, const mdj_table *t, int32_t key_col, const Plan &plan,
                    Side *out);
-
-// Two-level merge plans (F2 > 1, unstable passes) in two halves, for the
-// fused pass-2 + join path: pass 1 leaves `p1` (rows grouped by pass-1
-// bucket, off = final sub-bucket offsets: pass-1 bucket b holds sub-buckets
-// [b * F2, (b + 1) * F2)); pass 2 produces the final side from it.
-struct Side1 {
-  Side p1;                              // pass-1 copy: key, non-key columns, row ids, final offsets
-  const void *all_cols[MDJ_MAX_COLS];   // the same columns in table order
-  void *block;                          // the pass-1 allocation
-};
-bool merge_shuffle_unstable();  // false under MDJ_STABLE_SHUFFLE=1
-int partition_side_pass1(Workspace &ws, const mdj_table *t, int32_t key_col, const Plan &plan, Side1 *out);
-int partition_side_pass2(Workspace &ws, const mdj_table *t, int32_t key_col, const Plan &plan, const Side1 &in,
-                         Side *out);
 
 // Segmented partition of a batch: segment i = rows [seg_off[i], seg_off[i+1])
 // (host array) is split into seg_nb[i] = P_i * S_i buckets numbered from

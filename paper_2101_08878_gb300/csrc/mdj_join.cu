@@ -28,7 +28,6 @@
 #include "mdj_internal.cuh"
 #include "mdj_join_dev.cuh"
 #include "mdj_shuffle_dev.cuh"
-#include "mdj_tma.cuh"
 
 namespace mdj {
 namespace {
@@ -344,11 +343,8 @@ int make_items(Workspace &ws, const Side &Ls, const Side &Rs, uint32_t nb, uint3
   MDJ_LAUNCH_CHECK();
   MDJ_TRY(exclusive_scan_u64(ws, item_off, item_off, nb + 1));
   uint64_t nitems = 0;
-  int part_flag = 0;
   MDJ_CUDA_TRY(cudaMemcpyAsync(&nitems, item_off + nb, 8, cudaMemcpyDeviceToHost, s));
-  if (ws.flag_word_if_any()) MDJ_CUDA_TRY(cudaMemcpyAsync(&part_flag, ws.flag_word_if_any(), 4, cudaMemcpyDeviceToHost, s));
   MDJ_CUDA_TRY(cudaStreamSynchronize(s));
-  if (part_flag) return MDJ_ERR_DEVICE_TIMEOUT;  // a partition pass gave up on a copy wait
   if (nitems >= (1ull << 31)) return MDJ_ERR_TOO_LARGE;
   *nitems_out = (uint32_t)nitems;
   *desc = (Item *)ws.get((size_t)(nitems ? nitems : 1) * sizeof(Item));
@@ -541,446 +537,6 @@ int run_join(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, md
   return MDJ_OK;
 }
 
-// ------------------------------------------------- fused pass 2 + join
-//
-// For a two-level plan the pass-2 copy of every side is written once and read
-// once by the join.  k_fused keeps it in L2 instead: pass-1 bucket w (a
-// "wave") is split by pass 2 into scratch slot w % kFuseSlots, and its join
-// items read the slot right after.  One persistent kernel runs both kinds of
-// work units, taken in a fixed order from one ticket:
-//   P2(0), P2(1), ..., P2(lag - 1), then P2(w), J(w - lag) for w = lag.. ,
-// where P2(w) = the pass-2 tiles of wave w (left side, then right side) and
-// J(w) = the join items of wave w.  J(w) waits until every P2(w) tile is done;
-// P2(w) waits until every J(w - kFuseSlots) item is done (its slot is free).
-// Each wait is on units with smaller tickets, all held by running blocks, so
-// the order cannot deadlock; every wait is still bounded (kFuseWaitNs of
-// %globaltimer time, then FLAG_TIMEOUT + FLAG_ABORT and the block stops).
-// Join units read the slot through L2 only (join_item's COHERENT mode).
-
-constexpr uint32_t kFuseSlots = 4;
-constexpr uint32_t kFuseLag = 2;
-constexpr uint64_t kFuseWaitNs = 2000000000ull;
-constexpr uint32_t kFuseTile = shuffle_tile<kShuffleNT>();
-static_assert(kFuseLag < kFuseSlots, "a wave's slot is reused only after its items ran");
-
-struct FuseWave {
-  uint32_t row0[2], rows[2];  // the wave's rows on each side (pass-1 order = final region)
-  uint32_t tiles[2];          // pass-2 tiles per side
-  uint32_t item0, nitems;     // its join items
-};
-
-// Scratch columns of one side in one slot: key, first payload, row ids.
-struct FuseSideSlot {
-  size_t key, pay, rid;  // byte offsets in the side's part of a slot
-  size_t bytes;          // the side's part of a slot
-};
-
-struct FuseArgs {
-  const ColMove *moves;   // [slot][side]: pass-1 copy -> the slot's scratch columns
-  const JSide *jsides;    // [slot][side]: the slot's scratch columns as join sides
-  const FuseWave *waves;
-  const uint32_t *seg_start;  // first unit of each segment (2 * (F1 + lag) + 1 entries)
-  uint32_t nseg, F1, F2;
-  const Item *desc;
-  uint32_t *ticket;
-  uint32_t *p2_done, *j_done;  // per wave
-  uint32_t *cursors[2];        // absolute sub-bucket cursors per side
-  const void *p1_key[2], *p1_pay[2];
-  const uint32_t *p1_rid[2];
-  int key_w, pay_w[2];         // widths (pay_w 0: no payload column)
-  unsigned char *slots;
-  size_t slot_bytes;
-  FuseSideSlot side[2];
-  BucketSpec sub;
-  uint32_t cap;
-};
-
-// Thread 0 waits until *ctr >= target; false when the wait ran out or another
-// block gave up.
-__device__ bool fuse_wait(const uint32_t *ctr, uint32_t target, int *flags) {
-  volatile const uint32_t *v = ctr;
-  if (*v >= target) {
-    __threadfence();
-    return true;
-  }
-  const uint64_t t0 = globaltimer_ns();
-  while (*v < target) {
-    if (((volatile int *)flags)[FLAG_ABORT]) return false;
-    if (globaltimer_ns() - t0 > kFuseWaitNs) {
-      atomicExch(&flags[FLAG_TIMEOUT], 1);
-      atomicExch(&flags[FLAG_ABORT], 1);
-      return false;
-    }
-    __nanosleep(200);
-  }
-  __threadfence();
-  return true;
-}
-
-// The waves, the unit order (segment starts) and the largest wave per side
-// (out[0], out[1]) and the unit count (out[2]); one block of 1024 threads.
-__global__ void __launch_bounds__(1024)
-    k_fuse_plan(const uint32_t *__restrict__ offL, const uint32_t *__restrict__ offR,
-                const uint64_t *__restrict__ bucket_items, uint32_t F1, uint32_t F2, FuseWave *__restrict__ waves,
-                uint32_t *__restrict__ seg_start, uint32_t *__restrict__ out) {
-  __shared__ uint32_t scratch[40];
-  __shared__ uint32_t mx[2];
-  if (threadIdx.x < 2) mx[threadIdx.x] = 0;
-  __syncthreads();
-  for (uint32_t w = threadIdx.x; w < F1; w += blockDim.x) {
-    FuseWave v;
-    const uint32_t a = w * F2, b = (w + 1) * F2;
-    v.row0[0] = offL[a];
-    v.rows[0] = offL[b] - offL[a];
-    v.row0[1] = offR[a];
-    v.rows[1] = offR[b] - offR[a];
-    v.tiles[0] = (v.rows[0] + kFuseTile - 1) / kFuseTile;
-    v.tiles[1] = (v.rows[1] + kFuseTile - 1) / kFuseTile;
-    v.item0 = (uint32_t)bucket_items[a];
-    v.nitems = (uint32_t)(bucket_items[b] - bucket_items[a]);
-    waves[w] = v;
-    atomicMax(&mx[0], v.rows[0]);
-    atomicMax(&mx[1], v.rows[1]);
-  }
-  __syncthreads();
-  // segment sizes in unit order, then an in-place exclusive scan
-  const uint32_t nseg = 2 * (F1 + kFuseLag);
-  for (uint32_t s = threadIdx.x; s <= nseg; s += blockDim.x) {
-    const uint32_t q = s / 2;
-    uint32_t size = 0;
-    if (s == nseg) {
-      size = 0;
-    } else if (s % 2 == 0) {
-      if (q < F1) size = waves[q].tiles[0] + waves[q].tiles[1];
-    } else if (q >= kFuseLag && q - kFuseLag < F1) {
-      size = waves[q - kFuseLag].nitems;
-    }
-    seg_start[s] = size;
-  }
-  __syncthreads();
-  block_scan_array(seg_start, nseg + 1, scratch);  // seg_start[nseg] = units (its input was 0)
-  if (threadIdx.x == 0) {
-    out[0] = mx[0];
-    out[1] = mx[1];
-    out[2] = seg_start[nseg];
-  }
-}
-
-// Segment of unit u (the last s with seg_start[s] <= u) and u's index in it.
-__device__ __forceinline__ void fuse_decode(const FuseArgs &a, uint32_t u, uint32_t *seg, uint32_t *local) {
-  uint32_t lo = 0, hi = a.nseg - 1;
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi + 1) / 2;
-    if (a.seg_start[mid] <= u)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  *seg = lo;
-  *local = u - a.seg_start[lo];
-}
-
-// The counter a unit of segment `seg` waits for and its target (ctr = NULL:
-// no wait): items of wave w wait for its pass-2 tiles, pass-2 tiles of wave
-// w >= kFuseSlots for the items of wave w - kFuseSlots.
-__device__ __forceinline__ const uint32_t *fuse_dep(const FuseArgs &a, uint32_t seg, uint32_t *target) {
-  const uint32_t q = seg / 2;
-  if (seg % 2 == 0) {
-    if (q < kFuseSlots) return nullptr;
-    *target = a.waves[q - kFuseSlots].nitems;
-    return &a.j_done[q - kFuseSlots];
-  }
-  const FuseWave &wv = a.waves[q - kFuseLag];
-  *target = wv.tiles[0] + wv.tiles[1];
-  return &a.p2_done[q - kFuseLag];
-}
-
-// Thread 0: the unit's dependency already met (one read, no waiting)?
-__device__ __forceinline__ int fuse_ready_now(const FuseArgs &a, uint32_t seg) {
-  uint32_t target = 0;
-  const uint32_t *ctr = fuse_dep(a, seg, &target);
-  if (!ctr) return 1;
-  if (*(volatile const uint32_t *)ctr < target) return 0;
-  __threadfence();
-  return 1;
-}
-
-template <typename KeyT>
-__global__ void __launch_bounds__(kShuffleNT, 2)
-    k_fused(FuseArgs a, Resv rs, JOut out) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ JoinShared js;
-  __shared__ uint32_t s_unit, s_seg, s_local;
-  __shared__ int s_ready, s_ok;
-  const uint32_t tid = threadIdx.x;
-  const uint32_t nunits = a.seg_start[a.nseg];
-  // the block's first unit; every later one is fetched while the previous
-  // unit runs, and decoded and checked while the block finishes it
-  if (tid == 0) {
-    s_unit = atomicAdd(a.ticket, 1u);
-    if (s_unit < nunits) {
-      fuse_decode(a, s_unit, &s_seg, &s_local);
-      s_ready = fuse_ready_now(a, s_seg);
-    }
-  }
-  __syncthreads();
-  for (;;) {
-    const uint32_t u = s_unit;
-    if (u >= nunits) break;
-    const uint32_t seg = s_seg, local = s_local;
-    const int ready = s_ready;
-    uint32_t nx = 0;
-    if (tid == 0) nx = atomicAdd(a.ticket, 1u);
-    if (!ready) {  // s_ready was read by every thread above; the wait reports in s_ok
-      if (tid == 0) {
-        uint32_t target = 0;
-        const uint32_t *ctr = fuse_dep(a, seg, &target);
-        s_ok = fuse_wait(ctr, target, rs.flags);
-      }
-      __syncthreads();
-      if (!s_ok) break;
-    }
-    const uint32_t q = seg / 2;
-    uint32_t w;
-    if (seg % 2 == 0) {
-      // ---- a pass-2 tile of wave q
-      w = q;
-      const FuseWave wv = a.waves[w];
-      const int side = local < wv.tiles[0] ? 0 : 1;
-      const uint32_t k = side ? local - wv.tiles[0] : local;
-      const uint32_t row0 = wv.row0[side] + k * kFuseTile;
-      const uint32_t rend = min(row0 + kFuseTile, wv.row0[side] + wv.rows[side]);
-      const ColMove &cm = a.moves[(w % kFuseSlots) * 2 + side];
-      const int reg_col = a.pay_w[side] ? 1 : -1;
-      KeyT kv[kRPL];
-      uint64_t pv[kRPL];
-      uint32_t rv[kRPL];
-      KeyT kf, kl;
-      const KeyT *keys = (const KeyT *)a.p1_key[side];
-      shuffle_load<KeyT, true>(keys, row0, rend, cm, reg_col, a.pay_w[side], a.p1_rid[side], kv, pv, rv, kf, kl);
-      shuffle_clear_counters<kShuffleNT>(smem);  // the shared memory held a join item before
-      __syncthreads();
-      shuffle_one_tile<kShuffleNT, KeyT, true, false>(smem, keys, row0, rend, w * a.F2, a.F2, a.sub,
-                                                      a.cursors[side], wv.row0[side], cm, reg_col, a.pay_w[side],
-                                                      a.p1_rid[side], (uint32_t *)cm.dst[2], kv, pv, rv, 0u, 0u, kf,
-                                                      kl, 0);
-    } else {
-      // ---- a join item of wave q - lag
-      w = q - kFuseLag;
-      const FuseWave wv = a.waves[w];
-      const uint32_t it = wv.item0 + local;
-      Item d = a.desc[it];
-      d.lbeg -= wv.row0[0];
-      d.rbeg -= wv.row0[1];
-      const JSide *jside = a.jsides + (w % kFuseSlots) * 2;
-      join_item<KeyT, false, true>(smem, a.cap, jside[0], jside[1], d, it, rs, out, js);
-    }
-    uint32_t nseg = 0, nlocal = 0;
-    int nready = 0;
-    if (tid == 0 && nx < nunits) {
-      fuse_decode(a, nx, &nseg, &nlocal);
-      nready = fuse_ready_now(a, nseg);
-    }
-    __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      atomicAdd(seg % 2 == 0 ? &a.p2_done[w] : &a.j_done[w], 1u);
-      s_unit = nx;
-      s_seg = nseg;
-      s_local = nlocal;
-      s_ready = nready;
-    }
-    __syncthreads();
-  }
-}
-
-// Resident blocks of k_fused (grid), and its dynamic shared memory.
-template <typename KeyT>
-int fused_launch_shape(uint32_t cap, size_t *smem, int *grid) {
-  const size_t a = shuffle_smem_bytes<kShuffleNT>(), b = WriteLayout<KeyT>(cap).total;
-  *smem = a > b ? a : b;
-  int per_sm = 0;
-  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_fused<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem));
-  MDJ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<KeyT>, kShuffleNT, *smem));
-  if (per_sm < 1) return MDJ_ERR_INTERNAL;
-  *grid = num_sms() * per_sm;
-  return MDJ_OK;
-}
-
-// MDJ_FUSED=1 turns the fused pass-2 + join path on.  Measured on GB300 for
-// the 100M x 100M merge it is slower than pass 2 + k_join_write (5.1-5.7 vs
-// 3.3 ms): join units wait on pass-2 tiles still in flight, and the slot
-// ring (4 x 16 MB) does not stay in L2 beside the streaming traffic.
-bool fused_enabled() {
-  const char *e = getenv("MDJ_FUSED");
-  return e && e[0] == '1';
-}
-
-constexpr size_t kFuseSlotBudget = 1ull << 30;  // scratch bytes at most (else the unfused path)
-
-// The fused pass 2 + join of a two-level plan from both sides' pass-1 copies.
-// *fallback = true (and no result) when the scratch would exceed its budget
-// or the output outgrew the optimistic buffer: the caller then runs pass 2
-// and the join separately.
-template <typename KeyT>
-int run_fused(Workspace &ws, const Side1 &L1, const Side1 &R1, const Plan &plan, mdj_result *res, bool *fallback) {
-  cudaStream_t s = ws.stream();
-  *fallback = false;
-  const Side &Ls = L1.p1, &Rs = R1.p1;
-  const uint32_t nb = plan.nbuckets, F1 = plan.F1, F2 = plan.F2;
-  const uint64_t cap_rows = output_capacity_hint(Ls.nrows, Rs.nrows);
-  mdj_result r;
-  JOut o;
-  MDJ_TRY(alloc_result(ws, Ls, Rs, sizeof(KeyT), cap_rows, &r, &o));
-  auto fail = [&](int rc) {
-    mdj_result_release(&r, ws.allocator(), (void *)s);
-    return rc;
-  };
-  // items per final sub-bucket, the waves and the unit order
-  uint64_t *bucket_items = (uint64_t *)ws.get((size_t)(nb + 1) * 8);
-  const uint32_t nseg = 2 * (F1 + kFuseLag);
-  FuseWave *waves = (FuseWave *)ws.get((size_t)F1 * sizeof(FuseWave));
-  uint32_t *seg = (uint32_t *)ws.get((size_t)(nseg + 1) * 4);
-  uint32_t *pout = (uint32_t *)ws.get(16);
-  if (!bucket_items || !waves || !seg || !pout) return fail(MDJ_ERR_OOM);
-  {
-    TraceScope tr("join_items", s);
-    k_items<<<(nb + 1 + 255) / 256, 256, 0, s>>>(Ls.off, Rs.off, nb, plan.cap, kWriteChunk, bucket_items);
-  }
-  if (cudaGetLastError() != cudaSuccess) return fail(MDJ_ERR_CUDA);
-  int rc = exclusive_scan_u64(ws, bucket_items, bucket_items, nb + 1);
-  if (rc != MDJ_OK) return fail(rc);
-  {
-    TraceScope tr("fuse_plan", s);
-    k_fuse_plan<<<1, 1024, 0, s>>>(Ls.off, Rs.off, bucket_items, F1, F2, waves, seg, pout);
-  }
-  uint64_t nitems = 0;
-  uint32_t hp[4] = {0, 0, 0, 0};
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&nitems, bucket_items + nb, 8, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(hp, pout, 12, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return fail(cuda_status(e));
-  if (nitems >= (1ull << 31)) return fail(MDJ_ERR_TOO_LARGE);
-
-  FuseArgs a;
-  memset(&a, 0, sizeof a);
-  a.key_w = (int)sizeof(KeyT);
-  const Side *sd[2] = {&Ls, &Rs};
-  const uint32_t maxrows[2] = {hp[0], hp[1]};
-  auto part = [](size_t bytes) { return (bytes + 255) & ~(size_t)255; };
-  for (int i = 0; i < 2; i++) {
-    a.pay_w[i] = sd[i]->ncols ? sd[i]->widths[0] : 0;
-    a.side[i].key = 0;
-    a.side[i].pay = part((size_t)maxrows[i] * sizeof(KeyT));
-    a.side[i].rid = a.side[i].pay + part((size_t)maxrows[i] * (a.pay_w[i] ? a.pay_w[i] : 0));
-    a.side[i].bytes = a.side[i].rid + part((size_t)maxrows[i] * 4);
-    a.p1_key[i] = sd[i]->key;
-    a.p1_pay[i] = sd[i]->ncols ? sd[i]->cols[0] : nullptr;
-    a.p1_rid[i] = sd[i]->rid;
-  }
-  a.slot_bytes = a.side[0].bytes + a.side[1].bytes;
-  if (a.slot_bytes * kFuseSlots > kFuseSlotBudget || nitems == 0) {
-    mdj_result_release(&r, ws.allocator(), (void *)s);
-    *fallback = true;
-    return MDJ_OK;
-  }
-  Item *desc = (Item *)ws.get((size_t)nitems * sizeof(Item));
-  a.slots = (unsigned char *)ws.get(a.slot_bytes * kFuseSlots);
-  // p2_done[F1] | j_done[F1] | ticket | cursors L[nb] | cursors R[nb]
-  const size_t cwords = 2 * (size_t)F1 + 1 + 2 * (size_t)nb;
-  uint32_t *cw = (uint32_t *)ws.get(cwords * 4);
-  // item_off[nitems] | total | flags
-  unsigned long long *st = (unsigned long long *)ws.get(((size_t)nitems + 3) * 8);
-  if (!desc || !a.slots || !cw || !st) return fail(MDJ_ERR_OOM);
-  {
-    TraceScope tr("join_expand", s);
-    const uint64_t want = (nitems + 255) / 256, most = (uint64_t)num_sms() * 8;
-    k_expand<<<(unsigned)(want < most ? want : most), 256, 0, s>>>(Ls.off, Rs.off, nb, plan.cap, kWriteChunk,
-                                                                   bucket_items, (uint32_t)nitems, desc);
-  }
-  e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaMemsetAsync(cw, 0, (2 * (size_t)F1 + 1) * 4, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(cw + 2 * F1 + 1, Ls.off, (size_t)nb * 4, cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(cw + 2 * F1 + 1 + nb, Rs.off, (size_t)nb * 4, cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, ((size_t)nitems + 3) * 8, s);
-  if (e != cudaSuccess) return fail(cuda_status(e));
-  // per (slot, side): the pass-2 column move (key, payload, and the row ids
-  // as dst[2]) and the join side over the slot's scratch columns
-  ColMove hm[kFuseSlots * 2];
-  JSide hj[kFuseSlots * 2];
-  memset(hm, 0, sizeof hm);
-  memset(hj, 0, sizeof hj);
-  for (uint32_t k = 0; k < kFuseSlots; k++)
-    for (int i = 0; i < 2; i++) {
-      unsigned char *base = a.slots + (size_t)k * a.slot_bytes + (i ? a.side[0].bytes : 0);
-      ColMove &m = hm[k * 2 + i];
-      m.n = a.pay_w[i] ? 2 : 1;
-      m.key_index = 0;
-      m.src[0] = a.p1_key[i];
-      m.dst[0] = base + a.side[i].key;
-      m.width[0] = (int)sizeof(KeyT);
-      m.src[1] = a.p1_pay[i];
-      m.dst[1] = base + a.side[i].pay;
-      m.width[1] = a.pay_w[i];
-      m.dst[2] = base + a.side[i].rid;
-      JSide &j = hj[k * 2 + i];
-      j.key = base + a.side[i].key;
-      j.rid = (const uint32_t *)(base + a.side[i].rid);
-      j.cols[0] = base + a.side[i].pay;
-      j.width[0] = a.pay_w[i];
-      j.ncols = a.pay_w[i] ? 1 : 0;
-    }
-  ColMove *dm = (ColMove *)ws.get(sizeof hm);
-  JSide *dj = (JSide *)ws.get(sizeof hj);
-  if (!dm || !dj) return fail(MDJ_ERR_OOM);
-  e = cudaMemcpyAsync(dm, hm, sizeof hm, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dj, hj, sizeof hj, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return fail(cuda_status(e));
-  a.moves = dm;
-  a.jsides = dj;
-  a.waves = waves;
-  a.seg_start = seg;
-  a.nseg = nseg;
-  a.F1 = F1;
-  a.F2 = F2;
-  a.desc = desc;
-  a.p2_done = cw;
-  a.j_done = cw + F1;
-  a.ticket = cw + 2 * F1;
-  a.cursors[0] = cw + 2 * F1 + 1;
-  a.cursors[1] = cw + 2 * F1 + 1 + nb;
-  a.sub = make_spec(plan.P, plan.S, 1);
-  a.cap = plan.cap;
-  unsigned long long *total = st + nitems;
-  int *flags = (int *)(st + nitems + 1);
-  const Resv rs = {nullptr, (uint64_t *)st, total, cap_rows, flags, 0, 0};
-  size_t smem = 0;
-  int grid = 0;
-  rc = fused_launch_shape<KeyT>(plan.cap, &smem, &grid);
-  if (rc != MDJ_OK) return fail(rc);
-  {
-    TraceScope tr("fused_p2_join", s);
-    k_fused<KeyT><<<grid, kShuffleNT, smem, s>>>(a, rs, o);
-  }
-  unsigned long long host_total = 0;
-  int host_flags[FLAG_WORDS] = {0, 0, 0, 0};
-  e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&host_total, total, 8, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(host_flags, flags, sizeof host_flags, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return fail(cuda_status(e));
-  if (host_flags[FLAG_TIMEOUT]) return fail(MDJ_ERR_DEVICE_TIMEOUT);
-  if (host_total > cap_rows) {
-    mdj_result_release(&r, ws.allocator(), (void *)s);
-    *fallback = true;
-    return MDJ_OK;
-  }
-  r.nrows = host_total;
-  *res = r;
-  return MDJ_OK;
-}
-
 // pair_off[i] = output offset of pair i's first item (or of the next pair's,
 // for a pair without items); pair_off[npairs] = total rows.
 __global__ void k_pair_offsets(const uint32_t *__restrict__ seg_base, uint32_t npairs, uint32_t nb,
@@ -1037,21 +593,6 @@ int merge_impl(const mdj_table *left, int32_t lk, const mdj_table *right, int32_
   // ordered output is deterministic only over stable partition passes
   plan.stable = ordered_output() != 0;
   const bool k64 = left->cols[lk].dtype == MDJ_I64;
-  if (!checksum_mode && fused_enabled() && merge_shuffle_unstable() && plan.partition && !plan.lsd &&
-      !plan.stable && plan.F2 > 1 && left->ncols <= 2 && right->ncols <= 2) {
-    // two-level plan: pass 2 and the join fused through L2-resident scratch
-    Side1 L1, R1;
-    MDJ_TRY(partition_side_pass1(ws, left, lk, plan, &L1));
-    MDJ_TRY(partition_side_pass1(ws, right, rk, plan, &R1));
-    bool fallback = false;
-    MDJ_TRY(k64 ? run_fused<int64_t>(ws, L1, R1, plan, out, &fallback)
-                : run_fused<int32_t>(ws, L1, R1, plan, out, &fallback));
-    if (!fallback) return MDJ_OK;
-    Side L, R;
-    MDJ_TRY(partition_side_pass2(ws, left, lk, plan, L1, &L));
-    MDJ_TRY(partition_side_pass2(ws, right, rk, plan, R1, &R));
-    return k64 ? run_join<int64_t>(ws, L, R, plan, out) : run_join<int32_t>(ws, L, R, plan, out);
-  }
   Side L, R;
   MDJ_TRY(partition_side(ws, left, lk, plan, &L));
   MDJ_TRY(partition_side(ws, right, rk, plan, &R));

@@ -6,7 +6,6 @@
 #include <string.h>
 
 #include "mdj_internal.cuh"
-#include "mdj_tma.cuh"
 
 namespace mdj {
 namespace {
@@ -210,27 +209,7 @@ struct Resv {
   int ordered;
 };
 
-// A load through L2 only: the fused kernel reads rows that other blocks wrote
-// during the same launch, which a line left in this SM's L1 by an earlier
-// wave could shadow.
-template <typename T>
-__device__ __forceinline__ T ld_l2(const T *p) {
-  if constexpr (sizeof(T) == 8) {
-    const unsigned long long v = __ldcg((const unsigned long long *)p);
-    T r;
-    memcpy(&r, &v, 8);
-    return r;
-  } else {
-    const unsigned int v = __ldcg((const unsigned int *)p);
-    T r;
-    memcpy(&r, &v, 4);
-    return r;
-  }
-}
-
-// COHERENT: every read of the two sides goes through L2 (ld_l2), and the
-// build chunk is staged by ordinary loads instead of cp.async.
-template <typename KeyT, bool HAVE_OFFSETS, bool COHERENT = false>
+template <typename KeyT, bool HAVE_OFFSETS>
 __device__ __forceinline__ void join_item(unsigned char *smem, uint32_t cap, const JSide &L, const JSide &R,
                                           const Item &d, uint32_t it, const Resv &rs, const JOut &out,
                                           JoinShared &js) {
@@ -248,37 +227,6 @@ __device__ __forceinline__ void join_item(unsigned char *smem, uint32_t cap, con
   const int rpw = R.ncols > 0 ? R.width[0] : 0;
 
     // 1. stage the build chunk; probe keys to registers; clear the heads
-    if (COHERENT) {
-      constexpr int kU = 4;  // rows per thread per round
-      for (uint32_t i0 = 0; i0 < d.nl; i0 += kU * kWT) {
-        KeyT k2[kU];
-        uint32_t r2[kU];
-        uint64_t p2[kU];
-#pragma unroll
-        for (int u = 0; u < kU; u++) {
-          const uint32_t i = i0 + u * kWT + tid;
-          const uint32_t g = d.lbeg + i;
-          k2[u] = KeyT(0);
-          r2[u] = 0;
-          p2[u] = 0;
-          if (i < d.nl) {
-            k2[u] = ld_l2(&Lkey[g]);
-            r2[u] = L.rid ? ld_l2(&L.rid[g]) : g;
-            if (lpw == 8) p2[u] = ld_l2(&((const uint64_t *)L.cols[0])[g]);
-            if (lpw == 4) p2[u] = ld_l2(&((const uint32_t *)L.cols[0])[g]);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < kU; u++) {
-          const uint32_t i = i0 + u * kWT + tid;
-          if (i < d.nl) {
-            bkey[i] = k2[u];
-            brid[i] = r2[u];
-            bpay[i] = p2[u];
-          }
-        }
-      }
-    } else
     for (uint32_t i = tid; i < d.nl; i += kWT) {
       const uint32_t g = d.lbeg + i;
       if (sizeof(KeyT) == 8)
@@ -296,7 +244,7 @@ __device__ __forceinline__ void join_item(unsigned char *smem, uint32_t cap, con
 #pragma unroll
     for (int j = 0; j < kWPF; j++) {
       const uint32_t rl = j * kWT + tid;
-      rk[j] = rl < d.nr ? (COHERENT ? ld_l2(&Rkey[d.rbeg + rl]) : Rkey[d.rbeg + rl]) : KeyT(0);
+      rk[j] = rl < d.nr ? Rkey[d.rbeg + rl] : KeyT(0);
     }
     uint32_t logt = 5;
     while ((1u << logt) < d.nl) logt++;
@@ -345,15 +293,9 @@ __device__ __forceinline__ void join_item(unsigned char *smem, uint32_t cap, con
       rp[j] = 0;
       if (ch[j]) {
         const uint32_t r = d.rbeg + j * kWT + tid;
-        if (COHERENT) {
-          rr[j] = R.rid ? ld_l2(&R.rid[r]) : r;
-          if (rpw == 8) rp[j] = ld_l2(&((const uint64_t *)R.cols[0])[r]);
-          if (rpw == 4) rp[j] = ld_l2(&((const uint32_t *)R.cols[0])[r]);
-        } else {
-          rr[j] = R.rid ? R.rid[r] : r;
-          if (rpw == 8) rp[j] = ((const uint64_t *)R.cols[0])[r];
-          if (rpw == 4) rp[j] = ((const uint32_t *)R.cols[0])[r];
-        }
+        rr[j] = R.rid ? R.rid[r] : r;
+        if (rpw == 8) rp[j] = ((const uint64_t *)R.cols[0])[r];
+        if (rpw == 4) rp[j] = ((const uint32_t *)R.cols[0])[r];
       }
     }
 

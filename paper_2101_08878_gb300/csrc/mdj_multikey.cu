@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include "mdj_internal.cuh"
+#include "mdj_sizes.h"
 
 namespace mdj {
 namespace {
@@ -62,8 +63,9 @@ __global__ void k_verify(const __grid_constant__ KeyCols Lk, const __grid_consta
 }
 
 // Rows with keep[i] move to position pos[i] (exclusive scan of keep).
+template <typename PosT>
 __global__ void k_compact_col(const void *__restrict__ src, void *__restrict__ dst, int width, uint64_t m,
-                              const uint32_t *__restrict__ keep, const uint32_t *__restrict__ pos) {
+                              const uint32_t *__restrict__ keep, const PosT *__restrict__ pos) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
     if (!keep[i]) continue;
@@ -72,6 +74,11 @@ __global__ void k_compact_col(const void *__restrict__ src, void *__restrict__ d
     else
       ((uint32_t *)dst)[pos[i]] = ((const uint32_t *)src)[i];
   }
+}
+
+__global__ void k_flags_u64(const uint32_t *__restrict__ keep, uint64_t m, uint64_t *__restrict__ out) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= m; i += stride) out[i] = i < m ? keep[i] : 0;
 }
 
 int weak_hash_for_tests() {
@@ -202,11 +209,26 @@ int merge_multi_impl(const mdj_table *left, const int32_t *lkeys, const mdj_tabl
     *out = r;
     return MDJ_OK;
   }
-  // drop the colliding rows: positions by a scan of keep, then each column
-  uint32_t *pos = (uint32_t *)ws.get((size_t)(m + 1) * 4);
-  rc2 = pos ? MDJ_OK : MDJ_ERR_OOM;
-  if (rc2 == MDJ_OK) rc2 = cuda_status(cudaMemsetAsync(keep + m, 0, 4, s));
-  if (rc2 == MDJ_OK) rc2 = exclusive_scan_u32(ws, keep, pos, (size_t)m + 1);
+  // drop the colliding rows: positions by a scan of keep (64-bit positions
+  // once m + 1 flags no longer fit a 32-bit total), then each column
+  const bool wide = compaction_needs_u64_positions(m);
+  uint32_t *pos = nullptr;
+  uint64_t *pos64 = nullptr;
+  if (wide) {
+    pos64 = (uint64_t *)ws.get((size_t)(m + 1) * 8);
+    rc2 = pos64 ? MDJ_OK : MDJ_ERR_OOM;
+    if (rc2 == MDJ_OK) {
+      TraceScope tr("tuple_flags_u64", s);
+      k_flags_u64<<<grid_of(m + 1), 256, 0, s>>>(keep, m, pos64);
+      rc2 = cuda_status(cudaGetLastError());
+    }
+    if (rc2 == MDJ_OK) rc2 = exclusive_scan_u64(ws, pos64, pos64, (size_t)m + 1);
+  } else {
+    pos = (uint32_t *)ws.get((size_t)(m + 1) * 4);
+    rc2 = pos ? MDJ_OK : MDJ_ERR_OOM;
+    if (rc2 == MDJ_OK) rc2 = cuda_status(cudaMemsetAsync(keep + m, 0, 4, s));
+    if (rc2 == MDJ_OK) rc2 = exclusive_scan_u32(ws, keep, pos, (size_t)m + 1);
+  }
   const uint64_t kept = m - host_dropped;
   r.nrows = kept;
   auto move = [&](const void *src, int width, void **dst) -> int {
@@ -214,7 +236,10 @@ int merge_multi_impl(const mdj_table *left, const int32_t *lkeys, const mdj_tabl
     if (kept && !*dst) return MDJ_ERR_OOM;
     if (kept) {
       TraceScope tr("tuple_compact", s);
-      k_compact_col<<<grid_of(m), 256, 0, s>>>(src, *dst, width, m, keep, pos);
+      if (wide)
+        k_compact_col<uint64_t><<<grid_of(m), 256, 0, s>>>(src, *dst, width, m, keep, pos64);
+      else
+        k_compact_col<uint32_t><<<grid_of(m), 256, 0, s>>>(src, *dst, width, m, keep, pos);
     }
     return cuda_status(cudaGetLastError());
   };

@@ -20,7 +20,6 @@
 
 #include "mdj_internal.cuh"
 #include "mdj_shuffle_dev.cuh"
-#include "mdj_tma.cuh"
 
 namespace mdj {
 namespace {
@@ -258,251 +257,6 @@ __global__ void __launch_bounds__(kNW * 32, 2)
   }
 }
 
-// ------------------------------------------------------ pipelined scatter
-//
-// Same result as k_scatter, organised so that no thread waits on a global
-// load: persistent 512-thread blocks, two per SM, each walking tiles
-// t = blockIdx.x, +gridDim.x, ... of kPTile rows.  The columns of a block's
-// next tile stream into the other half of a double buffer by bulk copies
-// (TMA, completing on an mbarrier) while the current tile is ranked and
-// written, and the current tile's run bases are loaded before ranking starts.
-// Ranking reads keys from shared memory; the write-out walks the tile in
-// sorted order through a sorted-position -> row permutation and reads each
-// row from the tile buffer, so consecutive threads store consecutive rows of
-// one bucket run.  Used when every loaded column is 16-byte aligned, a row
-// loads at most kPipeRowBytes and a tile has at most kPipeMaxLocal local
-// buckets; other cases use k_scatter.
-
-constexpr int kPT = 512;                        // threads of the pipelined block
-constexpr int kPW = kPT / 32;                   // warps
-constexpr uint32_t kPTile = 2048;               // rows per pipelined tile
-constexpr int kPRL = kPTile / kPT;              // rows per lane (4)
-constexpr uint32_t kPipeRowBytes = 20;          // loaded bytes per row, all columns
-constexpr uint32_t kPipeMaxLocal = 256;         // local buckets per tile
-constexpr uint64_t kPipeWaitNs = 1000000000ull;
-
-struct PipeCols {
-  int32_t n;            // loaded columns (table columns, then row ids if loaded)
-  int32_t key_index;
-  int32_t rid_col;      // index of the row-id column among the loaded, -1: row ids = row numbers
-  const void *src[MDJ_MAX_COLS + 1];
-  void *dst[MDJ_MAX_COLS + 1];
-  int32_t width[MDJ_MAX_COLS + 1];
-  uint32_t off[MDJ_MAX_COLS + 1];  // byte offset of the column's tile slab in a buffer half
-  uint32_t half_bytes;             // bytes of one buffer half
-  uint32_t *rid_out;               // written when rid_col < 0 (row numbers)
-};
-
-// u16 entries per warp row of the rank counters: even, and an odd number of
-// 32-bit words.
-__host__ __device__ __forceinline__ uint32_t pipe_row_stride(uint32_t F) {
-  uint32_t w = (F + 1) / 2;
-  if ((w & 1) == 0) w++;
-  return 2 * w;
-}
-
-struct PipeLayout {
-  size_t buf, inv, sbk, whist, lstart, gbase, scratch, mbar, total;
-  __host__ __device__ PipeLayout(uint32_t half_bytes, uint32_t FL) {
-    buf = 0;
-    inv = 2 * (size_t)half_bytes;
-    sbk = inv + (size_t)kPTile * 2;
-    whist = sbk + (size_t)kPTile * 2;
-    lstart = align16(whist + (size_t)kPW * pipe_row_stride(FL) * 2);
-    gbase = lstart + (size_t)(FL + 1) * 4;
-    scratch = gbase + (size_t)FL * 4;
-    mbar = align16(scratch + 40 * 4);
-    total = mbar + 16;
-  }
-};
-
-template <typename KeyT>
-__device__ __forceinline__ KeyT tile_key(const unsigned char *half, const PipeCols &pc, uint32_t i) {
-  return ((const KeyT *)(half + pc.off[pc.key_index]))[i];
-}
-
-// Thread 0: bulk copies of the 16-byte-aligned part of every loaded column of tile t.
-__device__ void pipe_issue(const PipeCols &pc, uint32_t t, uint32_t n, unsigned char *half, uint64_t *bar) {
-  const uint32_t row0 = t * kPTile;
-  const uint32_t rows = min(kPTile, n - row0);
-  uint32_t total = 0;
-  for (int j = 0; j < pc.n; j++) total += (rows * pc.width[j]) & ~15u;
-  fence_proxy_async_shared();
-  mbar_arrive_expect_tx(bar, total);
-  for (int j = 0; j < pc.n; j++) {
-    const uint32_t bytes = (rows * pc.width[j]) & ~15u;
-    if (bytes) tma_load_1d(half + pc.off[j], (const unsigned char *)pc.src[j] + (size_t)row0 * pc.width[j], bytes, bar);
-  }
-}
-
-template <typename KeyT, bool RESERVE>
-__global__ void __launch_bounds__(kPT, 2)
-    k_scatter_pipe(uint32_t n, BucketSpec bs, uint32_t F, uint32_t ntiles, const uint32_t *__restrict__ tile_base,
-                   uint32_t *__restrict__ cursors, uint32_t F2, uint32_t FL, PipeCols pc, int *flags) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const PipeLayout lay(pc.half_bytes, FL);
-  uint16_t *inv = (uint16_t *)(smem + lay.inv);
-  uint16_t *sbk = (uint16_t *)(smem + lay.sbk);
-  uint16_t *whist = (uint16_t *)(smem + lay.whist);
-  uint32_t *lstart = (uint32_t *)(smem + lay.lstart);
-  uint32_t *gbase = (uint32_t *)(smem + lay.gbase);
-  uint32_t *scratch = (uint32_t *)(smem + lay.scratch);
-  uint64_t *bar = (uint64_t *)(smem + lay.mbar);
-  __shared__ int s_ok;
-
-  const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    if (blockIdx.x < ntiles) pipe_issue(pc, blockIdx.x, n, smem + lay.buf, &bar[0]);
-  }
-  __syncthreads();
-  uint32_t buf = 0, ph0 = 0, ph1 = 0;
-  for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    unsigned char *half = smem + lay.buf + (size_t)buf * pc.half_bytes;
-    const uint32_t row0 = t * kPTile;
-    const uint32_t rows = min(kPTile, n - row0);
-    // run bases of this tile (stable pass): loaded now, used after ranking
-    uint32_t gb = 0;
-    if (!RESERVE && tid < F) gb = tile_base[(size_t)tid * ntiles + t];
-    if (tid == 0) {
-      const uint32_t par = buf ? ph1 : ph0;
-      const bool ok = mbar_wait_bounded(&bar[buf], par, kPipeWaitNs);
-      if (!ok) {
-        mbar_wait_bounded(&bar[buf], par, kPipeWaitNs);  // let the copy land before giving up
-        atomicExch(&flags[0], 1);
-      } else if (t + gridDim.x < ntiles) {
-        pipe_issue(pc, t + gridDim.x, n, smem + lay.buf + (size_t)(buf ^ 1) * pc.half_bytes, &bar[buf ^ 1]);
-      }
-      s_ok = ok;
-    }
-    if (buf) ph1 ^= 1; else ph0 ^= 1;
-    __syncthreads();
-    if (!s_ok) break;
-    // ragged tail of the last tile: the bytes the bulk copies left out
-    if (rows < kPTile) {
-      for (int j = 0; j < pc.n; j++) {
-        const uint32_t w = pc.width[j];
-        const uint32_t first = ((rows * w) & ~15u) / w;
-        for (uint32_t i = first + tid; i < rows; i += kPT) {
-          if (w == 8)
-            ((uint64_t *)(half + pc.off[j]))[i] = ((const uint64_t *)pc.src[j])[row0 + i];
-          else
-            ((uint32_t *)(half + pc.off[j]))[i] = ((const uint32_t *)pc.src[j])[row0 + i];
-        }
-      }
-      __syncthreads();
-    }
-
-    uint32_t Floc = F, lb0 = 0;
-    if (RESERVE) {
-      // every thread derives the tile's pass-1 bucket range from its first and last rows
-      const uint32_t b1f = sub_bucket_of(fmix64(key_bits(tile_key<KeyT>(half, pc, 0))), bs) / F2;
-      const uint32_t b1l = sub_bucket_of(fmix64(key_bits(tile_key<KeyT>(half, pc, rows - 1))), bs) / F2;
-      lb0 = b1f * F2;
-      Floc = (b1l - b1f + 1) * F2;
-      if (Floc > FL) {
-        // rows span too many buckets for the shared counters: reserve per
-        // warp-aggregated group and write each row directly
-        for (uint32_t i = tid; i < ((rows + 31) & ~31u); i += kPT) {
-          const bool valid = i < rows;
-          const uint32_t fb = valid ? sub_bucket_of(fmix64(key_bits(tile_key<KeyT>(half, pc, i))), bs) : 0xFFFFFFFFu;
-          const uint32_t peers = __match_any_sync(0xffffffffu, fb);
-          const int leader = __ffs(peers) - 1;
-          uint32_t base = 0;
-          if (valid && (int)lane == leader) base = atomicAdd(&cursors[fb], (uint32_t)__popc(peers));
-          base = __shfl_sync(0xffffffffu, base, leader);
-          if (valid) {
-            const uint32_t pos = base + __popc(peers & lanemask_lt());
-            for (int j = 0; j < pc.n; j++) {
-              if (pc.width[j] == 8)
-                ((uint64_t *)pc.dst[j])[pos] = ((const uint64_t *)(half + pc.off[j]))[i];
-              else
-                ((uint32_t *)pc.dst[j])[pos] = ((const uint32_t *)(half + pc.off[j]))[i];
-            }
-            if (pc.rid_col < 0 && pc.rid_out) pc.rid_out[pos] = row0 + i;
-          }
-        }
-        fence_proxy_async_shared();
-        __syncthreads();
-        buf ^= 1;
-        continue;
-      }
-    }
-
-    // 1. per-warp stable ranks (warp w owns tile rows [w*32*kPRL, (w+1)*32*kPRL)).
-    //    Row stride Ws (u16) spans an odd number of 32-bit words, so the
-    //    column reads of step 2 (lane w reads row w) fall in distinct banks.
-    const uint32_t Ws = pipe_row_stride(Floc);
-    for (uint32_t i = tid; i < kPW * Ws / 2; i += kPT) ((uint32_t *)whist)[i] = 0;
-    __syncthreads();
-    uint32_t pk[kPRL];
-    uint16_t *wh = whist + warp * Ws;
-#pragma unroll
-    for (int c = 0; c < kPRL; c++) {
-      const uint32_t i = warp * 32 * kPRL + c * 32 + lane;
-      const bool valid = i < rows;
-      const uint32_t b = valid ? bucket_of(fmix64(key_bits(tile_key<KeyT>(half, pc, i))), bs) - lb0 : 0xFFFFFFFFu;
-      const uint32_t peers = __match_any_sync(0xffffffffu, b);
-      const uint32_t rank = __popc(peers & lanemask_lt());
-      const uint32_t old = valid ? wh[b] : 0u;
-      __syncwarp();
-      if (valid && rank == 0) wh[b] = (uint16_t)(old + __popc(peers));
-      __syncwarp();
-      pk[c] = (b << 16) | (old + rank);
-    }
-    __syncthreads();
-    // 2. warp offsets inside each bucket (a shuffle scan across the warps'
-    //    counts, lane w = warp w) and the bucket totals
-    for (uint32_t b = warp; b < Floc; b += kPW) {
-      const uint32_t v = lane < kPW ? whist[lane * Ws + b] : 0u;
-      const uint32_t inc = warp_inclusive_scan<uint32_t>(v);
-      if (lane < kPW) whist[lane * Ws + b] = (uint16_t)(inc - v);
-      if (lane == 31) lstart[b] = inc;
-    }
-    __syncthreads();
-    block_scan_array(lstart, Floc, scratch);
-    // 3. global base of each bucket's run
-    for (uint32_t b = tid; b < Floc; b += kPT) {
-      if (!RESERVE) {
-        gbase[b] = gb;  // tid == b here: F <= kPT
-      } else {
-        const uint32_t e = b + 1 < Floc ? lstart[b + 1] : rows;
-        const uint32_t cnt = e - lstart[b];
-        gbase[b] = cnt ? atomicAdd(&cursors[lb0 + b], cnt) : 0u;
-      }
-    }
-    // 4. sorted position of each row
-#pragma unroll
-    for (int c = 0; c < kPRL; c++) {
-      const uint32_t i = warp * 32 * kPRL + c * 32 + lane;
-      if (i < rows) {
-        const uint32_t b = pk[c] >> 16;
-        const uint32_t p = lstart[b] + whist[warp * Ws + b] + (pk[c] & 0xFFFFu);
-        inv[p] = (uint16_t)i;
-        sbk[p] = (uint16_t)b;
-      }
-    }
-    __syncthreads();
-    // 5. write out in sorted order: runs of one bucket are contiguous
-    for (uint32_t j = tid; j < rows; j += kPT) {
-      const uint32_t i = inv[j], b = sbk[j];
-      const uint32_t dst = gbase[b] + (j - lstart[b]);
-      for (int c = 0; c < pc.n; c++) {
-        if (pc.width[c] == 8)
-          ((uint64_t *)pc.dst[c])[dst] = ((const uint64_t *)(half + pc.off[c]))[i];
-        else
-          ((uint32_t *)pc.dst[c])[dst] = ((const uint32_t *)(half + pc.off[c]))[i];
-      }
-      if (pc.rid_col < 0 && pc.rid_out) pc.rid_out[dst] = row0 + i;
-    }
-    fence_proxy_async_shared();
-    __syncthreads();
-    buf ^= 1;
-  }
-}
-
 // ------------------------------------------------- unstable shuffle (merge)
 //
 // The merge needs every row in its sub-bucket, not the input order inside a
@@ -659,22 +413,6 @@ __global__ void k_u32_to_i64(const uint32_t *__restrict__ a, int64_t *__restrict
 
 // ------------------------------------------------------------- host passes
 
-// The pipelined scatter is opt-in (MDJ_PIPE_SCATTER=1).  Measured on GB300
-// for the 100M x 100M merge, the two-block k_scatter is faster (1.10 vs 1.80
-// ms per stable pass, 1.19 vs 1.55 ms per second-level pass): the tile's
-// serialised phases, not its load latency, bound both kernels.
-bool pipe_disabled() {
-  const char *e = getenv("MDJ_PIPE_SCATTER");
-  return !(e && e[0] == '1');
-}
-
-// Device word that a pipelined scatter sets when a bounded copy wait ran out;
-// one per workspace, zeroed on first use, read back by the merge path.
-int *pipe_flags(Workspace &ws) {
-  int *f = ws.flag_word();
-  return f;
-}
-
 int hist_grid(size_t smem) {
   int per_sm = 1;
   if (smem <= 48 * 1024) per_sm = 4;
@@ -684,78 +422,18 @@ int hist_grid(size_t smem) {
 
 template <typename KeyT>
 int set_smem_attrs() {
-  static bool done = false;
-  if (done) return MDJ_OK;
-  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_scatter<KeyT, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)scatter_smem_bytes(kMaxFanout)));
-  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_scatter<KeyT, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)scatter_smem_bytes(kPass2SpanMax)));
-  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_scatter<KeyT, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)scatter_smem_bytes(kPass2SpanMax)));
-  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_hist<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)((kMaxFanout + kMaxSubBuckets) * 4)));
-  done = true;
-  return MDJ_OK;
-}
-
-// Column set of a pipelined pass, if it qualifies (see k_scatter_pipe).
-bool make_pipe_cols(const ColMove &cm, const uint32_t *rid_in, uint32_t *rid_out, uint32_t FL, PipeCols *out) {
-  if (FL > kPipeMaxLocal || FL == 0 || pipe_disabled()) return false;
-  PipeCols pc;
-  memset(&pc, 0, sizeof pc);
-  uint32_t row_bytes = 0;
-  for (int j = 0; j < cm.n; j++) {
-    pc.src[j] = cm.src[j];
-    pc.dst[j] = cm.dst[j];
-    pc.width[j] = cm.width[j];
-    row_bytes += cm.width[j];
-    if (((uintptr_t)cm.src[j] & 15) != 0) return false;
-  }
-  pc.n = cm.n;
-  pc.key_index = cm.key_index;
-  pc.rid_col = -1;
-  pc.rid_out = rid_out;
-  if (rid_in) {
-    if (!rid_out || ((uintptr_t)rid_in & 15) != 0) return false;
-    pc.src[pc.n] = rid_in;
-    pc.dst[pc.n] = rid_out;
-    pc.width[pc.n] = 4;
-    pc.rid_col = pc.n;
-    pc.n++;
-    row_bytes += 4;
-  }
-  if (row_bytes > kPipeRowBytes) return false;
-  uint32_t off = 0;
-  for (int j = 0; j < pc.n; j++) {
-    pc.off[j] = off;
-    off += kPTile * pc.width[j];
-  }
-  pc.half_bytes = off;
-  *out = pc;
-  return true;
-}
-
-template <typename KeyT, bool RESERVE>
-int launch_pipe(Workspace &ws, uint32_t n, const BucketSpec &bs, uint32_t F, uint32_t ntiles, const uint32_t *tile_base,
-                uint32_t *cursors, uint32_t F2, uint32_t FL, const PipeCols &pc) {
-  static bool attr_done = false;
-  if (!attr_done) {
-    MDJ_CUDA_TRY(cudaFuncSetAttribute(k_scatter_pipe<KeyT, RESERVE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)PipeLayout(kPTile * kPipeRowBytes, kPipeMaxLocal).total));
-    attr_done = true;
-  }
-  int *flags = pipe_flags(ws);
-  if (!flags) return MDJ_ERR_OOM;
-  const uint32_t most = 2u * (uint32_t)num_sms();
-  const uint32_t grid = ntiles < most ? ntiles : most;
-  const size_t smem = PipeLayout(pc.half_bytes, FL).total;
-  {
-    TraceScope tr(RESERVE ? "scatter_reserve" : "scatter_stable", ws.stream());
-    k_scatter_pipe<KeyT, RESERVE><<<grid, kPT, smem, ws.stream()>>>(n, bs, F, ntiles, tile_base, cursors, F2, FL, pc,
-                                                                    flags);
-  }
-  MDJ_LAUNCH_CHECK();
-  return MDJ_OK;
+  static PerDeviceOnce once;
+  return once_per_device(once, [] {
+    MDJ_CUDA_TRY(cudaFuncSetAttribute(k_scatter<KeyT, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)scatter_smem_bytes(kMaxFanout)));
+    MDJ_CUDA_TRY(cudaFuncSetAttribute(k_scatter<KeyT, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)scatter_smem_bytes(kPass2SpanMax)));
+    MDJ_CUDA_TRY(cudaFuncSetAttribute(k_scatter<KeyT, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)scatter_smem_bytes(kPass2SpanMax)));
+    MDJ_CUDA_TRY(cudaFuncSetAttribute(k_hist<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)((kMaxFanout + kMaxSubBuckets) * 4)));
+    return (int)MDJ_OK;
+  });
 }
 
 // One stable scatter pass over n rows into F <= kMaxFanout buckets.  If
@@ -767,9 +445,7 @@ int stable_pass(Workspace &ws, const KeyT *keys, uint32_t n, const BucketSpec &b
                 const uint32_t *rid_in, uint32_t *rid_out, uint32_t *start, uint32_t *total2, uint32_t nsub) {
   cudaStream_t s = ws.stream();
   MDJ_TRY(set_smem_attrs<KeyT>());
-  PipeCols pc;
-  const bool piped = make_pipe_cols(cm, rid_in, rid_out, F, &pc);
-  const uint32_t tile = piped ? kPTile : kTile;
+  const uint32_t tile = kTile;
   const uint32_t ntiles = (n + tile - 1) / tile;
   if (ntiles == 0) {
     if (start) MDJ_CUDA_TRY(cudaMemsetAsync(start, 0, (size_t)(F + 1) * 4, s));
@@ -790,9 +466,7 @@ int stable_pass(Workspace &ws, const KeyT *keys, uint32_t n, const BucketSpec &b
     k_bucket_starts<<<(F + 1 + 255) / 256, 256, 0, s>>>(hist, F, ntiles, n, start);
   }
   MDJ_LAUNCH_CHECK();
-  if (piped) {
-    MDJ_TRY((launch_pipe<KeyT, false>(ws, n, bs, F, ntiles, hist, nullptr, 1, F, pc)));
-  } else {
+  {
     TraceScope tr("scatter_stable", s);
     k_scatter<KeyT, false, false><<<ntiles, kNW * 32, scatter_smem_bytes(F), s>>>(
         keys, n, bs, F, ntiles, hist, nullptr, 1, cm, rid_in, rid_out, nullptr, nullptr, nullptr, nullptr, nullptr);
@@ -809,12 +483,6 @@ int reserve_pass(Workspace &ws, const KeyT *keys, uint32_t n, const BucketSpec &
                  uint32_t *cursors, const ColMove &cm, const uint32_t *rid_in, uint32_t *rid_out) {
   cudaStream_t s = ws.stream();
   MDJ_TRY(set_smem_attrs<KeyT>());
-  PipeCols pc;
-  if (make_pipe_cols(cm, rid_in, rid_out, 2 * F2, &pc)) {
-    const uint32_t ntiles = (n + kPTile - 1) / kPTile;
-    if (ntiles) MDJ_TRY((launch_pipe<KeyT, true>(ws, n, bs_sub, 0, ntiles, nullptr, cursors, F2, 2 * F2, pc)));
-    return MDJ_OK;
-  }
   const uint32_t ntiles = (n + kTile - 1) / kTile;
   if (ntiles == 0) return MDJ_OK;
   {
@@ -876,18 +544,18 @@ bool fast_shuffle_enabled() {
 
 template <typename KeyT>
 int set_shuffle_attrs() {
-  static bool done = false;
-  if (done) return MDJ_OK;
-  constexpr int NT = kShuffleNT;
-  const int sm = (int)shuffle_smem_bytes<NT>();
-  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_shuffle<NT, KeyT, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_shuffle<NT, KeyT, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_shuffle<NT, KeyT, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_shuffle<NT, KeyT, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  MDJ_CUDA_TRY(cudaFuncSetAttribute(k_tot<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(kMaxSubBuckets * 4)));
-  done = true;
-  return MDJ_OK;
+  static PerDeviceOnce once;
+  return once_per_device(once, [] {
+    constexpr int NT = kShuffleNT;
+    const int sm = (int)shuffle_smem_bytes<NT>();
+    MDJ_CUDA_TRY(cudaFuncSetAttribute(k_shuffle<NT, KeyT, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    MDJ_CUDA_TRY(cudaFuncSetAttribute(k_shuffle<NT, KeyT, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    MDJ_CUDA_TRY(cudaFuncSetAttribute(k_shuffle<NT, KeyT, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    MDJ_CUDA_TRY(cudaFuncSetAttribute(k_shuffle<NT, KeyT, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    MDJ_CUDA_TRY(cudaFuncSetAttribute(k_tot<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(kMaxSubBuckets * 4)));
+    return (int)MDJ_OK;
+  });
 }
 
 template <typename KeyT>
@@ -1191,11 +859,7 @@ Plan make_plan(uint64_t n_build, uint32_t P, uint32_t cap, bool force_partition)
     pl.nbuckets = pl.F1;
     return pl;
   }
-  uint32_t fan = kMergeFanout;
-  if (const char *e = getenv("MDJ_MERGE_FANOUT")) {  // pass-1 buckets, for tuning studies
-    const int v = atoi(e);
-    if (v >= 8 && v <= (int)kMaxFanout) fan = (uint32_t)v;
-  }
+  const uint32_t fan = kMergeFanout;
   uint32_t S1 = fan / P;
   if (S1 < 1) S1 = 1;
   uint64_t F2 = (S + S1 - 1) / S1;
@@ -1232,38 +896,6 @@ void fill_side(const mdj_table *t, int32_t key_col, const TableBufs &b, uint32_t
   out->nrows = t->nrows;
 }
 }  // namespace
-
-bool merge_shuffle_unstable() { return fast_shuffle_enabled(); }
-
-int partition_side_pass1(Workspace &ws, const mdj_table *t, int32_t key_col, const Plan &plan, Side1 *out) {
-  if (plan.F2 < 2 || plan.lsd || !plan.partition) return MDJ_ERR_INTERNAL;
-  uint32_t *off = (uint32_t *)ws.get((size_t)(plan.nbuckets + 1) * 4);
-  if (!off) return MDJ_ERR_OOM;
-  TableBufs p1;
-  if (t->cols[key_col].dtype == MDJ_I64)
-    MDJ_TRY(shuffle_count_pass1_t<int64_t>(ws, t, key_col, plan, off, &p1));
-  else
-    MDJ_TRY(shuffle_count_pass1_t<int32_t>(ws, t, key_col, plan, off, &p1));
-  memset(out, 0, sizeof *out);
-  fill_side(t, key_col, p1, off, &out->p1);
-  for (int j = 0; j < t->ncols; j++) out->all_cols[j] = p1.cols[j];
-  out->block = p1.block;
-  return MDJ_OK;
-}
-
-int partition_side_pass2(Workspace &ws, const mdj_table *t, int32_t key_col, const Plan &plan, const Side1 &in,
-                         Side *out) {
-  TableBufs p1, fin;
-  for (int j = 0; j < t->ncols; j++) p1.cols[j] = const_cast<void *>(in.all_cols[j]);
-  p1.rid = (uint32_t *)in.p1.rid;
-  p1.block = in.block;
-  if (t->cols[key_col].dtype == MDJ_I64)
-    MDJ_TRY(shuffle_pass2_t<int64_t>(ws, t, key_col, plan, in.p1.off, p1, &fin));
-  else
-    MDJ_TRY(shuffle_pass2_t<int32_t>(ws, t, key_col, plan, in.p1.off, p1, &fin));
-  fill_side(t, key_col, fin, (uint32_t *)in.p1.off, out);
-  return MDJ_OK;
-}
 
 int stable_partition(Workspace &ws, const mdj_table *t, int32_t key_col, uint32_t P, void *const *out_cols,
                      uint32_t *out_rid, int64_t *out_offsets) {

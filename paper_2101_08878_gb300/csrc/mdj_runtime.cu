@@ -66,18 +66,9 @@ void Workspace::give_back(void *p) {
 void *Workspace::get_owned_by_caller(size_t bytes) { return raw_alloc(bytes); }
 void Workspace::release_caller(void *p) { raw_free(p); }
 
-int *Workspace::flag_word() {
-  if (!flag_) {
-    flag_ = (int *)get(16);
-    if (flag_ && cudaMemsetAsync(flag_, 0, 16, stream_) != cudaSuccess) flag_ = nullptr;
-  }
-  return flag_;
-}
-
 void Workspace::release_all() {
   for (size_t i = owned_.size(); i-- > 0;) raw_free(owned_[i]);
   owned_.clear();
-  flag_ = nullptr;
   arena_ = nullptr;
   arena_used_ = 0;
 }

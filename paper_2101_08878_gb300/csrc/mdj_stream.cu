@@ -1035,7 +1035,7 @@ int group_and_index(Workspace &tmp, mdj_stream *h, const Side &L, const Side &R,
   }
   uint64_t t1 = 0, t2 = 0;
   uint32_t n1 = 0, n2 = 0;
-  int herr[4] = {0, 0, 0, 0}, pflag[2] = {0, 0};
+  int herr[4] = {0, 0, 0, 0};
   MDJ_CUDA_TRY(cudaMemcpyAsync(&t1, crows1 + c1, 8, cudaMemcpyDeviceToHost, s));
   MDJ_CUDA_TRY(cudaMemcpyAsync(&n1, cents1 + c1, 4, cudaMemcpyDeviceToHost, s));
   if (keep_left) {
@@ -1043,11 +1043,7 @@ int group_and_index(Workspace &tmp, mdj_stream *h, const Side &L, const Side &R,
     MDJ_CUDA_TRY(cudaMemcpyAsync(&n2, cents2 + c2, 4, cudaMemcpyDeviceToHost, s));
   }
   MDJ_CUDA_TRY(cudaMemcpyAsync(herr, err, 16, cudaMemcpyDeviceToHost, s));
-  // a shuffle pass that gave up on a bounded copy wait (opt-in bulk-copy scatter)
-  if (tmp.flag_word_if_any()) MDJ_CUDA_TRY(cudaMemcpyAsync(&pflag[0], tmp.flag_word_if_any(), 4, cudaMemcpyDeviceToHost, s));
-  if (keep.flag_word_if_any()) MDJ_CUDA_TRY(cudaMemcpyAsync(&pflag[1], keep.flag_word_if_any(), 4, cudaMemcpyDeviceToHost, s));
   MDJ_CUDA_TRY(cudaStreamSynchronize(s));
-  if (pflag[0] || pflag[1]) return MDJ_ERR_DEVICE_TIMEOUT;
   if (herr[0]) return MDJ_ERR_INTERNAL;
   const uint64_t total = t1 + t2;
   const uint32_t nm = n1 + n2;

@@ -203,3 +203,61 @@ def test_binding_rejects_bad_arguments_before_device_work(lib):
         mdj.mdj_merge_multi([k, p], [k, p], [0], [0], 8)              # not CUDA tensors
     assert mdj.HOW == {"inner": 0, "left": 1, "right": 2, "outer": 3}
     assert mdj.NO_ROW == 0xFFFFFFFF
+
+
+def test_compaction_position_width_gate(tmp_path):
+    # The key-tuple merge drops hash-collision candidates by a scan of m + 1
+    # keep flags; 32-bit positions must give way to 64-bit ones before the
+    # kept total can pass 2^32 - 1.  The gate is plain C++ (mdj_sizes.h), so it
+    # is compiled and checked here with the host compiler.
+    import shutil
+    import subprocess
+    if not shutil.which("g++"):
+        pytest.skip("no host C++ compiler")
+    src = tmp_path / "gate.cc"
+    src.write_text(
+        '#include "mdj_sizes.h"\n#include <stdio.h>\n'
+        'int main() {\n'
+        '  const unsigned long long m[] = {0ull, 1ull, 4294967293ull, 4294967294ull, 4294967295ull, 1ull << 40};\n'
+        '  for (unsigned long long v : m) printf("%d\\n", (int)mdj::compaction_needs_u64_positions(v));\n'
+        '  return 0;\n}\n')
+    exe = tmp_path / "gate"
+    csrc = os.path.join(ROOT, "paper_2101_08878_gb300", "csrc")
+    subprocess.run(["g++", "-std=c++17", "-I", csrc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    # 32-bit positions while the scan covers at most 2^32 - 1 flags
+    assert out == ["0", "0", "0", "0", "1", "1"]
+
+
+def test_noalloc_size_limit_at_p8(lib):
+    # mdj_partition_noalloc's fixed array holds P*T + ceil(P*T/4096) + P + 1
+    # words (T = ceil(nrows / 4096)) of 4 Mi; at P = 8 that admits
+    # 2,146,951,168 rows.  One row more is refused before any device work, so
+    # the call needs no GPU and no buffers of that size (the pointers below are
+    # never dereferenced).
+    from paper_2101_08878_gb300.mdj import MdjCol, MdjTable
+
+    def words(n, P):
+        nh = P * ((n + 4095) // 4096)
+        return nh + (nh + 4095) // 4096 + P + 1
+
+    limit = 2_146_951_168
+    assert words(limit, 8) <= 4 << 20 < words(limit + 1, 8)
+    cols = (MdjCol * 2)()
+    cols[0].data = ctypes.c_void_p(0x1000)  # stand-ins: refused before use
+    cols[0].dtype = 2
+    cols[1].data = ctypes.c_void_p(0x2000)
+    cols[1].dtype = 4
+    outs = (ctypes.c_void_p * 2)(0x3000, 0x4000)
+    off = ctypes.c_void_p(0x5000)
+    over = MdjTable(cols, 2, limit + 1)
+    assert lib.mdj_partition_noalloc(ctypes.byref(over), 0, 8, outs, None, off, None) == -3
+    assert lib.mdj_partition_noalloc(ctypes.byref(MdjTable(cols, 2, 16_764_929)), 0, 1024, outs, None, off,
+                                     None) == -3
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        return  # below the limit the call would start device work on the stand-in pointers
+    # with no device, a size inside the limit gets past the gate and stops at
+    # the first CUDA call instead
+    fits = MdjTable(cols, 2, limit)
+    assert lib.mdj_partition_noalloc(ctypes.byref(fits), 0, 8, outs, None, off, None) == -5

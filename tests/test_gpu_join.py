@@ -126,17 +126,8 @@ def test_two_level_plan_stable_passes(monkeypatch):
     assert got["key"].size == math.floor(0.3 * 2_000_000)
 
 
-def test_two_level_plan_fused_pass2_join(monkeypatch):
-    # pass 2 and the join in one kernel through scratch slots (MDJ_FUSED=1)
-    monkeypatch.setenv("MDJ_FUSED", "1")
-    (lk, lp), (rk, rp) = datagen.match_fraction_tables(4_000_000, 2_000_000, 0.3, seed=8)
-    got = _check([lk, lp], [rk, rp], 8)
-    assert got["key"].size == math.floor(0.3 * 2_000_000)
-
-
 @pytest.mark.parametrize("kd,pd", [(np.int32, np.float32), (np.int64, np.float32), (np.int32, np.float64)])
-def test_two_level_plan_fused_dtypes_and_duplicates(monkeypatch, kd, pd):
-    monkeypatch.setenv("MDJ_FUSED", "1")
+def test_two_level_plan_dtypes_and_duplicates(kd, pd):
     # 5M build rows: more sub-buckets than one pass can make, so two passes
     rng = np.random.default_rng(17)
     n = 5_000_000
@@ -232,13 +223,6 @@ def test_both_output_modes_match_oracle(monkeypatch, ordered):
     monkeypatch.setenv("MDJ_ORDERED_OUTPUT", ordered)
     (lk, lp), (rk, rp) = datagen.zipf_tables(20_000, 30_000, 50_000, 1.1, seed=23)
     _check([lk, lp], [rk, rp], 8)
-
-
-def test_merge_with_pipelined_scatter(monkeypatch):
-    monkeypatch.setenv("MDJ_PIPE_SCATTER", "1")
-    (lk, lp), (rk, rp) = datagen.match_fraction_tables(4_000_000, 1_000_000, 0.3, seed=31)
-    got = _check([lk, lp], [rk, rp], 8)
-    assert got["key"].size == 300_000
 
 
 def test_merge_host_end_to_end():

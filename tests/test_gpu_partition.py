@@ -81,11 +81,3 @@ def test_partition_invalid_args():
     with pytest.raises(mdj.MdjError) as e:
         mdj.mdj_partition([k.double()], 0, 4)  # float key
     assert e.value.status == -2
-
-
-@pytest.mark.parametrize("P", [1, 8, 200])
-def test_partition_pipelined_scatter(monkeypatch, P):
-    # the bulk-copy (TMA) pipelined scatter path gives the same bytes
-    monkeypatch.setenv("MDJ_PIPE_SCATTER", "1")
-    # key + one 8-byte payload: 16 loaded bytes per row, within the pipelined limit
-    _check(_table(100_003, np.int64, seed=P + 7)[:2], 0, P)
