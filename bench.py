@@ -196,21 +196,43 @@ def whole_job_rate(rows_per_rank: int, world: int, seconds: float) -> float:
     return rows_per_rank * world / seconds
 
 
-def alg_bytes_per_launch(kernel: str, n_side: int, n_left: int, n_right: int, m: int):
-    """Bytes the method must move in one launch of `kernel` (8-byte keys and
-    payloads, 4-byte row ids); None for kernels outside the model."""
-    per_side = {
-        "hist": KEY,                                       # read keys
-        "shuffle_pass1": (KEY + PAY) + (KEY + PAY + RID),  # read row, write row + row id
-        "shuffle_pass2": (KEY + PAY + RID) * 2,            # second level: read + write row and row id
-        "scatter_stable": (KEY + PAY) + (KEY + PAY + RID),  # the stable passes (MDJ_STABLE_SHUFFLE=1)
-        "scatter_reserve": (KEY + PAY + RID) * 2,
-    }
-    if kernel in per_side:
-        return per_side[kernel] * n_side
-    if kernel in ("join_write", "join_write_exact"):
-        return (KEY + PAY + RID) * (n_left + n_right) + OUT_ROW * m  # read both sides, write the rows
-    return None
+# Steps of the hot path as the roofline counts them (8-byte keys and
+# payloads, 4-byte row ids): the per-side histogram read (a2), the exchange
+# (a4: read a row, write it with its row id; a second internal radix pass is
+# overhead and adds no algorithmic bytes) and the join (a5-a7: read both
+# sides' partitioned rows, write the output rows).
+STEP_KERNELS = {
+    "hist": ("a2 histogram", ["hist"]),
+    "exchange": ("a4 scatter (the exchange)", ["shuffle_pass1", "shuffle_pass2", "scatter_stable",
+                                               "scatter_reserve"]),
+    "join": ("a5-a7 build + probe + write", ["join_write", "join_write_exact"]),
+}
+
+
+def step_alg_bytes(step: str, n_left: int, n_right: int, m: int) -> int:
+    if step == "hist":
+        return KEY * (n_left + n_right)
+    if step == "exchange":
+        return ((KEY + PAY) + (KEY + PAY + RID)) * (n_left + n_right)
+    return (KEY + PAY + RID) * (n_left + n_right) + OUT_ROW * m
+
+
+def step_rooflines(prof: dict, steps: int, n_left: int, n_right: int, m: int, peak: float):
+    """Per-step achieved bandwidth: the step's algorithmic bytes per merge over
+    the device time of its kernels per merge (CUDA events around every launch,
+    on the launch stream)."""
+    out = {}
+    for step, (label, names) in STEP_KERNELS.items():
+        ms = sum(prof[k][1] for k in names if k in prof) / steps
+        launches = sum(prof[k][0] for k in names if k in prof) // max(steps, 1)
+        if ms <= 0:
+            continue
+        alg = step_alg_bytes(step, n_left, n_right, m)
+        gbs = alg / (ms / 1e3) / 1e9
+        out[step] = {"what": label, "kernels": [k for k in names if k in prof], "launches_per_merge": launches,
+                     "ms_per_merge": round(ms, 4), "alg_bytes_per_merge": alg, "achieved_gbs": round(gbs, 1),
+                     "frac": round(gbs / peak, 4)}
+    return out
 
 
 def run_gpu(args):
@@ -268,25 +290,27 @@ def run_gpu(args):
     ms_step = ms_total / args.steps
     value = whole_job_rate(N_LEFT + N_RIGHT, world, ms_step / 1e3)
 
-    # ---- roofline: dominant kernel by total device time inside the timed region
+    # ---- roofline: the dominant step of the path (by device time inside the
+    # timed region), its algorithmic bytes per merge over its kernels' time
     peak, peak_kind = peaks()
     launches = sum(v[0] for v in prof.values())
-    dom = max(prof.items(), key=lambda kv: kv[1][1])
-    dom_name, (dom_launches, dom_ms) = dom
-    per_launch_ms = dom_ms / max(dom_launches, 1)
-    alg = alg_bytes_per_launch(dom_name, N_LEFT, N_LEFT, N_RIGHT, m_expect)
-    achieved = alg / (per_launch_ms / 1e3) / 1e9 if alg else None
-    traffic = measured_traffic(dom_name)
-    b_alg_step = 64 * (N_LEFT + N_RIGHT) + OUT_ROW * m_expect
+    steps_roof = step_rooflines(prof, args.steps, N_LEFT, N_RIGHT, m_expect, peak)
+    dom_step = max(steps_roof, key=lambda k: steps_roof[k]["ms_per_merge"])
+    d = steps_roof[dom_step]
+    traffic = measured_traffic(dom_step)
+    b_alg_step = step_alg_bytes("hist", N_LEFT, N_RIGHT, m_expect) + \
+        step_alg_bytes("exchange", N_LEFT, N_RIGHT, m_expect) + step_alg_bytes("join", N_LEFT, N_RIGHT, m_expect)
+    assert b_alg_step == 64 * (N_LEFT + N_RIGHT) + OUT_ROW * m_expect
     roofline = {
-        "bound": "hbm", "kernel": dom_name, "achieved": round(achieved, 1) if achieved else None,
-        "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None,
-        "traffic": traffic, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
-        else "fallback 6800 GB/s", "launch_ms": round(per_launch_ms, 4),
-        "alg_bytes_per_launch": alg,
+        "bound": "hbm", "kernel": f"{dom_step}: {d['what']} ({', '.join(d['kernels'])})",
+        "achieved": d["achieved_gbs"], "peak": peak, "unit": "GB/s", "frac": d["frac"],
+        "traffic": traffic,
+        "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6800 GB/s",
+        "ms_per_merge": d["ms_per_merge"], "alg_bytes_per_merge": d["alg_bytes_per_merge"],
+        "launches_per_merge": d["launches_per_merge"],
     }
     step_roof = {"alg_bytes": b_alg_step, "achieved_gbs": round(b_alg_step / (ms_step / 1e3) / 1e9, 1),
-                 "frac": round(b_alg_step / (ms_step / 1e3) / 1e9 / peak, 4)}
+                 "frac": round(b_alg_step / (ms_step / 1e3) / 1e9 / peak, 4), "steps": steps_roof}
     kernels = {k: {"launches": v[0], "ms_per_step": round(v[1] / args.steps, 4),
                    "share": round(v[1] / max(sum(x[1] for x in prof.values()), 1e-9), 4)}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
@@ -301,26 +325,17 @@ def run_gpu(args):
     if args.multikey_steps > 0:
         multi_key = multikey_section(args, left, right, m_expect, ms_step, dev)
 
-    # ---- end to end: host (pinned) inputs -> device -> merge -> host result
+    # ---- end to end through the C ABI with host buffers: mdj_merge_host takes
+    # the pinned host tables, copies them in, merges, and hands the result to
+    # a sink that copies it into pinned host buffers
     e2e = None
     if args.e2e_steps > 0:
         hl = [torch.from_numpy(lk).pin_memory(), torch.from_numpy(lp).pin_memory()]
         hr = [torch.from_numpy(rk).pin_memory(), torch.from_numpy(rp).pin_memory()]
         del left[:], right[:]
         torch.cuda.empty_cache()
-        out, h2d, d2h = mdj.merge_host(hl, hr, P)  # warm
-        del out
-        barrier()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            out, h2d, d2h = mdj.merge_host(hl, hr, P)
-            assert out.nrows == m_expect
-            del out
-        torch.cuda.synchronize()
-        dt = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, dist, dev)
-        e2e = {"value": whole_job_rate(N_LEFT + N_RIGHT, world, dt), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "ms_per_step": round(dt * 1e3, 3), "steps": args.e2e_steps}
+        e2e = e2e_section(args, dev, hl, hr, m_expect, dist, world)
+        del hl, hr
 
     # ---- the same tables merged from host memory under a 1 GiB device budget
     # (after e2e: its host-memory traffic would otherwise sit in e2e's timing)
@@ -345,6 +360,9 @@ def run_gpu(args):
     }
     if host_tables is not None:
         line["host_tables"] = host_tables
+    if args.latency_calls > 0:
+        torch.cuda.empty_cache()
+        line["plain_1M"] = plain_1m_section(args, dev)
     if multi_key is not None:
         line["multi_key"] = multi_key
     if args.stream_windows > 0:
@@ -364,6 +382,88 @@ def run_gpu(args):
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def e2e_section(args, dev, hl, hr, m_expect, dist, world):
+    """mdj_merge_host (the library's host-table entry point) from pinned host
+    tables to pinned host result buffers, timed on the host around each call
+    (the call synchronises its stream before it returns)."""
+    import torch
+    from paper_2101_08878_gb300 import mdj
+
+    budget = 32 << 30  # both tables fit one bucket: copied in once, merged in place
+    out = {"key": torch.empty(m_expect, dtype=torch.int64, pin_memory=True),
+           "lrow": torch.empty(m_expect, dtype=torch.uint32, pin_memory=True),
+           "rrow": torch.empty(m_expect, dtype=torch.uint32, pin_memory=True),
+           "lpay": torch.empty(m_expect, dtype=torch.float64, pin_memory=True),
+           "rpay": torch.empty(m_expect, dtype=torch.float64, pin_memory=True)}
+
+    def to_host(first, piece):
+        n = piece.nrows
+        out["key"][first:first + n].copy_(piece.key, non_blocking=True)
+        out["lrow"][first:first + n].copy_(piece.left_row, non_blocking=True)
+        out["rrow"][first:first + n].copy_(piece.right_row, non_blocking=True)
+        out["lpay"][first:first + n].copy_(piece.left_cols[0], non_blocking=True)
+        out["rpay"][first:first + n].copy_(piece.right_cols[0], non_blocking=True)
+
+    def call():
+        total, _ = mdj.merge_host_chunked(hl, hr, P, budget, on_piece=to_host, device=dev)
+        assert total == m_expect, total
+        return total
+
+    call()
+    call()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.e2e_steps):
+        t0 = time.perf_counter()
+        call()
+        times.append(time.perf_counter() - t0)
+    dt = max_over_ranks(statistics.mean(times), dist, dev)
+    # spot check: the host copy holds joined rows (key equals the left key of its left row)
+    lk_host = hl[0]
+    idx = torch.randint(0, m_expect, (1000,))
+    assert torch.equal(out["key"][idx], lk_host[out["lrow"][idx].view(torch.int32).to(torch.int64) & 0xFFFFFFFF])
+    h2d = sum(c.numel() * c.element_size() for c in list(hl) + list(hr))
+    d2h = sum(t.numel() * t.element_size() for t in out.values())
+    return {"value": whole_job_rate(N_LEFT + N_RIGHT, world, dt), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": round(dt * 1e3, 3), "steps": args.e2e_steps,
+            "api": "mdj_merge_host (C ABI): pinned host tables in, sink copies each result window to pinned "
+                   "host buffers; host wall time per call"}
+
+
+def plain_1m_section(args, dev):
+    """The 1M x 1M plain merge with one partition (unique left keys, match
+    fraction 0.3): latency of single mdj_merge calls, host-observed (the call
+    returns after the output count is read back and the rows are written)
+    and on the device (CUDA events around the call)."""
+    import torch
+    from paper_2101_08878_gb300 import mdj
+
+    (lk, lp), (rk, rp) = datagen.match_fraction_tables(1_000_000, 1_000_000, FRAC, seed=0)
+    L = [torch.from_numpy(lk).to(dev), torch.from_numpy(lp).to(dev)]
+    R = [torch.from_numpy(rk).to(dev), torch.from_numpy(rp).to(dev)]
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(20):
+        assert mdj.mdj_merge(L, R, 1).nrows == 300_000
+    torch.cuda.synchronize()
+    host_ms, dev_ms = [], []
+    for _ in range(args.latency_calls):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        res = mdj.mdj_merge(L, R, 1)
+        e1.record(stream)
+        host_ms.append((time.perf_counter() - t0) * 1e3)
+        assert res.nrows == 300_000
+        del res
+        e1.synchronize()
+        dev_ms.append(e0.elapsed_time(e1))
+    q = (lambda v, f: float(np.percentile(np.array(v), f)))
+    return {"workload": "plain inner merge, P=1: 1M x 1M rows, unique left keys, match fraction 0.3, 300,000 rows out",
+            "calls": args.latency_calls, "p50_ms": round(q(host_ms, 50), 4), "p99_ms": round(q(host_ms, 99), 4),
+            "device_p50_ms": round(q(dev_ms, 50), 4), "device_p99_ms": round(q(dev_ms, 99), 4),
+            "value": 2_000_000 / (q(host_ms, 50) / 1e3), "unit": "input rows/s at p50"}
 
 
 def multikey_section(args, left, right, m_expect, merge_ms, dev):
@@ -518,6 +618,20 @@ def streamed_section(args, dev):
     ri = buf.right_row[-1].view(torch.int32).to(torch.int64)
     assert int(L[0][li]) == int(R[0][ri]) == int(buf.key[-1])
     st.close()
+    # count + checksum mode on the same tables (mdj_count_checksum): its
+    # count must equal the stream's row count
+    mdj.mdj_count_checksum(L, R, P_z)  # warm
+    torch.cuda.synchronize()
+    cms = []
+    for _ in range(3):
+        t1 = time.perf_counter()
+        cnt, csum = mdj.mdj_count_checksum(L, R, P_z)
+        cms.append((time.perf_counter() - t1) * 1e3)
+    assert cnt == m, (cnt, m)
+    count_mode = {"rows": cnt, "checksum": csum, "ms": round(statistics.median(cms), 3),
+                  "value": (n_l + n_r) / (statistics.median(cms) / 1e3), "unit": "input rows/s",
+                  "note": "host wall time per mdj_count_checksum call (ends with the totals read back); "
+                          "the count equals the streamed output's row count"}
     peak, _ = peaks()
     med = statistics.median(ms)
     per_row = OUT_ROW + RID + PAY  # written row + the grouped build side's row id and payload read
@@ -534,7 +648,7 @@ def streamed_section(args, dev):
                                   "alg_bytes_per_row": per_row,
                                   "note": "32 B written + 12 B grouped build side read per row; probe-side "
                                           "and entry reads not counted"}},
-            "all_rows_estimate_s": round(m / rate, 1)}
+            "all_rows_estimate_s": round(m / rate, 1), "count_mode": count_mode}
 
 
 def transpose_section(args, dev):
@@ -644,81 +758,267 @@ def batched_section(args, dev):
             "speedup": round(ms_p / ms_b, 3)}
 
 
-def served_section(args, dev):
-    """The served workload: Poisson arrivals of merge requests (P in {1, 8, 32}, n_L, n_R
-    log-uniform in [1e4, 2e7], int32/int64 keys and float32/float64 payloads
-    50/50, match fraction 0.3) over a device-resident pool of tables, served
-    by MergeServer with continuous batching versus the plain per-request path
-    (one slot, no batching), at 0.5x, 1x and 2x the plain path's capacity."""
-    import asyncio
-    import torch
-    from paper_2101_08878_gb300.server import MergeServer, latency_stats, run_poisson
+_FP_M = (1 << 64) - 1
 
-    rng = np.random.default_rng(4)
-    pool, pool_out = [], []
-    for i in range(args.serve_pool):
+
+def _fp_mix_np(x):
+    x = x ^ (x >> np.uint64(33))
+    x = x * np.uint64(0xFF51AFD7ED558CCD)
+    x = x ^ (x >> np.uint64(33))
+    x = x * np.uint64(0xC4CEB9FE1A85EC53)
+    return x ^ (x >> np.uint64(33))
+
+
+def fingerprint_np(key, lrow, rrow, lpay, rpay):
+    """Order-independent fingerprint of a join result: (rows, sum over rows of
+    a 64-bit mix of every column's bits, modulo 2^64).  Two results agree on
+    it when they hold the same multiset of rows (up to a 2^-64 chance)."""
+    with np.errstate(over="ignore"):
+        bits = (lambda a: np.ascontiguousarray(a).view(np.uint32 if a.dtype.itemsize == 4 else np.uint64)
+                .astype(np.uint64))
+        h = _fp_mix_np(bits(key) ^ np.uint64(0x9E3779B97F4A7C15))
+        h = _fp_mix_np(h ^ (bits(lrow) * np.uint64(0xBF58476D1CE4E5B9)))
+        h = _fp_mix_np(h ^ (bits(rrow) * np.uint64(0x94D049BB133111EB)))
+        h = _fp_mix_np(h ^ bits(lpay))
+        h = _fp_mix_np(h ^ (bits(rpay) + np.uint64(0x632BE59BD9B4E019)))
+        return int(key.size), int(h.sum(dtype=np.uint64))
+
+
+_FP_CONST = {}
+
+
+def _fp_consts(dev):
+    """The fingerprint's 64-bit constants as int64 device scalars (cached)."""
+    import torch
+    key = str(dev)
+    if key not in _FP_CONST:
+        vals = [0xFF51AFD7ED558CCD, 0xC4CEB9FE1A85EC53, 0x9E3779B97F4A7C15, 0xBF58476D1CE4E5B9,
+                0x94D049BB133111EB, 0x632BE59BD9B4E019]
+        _FP_CONST[key] = [torch.tensor(v - (1 << 64) if v >= (1 << 63) else v, dtype=torch.int64, device=dev)
+                          for v in vals]
+    return _FP_CONST[key]
+
+
+def _fp_mix_t(x, k):
+    lsr = (lambda v, s: (v >> s) & ((1 << (64 - s)) - 1))  # logical shift of int64 bits
+    x = x ^ lsr(x, 33)
+    x = x * k[0]
+    x = x ^ lsr(x, 33)
+    x = x * k[1]
+    return x ^ lsr(x, 33)
+
+
+def fingerprint_torch(res):
+    """fingerprint_np on a device JoinResult (int64 arithmetic wraps modulo
+    2^64 like uint64); returns a device tensor [sum] (the row count is known
+    on the host)."""
+    import torch
+
+    def bits(t):
+        if t.element_size() == 4:
+            return t.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+        return t.view(torch.int64)
+
+    k = _fp_consts(res.key.device)
+    h = _fp_mix_t(bits(res.key) ^ k[2], k)
+    h = _fp_mix_t(h ^ (bits(res.left_row) * k[3]), k)
+    h = _fp_mix_t(h ^ (bits(res.right_row) * k[4]), k)
+    h = _fp_mix_t(h ^ bits(res.left_cols[0]), k)
+    h = _fp_mix_t(h ^ (bits(res.right_cols[0]) + k[5]), k)
+    return h.sum().reshape(1)
+
+
+def _oracle_fp(args):
+    """Worker of the served check: the oracle's join of one request, fingerprinted."""
+    lk, lp, rk, rp = args
+    import oracle
+    want = oracle.merge_table([lk, lp], [rk, rp])
+    return fingerprint_np(want["key"], want["left_row"], want["right_row"], want["left_cols"][0],
+                          want["right_cols"][0])
+
+
+def served_requests(n: int, seed: int = 4):
+    """The request stream's parameters: P in {1, 8, 32}, n_L and n_R log-uniform
+    in [1e4, 2e7], int32 or int64 keys and float32 or float64 payloads (50/50)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
         nl = int(datagen.log_uniform_sizes(rng, 1, 10_000, 20_000_000)[0])
         nr = int(datagen.log_uniform_sizes(rng, 1, 10_000, 20_000_000)[0])
-        kd = np.int32 if rng.random() < 0.5 else np.int64
-        pd = np.float32 if rng.random() < 0.5 else np.float64
-        (lk, lp), (rk, rp) = datagen.match_fraction_tables(nl, nr, FRAC, seed=4000 + i, key_dtype=kd, pay_dtype=pd)
-        P = int(rng.choice([1, 8, 32]))
-        pool_out.append(int(np.floor(FRAC * nr)))
-        pool.append(([torch.from_numpy(lk).to(dev), torch.from_numpy(lp).to(dev)],
-                     [torch.from_numpy(rk).to(dev), torch.from_numpy(rp).to(dev)], P))
-    picks = rng.integers(0, len(pool), args.serve_requests)
-    out_rows = []
+        kd = "int32" if rng.random() < 0.5 else "int64"
+        pd = "float32" if rng.random() < 0.5 else "float64"
+        out.append({"i": i, "nl": nl, "nr": nr, "key": kd, "pay": pd, "P": int(rng.choice([1, 8, 32]))})
+    return out
+
+
+def request_tables(spec, dev):
+    """One request's tables on the device from its own seed (the match-fraction
+    recipe: left keys a permutation of [0, n_L), floor(0.3 n_R) right keys drawn
+    from the left keys, the rest from [n_L, 2 n_L), right rows shuffled;
+    payloads U[0, 1))."""
+    import torch
+    g = torch.Generator(device=dev)
+    g.manual_seed(4000 + spec["i"])
+    kd = getattr(torch, spec["key"])
+    pd = getattr(torch, spec["pay"])
+    nl, nr = spec["nl"], spec["nr"]
+    m = math.floor(FRAC * nr)
+    lk = torch.randperm(nl, generator=g, device=dev).to(kd)
+    pick = torch.randint(0, nl, (m,), generator=g, device=dev)
+    rk = torch.cat([lk[pick], torch.randint(nl, 2 * nl, (nr - m,), generator=g, device=dev).to(kd)])
+    rk = rk[torch.randperm(nr, generator=g, device=dev)]
+    lp = torch.rand(nl, generator=g, device=dev, dtype=pd)
+    rp = torch.rand(nr, generator=g, device=dev, dtype=pd)
+    return [lk, lp], [rk, rp], m
+
+
+def _canonical(res):
+    """The rows of a device JoinResult sorted by (key, left_row, right_row), all columns."""
+    import torch
+    order = torch.argsort(res.right_row.view(torch.int32).to(torch.int64) & 0xFFFFFFFF, stable=True)
+    for col in (res.left_row.view(torch.int32).to(torch.int64) & 0xFFFFFFFF, res.key.to(torch.int64)):
+        order = order[torch.argsort(col[order], stable=True)]
+    return [t[order] for t in [res.key, res.left_row, res.right_row, *res.left_cols, *res.right_cols]]
+
+
+def served_canonical_check(work, dev, max_batch_rows, groups: int = 8, per_group: int = 4):
+    """Seeded groups of requests with one dtype class are served together
+    (MergeServer, batching on) and every result is compared, column by column
+    and bit for bit after the canonical sort, with the request run alone."""
+    import asyncio
+    import torch
+    from paper_2101_08878_gb300 import mdj
+    from paper_2101_08878_gb300.server import MergeServer, run_poisson
+
+    rng = np.random.default_rng(47)
+    by_cls = {}
+    for i, (L, R, P_, m) in enumerate(work):
+        by_cls.setdefault((L[0].dtype, L[1].dtype), []).append(i)
+    checked = 0
+    for g in range(groups):
+        cls = sorted(by_cls, key=str)[g % len(by_cls)]
+        pick = rng.choice(by_cls[cls], min(per_group, len(by_cls[cls])), replace=False).tolist()
+        wl = [work[i][:3] for i in pick]
+        server = MergeServer(dev, slots=1, batching=True, max_batch_rows=max_batch_rows)
+        reqs, _ = asyncio.run(run_poisson(server, wl, np.zeros(len(wl))))
+        for i, req in zip(pick, reqs):
+            assert req.error is None, req.error
+            L, R, P_, m = work[i]
+            a = _canonical(mdj.mdj_merge(L, R, P_))
+            b = _canonical(req.result)
+            for x, y in zip(a, b):
+                if not torch.equal(x.view(torch.uint8), y.view(torch.uint8)):
+                    raise RuntimeError(f"request {i}: served rows differ from the same request alone")
+            req.result = None
+            checked += 1
+    return {"requests": checked, "how": "batches of up to 4 same-dtype requests, canonical sort, bit for bit"}
+
+
+def served_section(args, dev):
+    """The served workload at its configured scale: a Poisson stream of
+    merge requests, each with its own tables generated on the device from the
+    request's seed, served by MergeServer with continuous batching versus the
+    plain per-request path (one slot, no batching) at 0.5x, 1x and 2x the
+    plain path's capacity.  Every served result is checked against the same
+    request run alone (fingerprint over all columns' bits, and a full
+    canonical compare for a sample), and a seeded sample of requests plus
+    every request with both sides at most 1M rows against the CPU oracle."""
+    import asyncio
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    import torch
+    from paper_2101_08878_gb300 import mdj
+    from paper_2101_08878_gb300.server import MergeServer, latency_stats, run_poisson
+
+    specs = served_requests(args.serve_requests)
+    work = []
+    for sp in specs:
+        L, R, m = request_tables(sp, dev)
+        work.append((L, R, sp["P"], m))
+    torch.cuda.synchronize()
+    rows_all = sum(sp["nl"] + sp["nr"] for sp in specs)
+    # every request alone (the plain path), fingerprinted
+    alone_rows, alone = [], []
+    for L, R, P_, m in work:
+        res = mdj.mdj_merge(L, R, P_)
+        assert res.nrows == m
+        alone_rows.append(res.nrows)
+        alone.append(fingerprint_torch(res))
+        del res
+    alone = torch.cat(alone).cpu()
+    # served and plain runs: every result's fingerprint against the alone one
+    fps = {}
 
     def consume(req):
-        # the client reads its result and lets it go, as a caller of a server
-        # would; keeping thousands of results would fill the device
         if req.result is not None:
-            out_rows.append(req.result.nrows)
+            r = req.result
+            fps[id(req)] = (r.nrows, fingerprint_torch(r))
+            for t in [r.key, r.left_row, r.right_row, *r.left_cols, *r.right_cols]:
+                t.record_stream(torch.cuda.current_stream(dev))
             req.result = None
 
-    def run(rate, batching, slots, sel):
-        work = [pool[int(i)] for i in sel]
-        rows = sum(int(w[0][0].numel() + w[1][0].numel()) for w in work)
-        # match fraction 0.3 of the right side: the closed-form output row count
-        expect_rows = sum(pool_out[int(i)] for i in sel)
+    def run(rate, batching, slots, idx):
+        wl = [work[int(i)][:3] for i in idx]
+        rows = sum(int(w[0][0].numel() + w[1][0].numel()) for w in wl)
         server = MergeServer(dev, slots=slots, batching=batching, max_batch_rows=args.serve_batch_rows)
-        arrivals = np.cumsum(np.random.default_rng(44).exponential(1.0 / rate, len(work)))
-        out_rows.clear()
-        reqs, wall = asyncio.run(asyncio.wait_for(run_poisson(server, work, arrivals, consume), 300))
+        arrivals = np.cumsum(np.random.default_rng(44).exponential(1.0 / rate, len(wl)))
+        fps.clear()
+        reqs, wall = asyncio.run(asyncio.wait_for(run_poisson(server, wl, arrivals, consume), 600))
         bad = [r.error for r in reqs if r.error is not None]
         if bad:
             raise RuntimeError(f"served requests failed: {bad[0]}")
-        if sum(out_rows) != expect_rows:
-            raise RuntimeError(f"served output rows {sum(out_rows)} != {expect_rows}")
+        got = torch.cat([fps[id(r)][1] for r in reqs]).cpu()
+        want = alone[torch.as_tensor(np.asarray(idx, dtype=np.int64))]
+        mism = int((got != want).sum()) + sum(1 for r, i in zip(reqs, idx) if fps[id(r)][0] != alone_rows[int(i)])
+        if mism:
+            raise RuntimeError(f"{mism} served results differ from the same requests run alone")
         st = latency_stats(reqs)
         st["rows_per_s"] = rows / wall
         st["wall_s"] = round(wall, 3)
         st["mean_batch"] = round(float(np.mean(server.group_sizes)), 2)
+        st["checked_vs_alone"] = len(reqs)
         return st
 
-    # first launches of each path's kernels (module loads, attribute setup)
-    # stay out of the timed runs
-    run(1e9, True, 2, picks[:100])
-    run(1e9, False, 1, picks[:100])
-    # capacity of the plain per-request path: everything queued at once
-    cap = run(1e9, False, 1, picks)
-    cap_rps = len(picks) / cap["wall_s"]
-    out = {"workload": f"{len(picks)} requests drawn from {len(pool)} device-resident table pairs; P in {{1,8,32}}, "
-                       f"n_L, n_R log-uniform [1e4, 2e7], int32/int64 keys, float32/float64 payloads, match 0.3",
+    idx_all = np.arange(len(work))
+    canonical_checked = served_canonical_check(work, dev, args.serve_batch_rows)
+    run(1e9, True, 2, idx_all[:100])  # first launches of each path stay out of the timed runs
+    run(1e9, False, 1, idx_all[:100])
+    cap = run(1e9, False, 1, idx_all)  # capacity of the plain path: everything queued at once
+    cap_rps = len(work) / cap["wall_s"]
+    out = {"workload": f"{len(work)} requests, each with its own tables generated on the device from its seed; "
+                       f"P in {{1,8,32}}, n_L, n_R log-uniform [1e4, 2e7], int32/int64 keys, float32/float64 "
+                       f"payloads, match 0.3; {rows_all} input rows in all",
            "served_config": {"slots": 2, "max_batch_rows": args.serve_batch_rows},
            "plain_config": {"slots": 1, "batching": False},
            "plain_capacity_requests_per_s": round(cap_rps, 2), "rates": []}
     for mult in (0.5, 1.0, 2.0):
         rate = mult * cap_rps
         out["rates"].append({"x_plain_capacity": mult, "requests_per_s": round(rate, 2),
-                             "served": run(rate, True, 2, picks), "plain": run(rate, False, 1, picks)})
+                             "served": run(rate, True, 2, idx_all), "plain": run(rate, False, 1, idx_all)})
+    # oracle: a seeded sample plus every request with both sides <= 1M rows
+    small = [i for i, sp in enumerate(specs) if sp["nl"] <= 1_000_000 and sp["nr"] <= 1_000_000]
+    sample = sorted(set(np.random.default_rng(46).choice(len(specs), min(100, len(specs)), replace=False).tolist())
+                    | set(small))
+    jobs = [(work[i][0][0].cpu().numpy(), work[i][0][1].cpu().numpy(), work[i][1][0].cpu().numpy(),
+             work[i][1][1].cpu().numpy()) for i in sample]
+    with ProcessPoolExecutor(max_workers=max(1, min(16, host_cores())), mp_context=mp.get_context("spawn")) as ex:
+        want = list(ex.map(_oracle_fp, jobs, chunksize=4))
+    got = alone[torch.as_tensor(sample, dtype=torch.int64)].tolist()
+    wrong = sum(1 for (n, h), g, i in zip(want, got, sample)
+                if n != alone_rows[i] or (h - (1 << 64) if h >= (1 << 63) else h) != g)
+    if wrong:
+        raise RuntimeError(f"{wrong} of {len(sample)} requests differ from the CPU oracle")
+    out["checked_vs_oracle"] = {"requests": len(sample), "with_both_sides_le_1M": len(small), "mismatches": 0}
+    out["checked_row_for_row_alone_vs_batched"] = canonical_checked
+    del work
     return out
 
 
-def measured_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from a committed ncu summary, if the
-    kernel's source files (comma-separated, hashed together) are unchanged
-    since the capture (else None)."""
+def measured_traffic(step: str):
+    """DRAM bytes per merge of one step of the path (dram__bytes_read.sum +
+    dram__bytes_write.sum of its kernels) from a committed ncu summary, scaled
+    from the captured case by input rows, if the step's source files (comma-
+    separated, hashed together) are unchanged since the capture (else None)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     src = os.path.join(ROOT, "paper_2101_08878_gb300", "csrc")
@@ -728,13 +1028,13 @@ def measured_traffic(kernel: str):
         return None
     for r in rows:
         kv = dict(x.split("=", 1) for x in r if "=" in x)
-        if kv.get("kernel") != kernel:
+        if kv.get("step") != step:
             continue
-        blob = b"".join(open(os.path.join(src, f), "rb").read() for f in kv["file"].split(","))
+        blob = b"".join(open(os.path.join(src, f), "rb").read() for f in kv["files"].split(","))
         h = hashlib.sha256(blob).hexdigest()[:16]
         if h != kv.get("src_sha"):
             return None
-        return int(float(kv["bytes_per_unit"]) * N_LEFT)
+        return int(float(kv["bytes_per_input_row"]) * (N_LEFT + N_RIGHT))
     return None
 
 
@@ -776,7 +1076,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mdj", choices=["mdj", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--latency-calls", type=int, default=300,
+                    help="timed calls of the 1M x 1M, P=1 merge (p50/p99 latency)")
     ap.add_argument("--cpu-sample", type=int, default=10_000_000)
     ap.add_argument("--ref-sample", type=int, default=2_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")

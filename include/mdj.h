@@ -364,6 +364,10 @@ MDJ_API int mdj_merge_multi(const mdj_table *left, const int32_t *left_keys, con
  *      of the bucket would then share one partition), and its rows
  *      are written window by window; each window's row ids are mapped back to
  *      the input tables and the window is handed to `sink`.
+ * When both tables together (with 4-byte row ids) take at most a sixth of the
+ * budget, B = 1: phase 1 is skipped, each column goes to the device with one
+ * copy, and an inner merge runs mdj_merge there and hands its result to the
+ * sink in windows that point into it (other join types stream as in 2.).
  *   left, right   : tables whose column pointers are HOST pointers (pageable
  *                   or pinned), read only
  *   device_budget : bytes of device memory the call sizes its pieces for

@@ -124,6 +124,105 @@ int bucket_to_device(Workspace &ws, const mdj_table *t, const HostBuckets &hb, u
   return MDJ_OK;
 }
 
+// A whole host table on the device: one block and one copy per column.
+int table_to_device(Workspace &ws, const mdj_table *t, mdj_col *cols, mdj_table *out) {
+  for (int j = 0; j < t->ncols; j++) {
+    const size_t bytes = t->nrows * (size_t)dtype_width(t->cols[j].dtype);
+    unsigned char *d = dev_block(ws, bytes);
+    if (!d) return MDJ_ERR_OOM;
+    if (bytes) MDJ_CUDA_TRY(cudaMemcpyAsync(d, t->cols[j].data, bytes, cudaMemcpyHostToDevice, ws.stream()));
+    cols[j].data = d;
+    cols[j].dtype = t->cols[j].dtype;
+  }
+  *out = {cols, t->ncols, t->nrows};
+  return MDJ_OK;
+}
+
+// Rows [q0, q0 + n) of a device result, as a piece pointing into it.
+mdj_result result_piece(const mdj_result &r, uint64_t q0, uint64_t n) {
+  mdj_result p = r;
+  p.nrows = n;
+  const int kw = dtype_width(r.key_dtype);
+  if (r.key) p.key = (unsigned char *)r.key + q0 * kw;
+  if (r.left_row) p.left_row = r.left_row + q0;
+  if (r.right_row) p.right_row = r.right_row + q0;
+  for (int j = 0; j < r.n_left_cols; j++)
+    if (r.left_cols[j]) p.left_cols[j] = (unsigned char *)r.left_cols[j] + q0 * dtype_width(r.left_dtypes[j]);
+  for (int j = 0; j < r.n_right_cols; j++)
+    if (r.right_cols[j]) p.right_cols[j] = (unsigned char *)r.right_cols[j] + q0 * dtype_width(r.right_dtypes[j]);
+  return p;
+}
+
+// Both tables fit one bucket of the budget: they go to the device once and
+// are merged in place.  An inner merge runs mdj_merge and hands its result to
+// the sink in windows that point into it; the other join types stream their
+// rows through one window buffer.  Row ids are already input row ids.
+int merge_resident(const mdj_table *left, int32_t lk, const mdj_table *right, int32_t rk, uint32_t P, int32_t how,
+                   uint64_t window, mdj_sink sink, void *sink_ctx, const mdj_allocator *alloc, cudaStream_t s,
+                   uint64_t *total_rows) {
+  Workspace ws(alloc, s);
+  mdj_col lc[MDJ_MAX_COLS], rc[MDJ_MAX_COLS];
+  mdj_table lt, rt;
+  MDJ_TRY(table_to_device(ws, left, lc, &lt));
+  MDJ_TRY(table_to_device(ws, right, rc, &rt));
+  uint64_t produced = 0;
+  int rc2 = MDJ_OK;
+  if (how == MDJ_INNER) {
+    mdj_result res;
+    MDJ_TRY(mdj_merge(&lt, lk, &rt, rk, P, alloc, (void *)s, &res));
+    rc2 = cuda_status(cudaStreamSynchronize(s));
+    for (uint64_t q0 = 0; q0 < res.nrows && rc2 == MDJ_OK; q0 += window) {
+      const uint64_t n = std::min(window, res.nrows - q0);
+      const mdj_result piece = result_piece(res, q0, n);
+      if (sink(&piece, produced, sink_ctx) != 0) rc2 = MDJ_ERR_ABORTED;
+      produced += n;
+    }
+    mdj_result_release(&res, alloc, (void *)s);
+  } else {
+    Workspace wbuf(alloc, s);
+    mdj_result piece;
+    memset(&piece, 0, sizeof piece);
+    mdj_window win;
+    memset(&win, 0, sizeof win);
+    piece.key_dtype = left->cols[lk].dtype;
+    win.key = piece.key = dev_block(wbuf, window * dtype_width(piece.key_dtype));
+    win.left_row = piece.left_row = (uint32_t *)dev_block(wbuf, window * 4);
+    win.right_row = piece.right_row = (uint32_t *)dev_block(wbuf, window * 4);
+    if (!piece.key || !piece.left_row || !piece.right_row) return MDJ_ERR_OOM;
+    for (int j = 0, c = 0; j < left->ncols; j++) {
+      if (j == lk) continue;
+      piece.left_dtypes[c] = left->cols[j].dtype;
+      if (!(piece.left_cols[c] = win.left_cols[c] = dev_block(wbuf, window * dtype_width(left->cols[j].dtype))))
+        return MDJ_ERR_OOM;
+      piece.n_left_cols = ++c;
+    }
+    for (int j = 0, c = 0; j < right->ncols; j++) {
+      if (j == rk) continue;
+      piece.right_dtypes[c] = right->cols[j].dtype;
+      if (!(piece.right_cols[c] = win.right_cols[c] = dev_block(wbuf, window * dtype_width(right->cols[j].dtype))))
+        return MDJ_ERR_OOM;
+      piece.n_right_cols = ++c;
+    }
+    mdj_stream *h = nullptr;
+    uint64_t m = 0;
+    MDJ_TRY(mdj_stream_open(&lt, lk, &rt, rk, P, how, alloc, (void *)s, &h, &m));
+    for (uint64_t q0 = 0; q0 < m && rc2 == MDJ_OK; q0 += window) {
+      const uint64_t n = std::min(window, m - q0);
+      rc2 = mdj_stream_emit(h, q0, n, &win);
+      if (rc2 == MDJ_OK) rc2 = cuda_status(cudaStreamSynchronize(s));
+      if (rc2 != MDJ_OK) break;
+      piece.nrows = n;
+      if (sink(&piece, produced, sink_ctx) != 0) rc2 = MDJ_ERR_ABORTED;
+      produced += n;
+    }
+    mdj_stream_close(h);
+  }
+  MDJ_TRY(rc2);
+  MDJ_CUDA_TRY(cudaStreamSynchronize(s));
+  *total_rows = produced;
+  return MDJ_OK;
+}
+
 uint64_t row_bytes(const mdj_table *t) {
   uint64_t b = 0;
   for (int j = 0; j < t->ncols; j++) b += dtype_width(t->cols[j].dtype);
@@ -161,6 +260,8 @@ int merge_host_impl(const mdj_table *left, int32_t lk, const mdj_table *right, i
   const uint64_t chunk_rows = std::max<uint64_t>(1, (budget / 4) / (2 * std::max(wl, wr) + 4));
   const uint64_t out_row = wl + wr + 8 - dtype_width(kd);  // key once, both row ids, every other column
   const uint64_t window = std::max<uint64_t>(1, (budget / 6) / out_row);
+
+  if (B == 1) return merge_resident(left, lk, right, rk, P, how, window, sink, sink_ctx, alloc, s, total_rows);
 
   HostBuckets hl, hr;
   MDJ_TRY(partition_to_host(left, lk, (uint32_t)B, chunk_rows, alloc, s, &hl));

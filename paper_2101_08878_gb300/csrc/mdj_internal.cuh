@@ -183,6 +183,22 @@ __device__ __forceinline__ void block_scan_array(uint32_t *a, uint32_t n, uint32
   __syncthreads();
 }
 
+// Bits of element i of a 4- or 8-byte column (0 for a missing column).
+__device__ __forceinline__ uint64_t pay_bits(const void *col, int width, uint32_t i) {
+  if (!col) return 0;
+  return width == 8 ? ((const uint64_t *)col)[i] : (uint64_t)((const uint32_t *)col)[i];
+}
+
+// The two terms of mdj_count_checksum's checksum (defined in mdj.h):
+// f(l) for a left row l with key bits kbits and first-payload bits pbits,
+// g(r) for a right row r; the checksum is the sum of f(l) g(r) over pairs.
+__device__ __forceinline__ uint64_t term_f(uint64_t kbits, uint32_t lrow, uint64_t pbits) {
+  return fmix64(kbits ^ (0x9E3779B97F4A7C15ULL * ((uint64_t)lrow + 1)) ^ pbits);
+}
+__device__ __forceinline__ uint64_t term_g(uint32_t rrow, uint64_t pbits) {
+  return fmix64((0xC2B2AE3D27D4EB4FULL * ((uint64_t)rrow + 1)) ^ pbits);
+}
+
 // ------------------------------------------------------------ host helpers
 
 inline int dtype_width(int32_t dt) {
@@ -318,6 +334,14 @@ size_t stable_partition_scratch_words(uint64_t n, uint32_t P);
 int stable_partition_scratch(const mdj_table *t, int32_t key_col, uint32_t P, void *const *out_cols,
                              uint32_t *out_rid, int64_t *out_offsets, uint32_t *scratch, size_t scratch_words,
                              cudaStream_t s);
+
+// mdj_count_checksum: the pair count and checksum of the inner join, from
+// the streamed output's grouping (every key group of the build side gathered
+// once, each probe row told its group): count = sum of the probe rows' group
+// sizes, checksum = sum over probe rows r of g(r) times the sum of f over r's
+// group (a prefix sum over the grouped build rows).
+int grouped_count_checksum(const mdj_table *left, int32_t lk, const mdj_table *right, int32_t rk, uint32_t P,
+                           const mdj_allocator *alloc, void *stream, uint64_t *count, uint64_t *checksum);
 
 // Exclusive scans (out may equal in).  n may be 0.
 int exclusive_scan_u32(Workspace &ws, const uint32_t *in, uint32_t *out, size_t n);

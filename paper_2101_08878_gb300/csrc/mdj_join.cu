@@ -16,13 +16,9 @@
 // counts are already known, so one exact write pass at the recorded item
 // offsets follows.  The grand total is the one value read back to the host.
 //
-// Table layout (per block, shared memory): build keys keys_s[cap]; slot words
-// (tag16 << 16 | head+1) over 2^k >= 2*rows slots with linear probing; one
-// slot per DISTINCT key, with its member count cnt[] and a member chain nxt[]
-// through the build rows, so duplicate keys cost one slot and the probe finds a
-// key in O(1) however many copies it has.  Slots and tags come from a cheap
-// multiplicative hash of the key: bucket membership was already randomised by
-// the partition hash.
+// The pair count and checksum of a join (mdj_count_checksum) come from the
+// streamed output's grouping instead (mdj_stream.cu), which handles key groups
+// of any size without re-reading probe rows.
 #include <string.h>
 
 #include "mdj_internal.cuh"
@@ -32,35 +28,6 @@
 namespace mdj {
 namespace {
 
-
-template <typename KeyT>
-size_t join_smem_bytes(uint32_t cap, bool fsum) {
-  size_t t = 32;
-  while (t < 2 * (size_t)cap) t *= 2;  // slots of the largest table
-  size_t b = align16((size_t)cap * sizeof(KeyT) + (size_t)cap * 2) + t * 8;
-  if (fsum) b += t * 8;
-  return b;
-}
-
-__device__ __forceinline__ uint64_t pay_bits(const void *col, int width, uint32_t i) {
-  if (!col) return 0;
-  return width == 8 ? ((const uint64_t *)col)[i] : (uint64_t)((const uint32_t *)col)[i];
-}
-
-// checksum terms (mdj_count_checksum)
-__device__ __forceinline__ uint64_t term_f(uint64_t kbits, uint32_t lrow, uint64_t pbits) {
-  return fmix64(kbits ^ (0x9E3779B97F4A7C15ULL * ((uint64_t)lrow + 1)) ^ pbits);
-}
-__device__ __forceinline__ uint64_t term_g(uint32_t rrow, uint64_t pbits) {
-  return fmix64((0xC2B2AE3D27D4EB4FULL * ((uint64_t)rrow + 1)) ^ pbits);
-}
-
-// In-table position: top logt bits of key * golden-ratio constant; tag: bits 32..47.
-__device__ __forceinline__ void slot_tag(uint64_t kb, uint32_t logt, uint32_t &slot, uint32_t &tag) {
-  const uint64_t g = kb * 0x9E3779B97F4A7C15ULL;
-  slot = (uint32_t)(g >> (64 - logt));
-  tag = (uint32_t)(g >> 32) & 0xFFFFu;
-}
 
 // ------------------------------------------------------------- work items
 
@@ -103,181 +70,22 @@ __global__ void k_expand(const uint32_t *__restrict__ offL, const uint32_t *__re
   }
 }
 
-// ------------------------------------------------------------ table build
-
-template <typename KeyT>
-__device__ __forceinline__ uint32_t table_log(uint32_t nl) {
-  uint32_t logt = 5;
-  while ((1u << logt) < 2 * nl) logt++;
-  return logt;
-}
-
-// Loads the build keys into shared memory and clears 2^logt slots.
-template <typename KeyT, bool FSUM>
-__device__ __forceinline__ void load_and_clear(const KeyT *__restrict__ Lkey, uint32_t lbeg, uint32_t nl, uint32_t tsz,
-                                               KeyT *keys_s, uint32_t *slots, uint32_t *cnt, uint64_t *fsum) {
-  const uint32_t nthr = blockDim.x, tid = threadIdx.x;
-  for (uint32_t i0 = 0; i0 < nl; i0 += 4 * nthr) {
-    KeyT v[4];
-#pragma unroll
-    for (int u = 0; u < 4; u++) {
-      const uint32_t i = i0 + u * nthr + tid;
-      v[u] = i < nl ? Lkey[lbeg + i] : KeyT(0);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; u++) {
-      const uint32_t i = i0 + u * nthr + tid;
-      if (i < nl) keys_s[i] = v[u];
-    }
-  }
-  uint4 z = make_uint4(0, 0, 0, 0);
-  for (uint32_t s = tid * 4; s < tsz; s += nthr * 4) {
-    *(uint4 *)(slots + s) = z;
-    *(uint4 *)(cnt + s) = z;
-  }
-  if (FSUM)
-    for (uint32_t s = tid * 2; s < tsz; s += nthr * 2) *(uint4 *)(fsum + s) = z;
-}
-
-// One slot per distinct key; rows of a key are chained through nxt[] (head =
-// the slot word's index, most recent insert first) and counted in cnt[].
-template <typename KeyT, bool FSUM>
-__device__ __forceinline__ void build_table(const KeyT *keys_s, uint32_t nl, uint32_t logt, uint32_t *slots,
-                                            uint32_t *cnt, uint16_t *nxt, uint64_t *fsum, const JSide &L,
-                                            uint32_t lbeg) {
-  const uint32_t mask = (1u << logt) - 1;
-  for (uint32_t i = threadIdx.x; i < nl; i += blockDim.x) {
-    const KeyT k = keys_s[i];
-    uint32_t s, tag;
-    slot_tag(key_bits(k), logt, s, tag);
-    const uint32_t w = (tag << 16) | (i + 1);
-    for (uint32_t probe = 0; probe <= mask; probe++) {
-      uint32_t cur = slots[s];
-      if (cur == 0) {
-        const uint32_t prev = atomicCAS(&slots[s], 0u, w);
-        if (prev == 0) {
-          nxt[i] = 0;
-          break;
-        }
-        cur = prev;
-      }
-      if ((cur >> 16) == tag && keys_s[(cur & 0xFFFFu) - 1] == k) {
-        const uint32_t prev = atomicExch(&slots[s], w);
-        nxt[i] = (uint16_t)(prev & 0xFFFFu);
-        break;
-      }
-      s = (s + 1) & mask;
-    }
-    atomicAdd(&cnt[s], 1u);
-    if (FSUM) {
-      const uint32_t lr = L.rid ? L.rid[lbeg + i] : lbeg + i;
-      const uint64_t pb = L.ncols > 0 ? pay_bits(L.cols[0], L.width[0], lbeg + i) : 0ull;
-      atomicAdd((unsigned long long *)&fsum[s], (unsigned long long)term_f(key_bits(k), lr, pb));
-    }
-  }
-}
-
-// Probe: slot of key k (or where the search ended) and the chain head (0: absent).
-template <typename KeyT>
-__device__ __forceinline__ uint32_t probe_table(const KeyT k, const KeyT *keys_s, const uint32_t *slots, uint32_t logt,
-                                                uint32_t &slot_out) {
-  const uint32_t mask = (1u << logt) - 1;
-  uint32_t s, tag;
-  slot_tag(key_bits(k), logt, s, tag);
-  uint32_t head = 0;
-  for (uint32_t probe = 0; probe <= mask; probe++) {
-    const uint32_t w = slots[s];
-    if (w == 0) break;
-    if ((w >> 16) == tag && keys_s[(w & 0xFFFFu) - 1] == k) {
-      head = w & 0xFFFFu;
-      break;
-    }
-    s = (s + 1) & mask;
-  }
-  slot_out = s;
-  return head;
-}
-
-__device__ __forceinline__ uint32_t next_ticket(uint32_t *ticket, uint32_t *s_it) {
-  if (threadIdx.x == 0) *s_it = atomicAdd(ticket, 1u);
-  __syncthreads();
-  const uint32_t it = *s_it;
-  __syncthreads();
-  return it;
-}
-
-// ---------------------------------------------------- count (+ checksum)
-
-// Pair count (and pair checksum) of every item, summed into totals[0..1].
-template <typename KeyT, bool CHECKSUM>
-__global__ void __launch_bounds__(kJoinThreads, 2)
-    k_join_count(JSide L, JSide R, const Item *__restrict__ desc, uint32_t nitems, uint32_t *ticket,
-                 unsigned long long *totals) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ uint32_t s_it;
-  const KeyT *__restrict__ Lkey = (const KeyT *)L.key;
-  const KeyT *__restrict__ Rkey = (const KeyT *)R.key;
-  const uint32_t nthr = blockDim.x, tid = threadIdx.x;
-  for (;;) {
-    const uint32_t it = next_ticket(ticket, &s_it);
-    if (it >= nitems) break;
-    const Item d = desc[it];
-    const uint32_t logt = table_log<KeyT>(d.nl), tsz = 1u << logt;
-    KeyT *keys_s = (KeyT *)smem;
-    uint16_t *nxt = (uint16_t *)(smem + (size_t)d.nl * sizeof(KeyT));
-    uint32_t *slots = (uint32_t *)(smem + align16((size_t)d.nl * (sizeof(KeyT) + 2)));
-    uint32_t *cnt = slots + tsz;
-    uint64_t *fsum = (uint64_t *)(cnt + tsz);
-    load_and_clear<KeyT, CHECKSUM>(Lkey, d.lbeg, d.nl, tsz, keys_s, slots, cnt, fsum);
-    __syncthreads();
-    build_table<KeyT, CHECKSUM>(keys_s, d.nl, logt, slots, cnt, nxt, fsum, L, d.lbeg);
-    __syncthreads();
-    uint64_t acc = 0, csum = 0;
-    for (uint32_t r0 = d.rbeg; r0 < d.rbeg + d.nr; r0 += kPF * nthr) {
-      KeyT rk[kPF];
-#pragma unroll
-      for (int j = 0; j < kPF; j++) {
-        const uint32_t r = r0 + j * nthr + tid;
-        rk[j] = r < d.rbeg + d.nr ? Rkey[r] : KeyT(0);
-      }
-#pragma unroll
-      for (int j = 0; j < kPF; j++) {
-        const uint32_t r = r0 + j * nthr + tid;
-        if (r < d.rbeg + d.nr) {
-          uint32_t slot;
-          if (probe_table<KeyT>(rk[j], keys_s, slots, logt, slot)) {
-            acc += cnt[slot];
-            if (CHECKSUM) {
-              const uint32_t rr = R.rid ? R.rid[r] : r;
-              const uint64_t pb = R.ncols > 0 ? pay_bits(R.cols[0], R.width[0], r) : 0ull;
-              csum += term_g(rr, pb) * fsum[slot];
-            }
-          }
-        }
-      }
-    }
-    acc = warp_sum(acc);
-    if (CHECKSUM) csum = warp_sum(csum);
-    if ((tid & 31) == 0) {
-      if (acc) atomicAdd(&totals[0], (unsigned long long)acc);
-      if (CHECKSUM && csum) atomicAdd(&totals[1], (unsigned long long)csum);
-    }
-    __syncthreads();
-  }
-}
-
+// bulk: the build side's staged columns (key, row ids, first payload) have
+// 16-byte-aligned bases, so items stage them by bulk copies.
 template <typename KeyT, bool HAVE_OFFSETS>
 __global__ void __launch_bounds__(kWT, 2)
     k_join_write(JSide L, JSide R, const Item *__restrict__ desc, uint32_t nitems, uint32_t cap, uint32_t *ticket,
                  unsigned long long *state, uint64_t *__restrict__ item_off, unsigned long long *total,
-                 uint64_t capacity, int *flags, int withhold_first, int ordered, JOut out) {
+                 uint64_t capacity, int *flags, int withhold_first, int ordered, int bulk, JOut out) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Item s_item;
   __shared__ uint32_t s_it;
-  __shared__ JoinShared js;
+  __shared__ __align__(8) JoinShared js;
   const uint32_t tid = threadIdx.x;
   const Resv rs = {state, item_off, total, capacity, flags, withhold_first, ordered};
+  uint32_t phase = 0;
   if (tid == 0) {
+    if (bulk) mbar_init(&js.bar, 1);
     s_it = atomicAdd(ticket, 1u);
     if (s_it < nitems) s_item = desc[s_it];
   }
@@ -293,7 +101,7 @@ __global__ void __launch_bounds__(kWT, 2)
       nx = atomicAdd(ticket, 1u);
       if (nx < nitems) dn = desc[nx];
     }
-    join_item<KeyT, HAVE_OFFSETS>(smem, cap, L, R, d, it, rs, out, js);
+    if (!join_item<KeyT, HAVE_OFFSETS>(smem, cap, L, R, d, it, rs, out, js, bulk != 0, phase)) break;
     if (tid == 0) {
       s_it = nx;
       if (nx < nitems) s_item = dn;
@@ -316,6 +124,12 @@ JSide to_jside(const Side &s) {
     j.width[c] = s.widths[c];
   }
   return j;
+}
+
+// The build side's staged columns all start on 16-byte boundaries (bulk copies).
+int bulk_ok(const Side &s) {
+  auto al = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
+  return al(s.key) && (!s.rid || al(s.rid)) && (s.ncols == 0 || al(s.cols[0])) ? 1 : 0;
 }
 
 template <typename KernelT>
@@ -360,33 +174,6 @@ int make_items(Workspace &ws, const Side &Ls, const Side &Rs, uint32_t nb, uint3
     *bucket_items = item_off;
   else
     ws.give_back(item_off);
-  return MDJ_OK;
-}
-
-template <typename KeyT>
-int run_count(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, uint64_t *count, uint64_t *checksum) {
-  cudaStream_t s = ws.stream();
-  Item *desc;
-  uint32_t nitems;
-  const uint32_t cap = plan.cap < kCountCapMax ? plan.cap : kCountCapMax;
-  MDJ_TRY(make_items(ws, Ls, Rs, plan.nbuckets, cap, kCountChunk, &desc, &nitems));
-  unsigned long long *tot = (unsigned long long *)ws.get(32);
-  if (!tot) return MDJ_ERR_OOM;
-  MDJ_CUDA_TRY(cudaMemsetAsync(tot, 0, 32, s));
-  uint32_t *ticket = (uint32_t *)(tot + 2);
-  if (nitems) {
-    const size_t sm = join_smem_bytes<KeyT>(cap, true);
-    int grid;
-    MDJ_TRY(resident_grid(k_join_count<KeyT, true>, sm, nitems, &grid));
-    TraceScope tr("join_checksum", s);
-    k_join_count<KeyT, true><<<grid, kJoinThreads, sm, s>>>(to_jside(Ls), to_jside(Rs), desc, nitems, ticket, tot);
-  }
-  MDJ_LAUNCH_CHECK();
-  unsigned long long host[2] = {0, 0};
-  MDJ_CUDA_TRY(cudaMemcpyAsync(host, tot, 16, cudaMemcpyDeviceToHost, s));
-  MDJ_CUDA_TRY(cudaStreamSynchronize(s));
-  *count = host[0];
-  *checksum = host[1];
   return MDJ_OK;
 }
 
@@ -490,7 +277,7 @@ int run_join(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, md
     TraceScope tr("join_write", s);
     k_join_write<KeyT, false><<<grid, kWT, sm, s>>>(to_jside(Ls), to_jside(Rs), desc, nitems, plan.cap, ticket,
                                                     state, item_off, total, cap_rows, flags, test_withhold_first(),
-                                                    force_ordered ? 1 : ordered_output(), o);
+                                                    force_ordered ? 1 : ordered_output(), bulk_ok(Ls), o);
   }
   cudaError_t e = cudaGetLastError();
   unsigned long long host_total = 0;
@@ -519,7 +306,7 @@ int run_join(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, md
       {
         TraceScope tr("join_write_exact", s);
         k_join_write<KeyT, true><<<grid, kWT, sm, s>>>(to_jside(Ls), to_jside(Rs), desc, nitems, plan.cap, ticket,
-                                                       state, item_off, total, m, flags, 0, 0, o);
+                                                       state, item_off, total, m, flags, 0, 0, bulk_ok(Ls), o);
       }
       e = cudaGetLastError();
       if (e != cudaSuccess) {
@@ -588,6 +375,7 @@ int merge_impl(const mdj_table *left, int32_t lk, const mdj_table *right, int32_
   if (checksum_mode && (!count || !checksum)) return MDJ_ERR_INVALID_ARG;
   if (out) memset(out, 0, sizeof *out);
 
+  if (checksum_mode) return grouped_count_checksum(left, lk, right, rk, P, alloc, stream, count, checksum);
   Workspace ws(alloc, (cudaStream_t)stream);
   Plan plan = make_plan(left->nrows, P, cap_from_env(), P > 1);
   // ordered output is deterministic only over stable partition passes
@@ -596,8 +384,6 @@ int merge_impl(const mdj_table *left, int32_t lk, const mdj_table *right, int32_
   Side L, R;
   MDJ_TRY(partition_side(ws, left, lk, plan, &L));
   MDJ_TRY(partition_side(ws, right, rk, plan, &R));
-  if (checksum_mode)
-    return k64 ? run_count<int64_t>(ws, L, R, plan, count, checksum) : run_count<int32_t>(ws, L, R, plan, count, checksum);
   return k64 ? run_join<int64_t>(ws, L, R, plan, out) : run_join<int32_t>(ws, L, R, plan, out);
 }
 

@@ -327,13 +327,12 @@ __global__ void k_pass1_cursors(const uint32_t *__restrict__ off, uint32_t F1, u
 // overlaps the write-out.  `reg_col` is the non-key column carried in
 // registers (-1: none); with EXTRA, the other non-key columns are loaded and
 // staged one at a time after the first write-out (and the next tile's load
-// waits until they are done).
-template <int NT, typename KeyT, bool PASS2, bool EXTRA>
-__global__ void __launch_bounds__(NT, 1024 / NT)
+// waits until they are done).  Run destinations are reserved on `cursors`.
+template <typename KeyT, bool PASS2, bool EXTRA>
+__global__ void __launch_bounds__(kShNT, 1)
     k_shuffle(const KeyT *__restrict__ keys, uint32_t n, uint32_t ntiles, BucketSpec bs, uint32_t F, uint32_t F2,
-              uint32_t *__restrict__ cursors, ColMove cm, int reg_col, const uint32_t *__restrict__ rid_in,
-              uint32_t *__restrict__ rid_out) {
-  constexpr uint32_t kFTile = shuffle_tile<NT>(), kFSpan = shuffle_span<NT>();
+              uint32_t *__restrict__ cursors, ColMove cm, int reg_col,
+              const uint32_t *__restrict__ rid_in, uint32_t *__restrict__ rid_out) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5;
   const int pw = reg_col >= 0 ? cm.width[reg_col] : 0;
@@ -344,23 +343,23 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
   uint32_t t = blockIdx.x;
   const uint32_t tend = ntiles, tstep = gridDim.x;
   if (t >= tend) return;
-  shuffle_load<KeyT, PASS2>(keys, t * kFTile, min(t * kFTile + kFTile, n), cm, reg_col, pw, rid_in, kv, pv, rv, kfirst,
-                            klast);
-  shuffle_clear_counters<NT>(smem);
+  shuffle_load<KeyT, PASS2>(keys, t * kShTile, min(t * kShTile + kShTile, n), cm, reg_col, pw, rid_in, kv, pv, rv,
+                            kfirst, klast);
+  shuffle_clear_counters(smem);
   __syncthreads();
   int parity = 0;  // counter buffer of the next staged tile
 
   while (t < tend) {
     const uint32_t tn = t + tstep;
-    const uint32_t row0 = t * kFTile, rend = min(row0 + kFTile, n);
-    const uint32_t nrow0 = tn < tend ? tn * kFTile : 0u, nrend = tn < tend ? min(nrow0 + kFTile, n) : 0u;
+    const uint32_t row0 = t * kShTile, rend = min(row0 + kShTile, n);
+    const uint32_t nrow0 = tn < tend ? tn * kShTile : 0u, nrend = tn < tend ? min(nrow0 + kShTile, n) : 0u;
     uint32_t lb0 = 0, Floc = F;
     if (PASS2) {
       const uint32_t b1f = sub_bucket_of(fmix64(key_bits(kfirst)), bs) / F2;
       const uint32_t b1l = sub_bucket_of(fmix64(key_bits(klast)), bs) / F2;
       lb0 = b1f * F2;
       Floc = (b1l - b1f + 1) * F2;
-      if (Floc > kFSpan) {  // uniform over the block: no barrier inside
+      if (Floc > kShSpan) {  // uniform over the block: no barrier inside
         shuffle_direct<KeyT>(keys, row0 + warp * 32 * kRPL, rend, bs, cursors, cm, rid_in, rid_out);
         if (nrow0 < nrend)
           shuffle_load<KeyT, PASS2>(keys, nrow0, nrend, cm, reg_col, pw, rid_in, kv, pv, rv, kfirst, klast);
@@ -368,8 +367,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
         continue;
       }
     }
-    shuffle_one_tile<NT, KeyT, PASS2, EXTRA>(smem, keys, row0, rend, lb0, Floc, bs, cursors, 0u, cm, reg_col, pw,
-                                             rid_in, rid_out, kv, pv, rv, nrow0, nrend, kfirst, klast, parity);
+    shuffle_tile<KeyT, PASS2, EXTRA>(smem, keys, row0, rend, lb0, Floc, bs, cursors, cm, reg_col, pw, rid_in,
+                                     rid_out, kv, pv, rv, nrow0, nrend, kfirst, klast, parity);
     parity ^= 1;
     t = tn;
   }
@@ -546,12 +545,11 @@ template <typename KeyT>
 int set_shuffle_attrs() {
   static PerDeviceOnce once;
   return once_per_device(once, [] {
-    constexpr int NT = kShuffleNT;
-    const int sm = (int)shuffle_smem_bytes<NT>();
-    MDJ_CUDA_TRY(cudaFuncSetAttribute(k_shuffle<NT, KeyT, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    MDJ_CUDA_TRY(cudaFuncSetAttribute(k_shuffle<NT, KeyT, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    MDJ_CUDA_TRY(cudaFuncSetAttribute(k_shuffle<NT, KeyT, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    MDJ_CUDA_TRY(cudaFuncSetAttribute(k_shuffle<NT, KeyT, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    const int sm = (int)ShLayout::total;
+    MDJ_CUDA_TRY(cudaFuncSetAttribute(k_shuffle<KeyT, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    MDJ_CUDA_TRY(cudaFuncSetAttribute(k_shuffle<KeyT, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    MDJ_CUDA_TRY(cudaFuncSetAttribute(k_shuffle<KeyT, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    MDJ_CUDA_TRY(cudaFuncSetAttribute(k_shuffle<KeyT, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
     MDJ_CUDA_TRY(cudaFuncSetAttribute(k_tot<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(kMaxSubBuckets * 4)));
     return (int)MDJ_OK;
@@ -560,37 +558,25 @@ int set_shuffle_attrs() {
 
 template <typename KeyT>
 auto shuffle_kernel(bool pass2, bool extra) {
-  constexpr int NT = kShuffleNT;
-  if (pass2) return extra ? k_shuffle<NT, KeyT, true, true> : k_shuffle<NT, KeyT, true, false>;
-  return extra ? k_shuffle<NT, KeyT, false, true> : k_shuffle<NT, KeyT, false, false>;
+  if (pass2) return extra ? k_shuffle<KeyT, true, true> : k_shuffle<KeyT, true, false>;
+  return extra ? k_shuffle<KeyT, false, true> : k_shuffle<KeyT, false, false>;
 }
 
-// Resident blocks of a k_shuffle launch over ntiles tiles (its grid).
-template <typename KeyT>
-int shuffle_grid(bool pass2, bool extra, uint32_t ntiles, uint32_t *grid) {
-  int per_sm = 0;
-  MDJ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, shuffle_kernel<KeyT>(pass2, extra), kShuffleNT,
-                                                             shuffle_smem_bytes<kShuffleNT>()));
-  if (per_sm < 1) per_sm = 1;
-  const uint32_t full = (uint32_t)(num_sms() * per_sm);
-  *grid = ntiles < full ? ntiles : full;
-  return MDJ_OK;
-}
-
-// One unstable shuffle pass (see k_shuffle) of n rows on `grid` blocks with
+// One unstable shuffle pass (see k_shuffle) of n rows, one block per SM, with
 // run cursors `cur` (pass 1: one per pass-1 bucket; pass 2: one per sub-bucket).
 template <typename KeyT, bool PASS2>
-int shuffle_pass(Workspace &ws, const KeyT *keys, uint32_t n, uint32_t grid, const BucketSpec &bs, uint32_t F,
-                 uint32_t F2, uint32_t *cur, const ColMove &cm, const uint32_t *rid_in, uint32_t *rid_out) {
-  constexpr int NT = kShuffleNT;
-  const uint32_t ntiles = (n + shuffle_tile<NT>() - 1) / shuffle_tile<NT>();
+int shuffle_pass(Workspace &ws, const KeyT *keys, uint32_t n, const BucketSpec &bs, uint32_t F, uint32_t F2,
+                 uint32_t *cur, const ColMove &cm, const uint32_t *rid_in, uint32_t *rid_out) {
+  const uint32_t ntiles = (n + kShTile - 1) / kShTile;
   if (ntiles == 0) return MDJ_OK;
   int reg_col = -1;
   for (int j = 0; j < cm.n && reg_col < 0; j++)
     if (j != cm.key_index) reg_col = j;
+  const uint32_t sms = (uint32_t)num_sms();
+  const uint32_t grid = ntiles < sms ? ntiles : sms;
   TraceScope tr(PASS2 ? "shuffle_pass2" : "shuffle_pass1", ws.stream());
-  shuffle_kernel<KeyT>(PASS2, cm.n > 2)<<<grid, NT, shuffle_smem_bytes<NT>(), ws.stream()>>>(
-      keys, n, ntiles, bs, F, F2, cur, cm, reg_col, rid_in, rid_out);
+  shuffle_kernel<KeyT>(PASS2, cm.n > 2)<<<grid, kShNT, ShLayout::total, ws.stream()>>>(keys, n, ntiles, bs, F, F2, cur,
+                                                                                       cm, reg_col, rid_in, rid_out);
   MDJ_LAUNCH_CHECK();
   return MDJ_OK;
 }
@@ -610,7 +596,6 @@ int shuffle_count_pass1_t(Workspace &ws, const mdj_table *t, int32_t key_col, co
   for (int j = 0; j < t->ncols; j++) src[j] = t->cols[j].data;
   const KeyT *keys = (const KeyT *)src[key_col];
   const BucketSpec sub = make_spec(plan.P, plan.S, 1);
-  const uint32_t ntiles = (n + shuffle_tile<kShuffleNT>() - 1) / shuffle_tile<kShuffleNT>();
 
   MDJ_CUDA_TRY(cudaMemsetAsync(off, 0, (size_t)(nsub + 1) * 4, s));
   MDJ_TRY(alloc_table_bufs(ws, t, out, true));
@@ -636,15 +621,9 @@ int shuffle_count_pass1_t(Workspace &ws, const mdj_table *t, int32_t key_col, co
     k_pass1_cursors<<<(F1 + 255) / 256, 256, 0, s>>>(off, F1, plan.F2, cur);
   }
   MDJ_LAUNCH_CHECK();
-  uint32_t grid1 = 0;
-  MDJ_TRY(shuffle_grid<KeyT>(false, t->ncols > 2, ntiles, &grid1));
   ColMove cm = make_move(t, key_col, src, out->cols);
-  if (plan.F2 == 1) {
-    MDJ_TRY((shuffle_pass<KeyT, false>(ws, keys, n, grid1, sub, nsub, 1, cur, cm, nullptr, out->rid)));
-  } else {
-    MDJ_TRY((shuffle_pass<KeyT, false>(ws, keys, n, grid1, make_spec(plan.P, plan.S, plan.F2), F1, plan.F2, cur, cm,
-                                       nullptr, out->rid)));
-  }
+  const BucketSpec spec1 = plan.F2 == 1 ? sub : make_spec(plan.P, plan.S, plan.F2);
+  MDJ_TRY((shuffle_pass<KeyT, false>(ws, keys, n, spec1, F1, plan.F2, cur, cm, nullptr, out->rid)));
   ws.give_back(cur);
   return MDJ_OK;
 }
@@ -659,15 +638,12 @@ int shuffle_pass2_t(Workspace &ws, const mdj_table *t, int32_t key_col, const Pl
   const uint32_t nsub = plan.nbuckets;
   MDJ_TRY(alloc_table_bufs(ws, t, fin, true));
   if (n == 0) return MDJ_OK;
-  const uint32_t ntiles = (n + shuffle_tile<kShuffleNT>() - 1) / shuffle_tile<kShuffleNT>();
   uint32_t *cur = (uint32_t *)ws.get((size_t)(nsub + 1) * 4);
   if (!cur) return MDJ_ERR_OOM;
   MDJ_CUDA_TRY(cudaMemcpyAsync(cur, off, (size_t)nsub * 4, cudaMemcpyDeviceToDevice, s));
-  uint32_t grid2 = 0;
-  MDJ_TRY(shuffle_grid<KeyT>(true, t->ncols > 2, ntiles, &grid2));
   ColMove cm2 = make_move(t, key_col, p1.cols, fin->cols);
-  MDJ_TRY((shuffle_pass<KeyT, true>(ws, (const KeyT *)p1.cols[key_col], n, grid2, make_spec(plan.P, plan.S, 1), 0,
-                                    plan.F2, cur, cm2, p1.rid, fin->rid)));
+  MDJ_TRY((shuffle_pass<KeyT, true>(ws, (const KeyT *)p1.cols[key_col], n, make_spec(plan.P, plan.S, 1), 0, plan.F2,
+                                    cur, cm2, p1.rid, fin->rid)));
   ws.give_back(cur);
   return MDJ_OK;
 }

@@ -922,11 +922,14 @@ int entries_pass(Workspace &tmp, const EntrySrc &src, const uint64_t *rows0, con
 }
 
 // Groups the build side, probes, and builds the entries into the handle.
+// Groups the build side and finds every probe row's group (steps 2-4 of the
+// open): fills `o` (grouped build rows in `keep`, per-probe-row arrays in
+// `tmp`).  want_gkey: also the grouped keys; keep_left: also the group sizes
+// and hit flags that the unmatched-group entries need.  *err_out: a device
+// word set when a global-table probe sequence ran out (read it after a sync).
 template <typename KeyT>
-int group_and_index(Workspace &tmp, mdj_stream *h, const Side &L, const Side &R, uint32_t nb, int32_t how) {
-  const bool keep_left = how == MDJ_LEFT || how == MDJ_OUTER;
-  const bool keep_right = how == MDJ_RIGHT || how == MDJ_OUTER;
-  Workspace &keep = *h->ws;
+int group_sides(Workspace &tmp, Workspace &keep, const Side &L, const Side &R, uint32_t nb, bool keep_left,
+                bool want_gkey, GOut &o, int **err_out) {
   cudaStream_t s = tmp.stream();
   const uint32_t nL = (uint32_t)L.nrows, nR = (uint32_t)R.nrows;
   std::vector<uint32_t> offL(nb + 1), offR(nb + 1);
@@ -938,7 +941,6 @@ int group_and_index(Workspace &tmp, mdj_stream *h, const Side &L, const Side &R,
   if (un.hslots >= (1ull << 32) - 1) return MDJ_ERR_TOO_LARGE;
 
   // the grouped build side lives as long as the handle
-  GOut o;
   memset(&o, 0, sizeof o);
   o.grid = (uint32_t *)keep.get((size_t)nL * 4);
   if (!o.grid) return MDJ_ERR_OOM;
@@ -949,11 +951,14 @@ int group_and_index(Workspace &tmp, mdj_stream *h, const Side &L, const Side &R,
   int *err = (int *)tmp.get(16);  // [0]: a global-table probe sequence ran out
   if (!o.cnt || !o.gbase || !err) return MDJ_ERR_OOM;
   MDJ_CUDA_TRY(cudaMemsetAsync(err, 0, 16, s));
-  if (keep_left) {
+  if (keep_left || want_gkey) {
     o.gkey = keep.get((size_t)nL * sizeof(KeyT));
+    if (!o.gkey) return MDJ_ERR_OOM;
+  }
+  if (keep_left) {
     o.gsize = (uint32_t *)tmp.get((size_t)nL * 4);
     o.hit = (uint32_t *)tmp.get((size_t)nL * 4);
-    if (!o.gkey || !o.gsize || !o.hit) return MDJ_ERR_OOM;
+    if (!o.gsize || !o.hit) return MDJ_ERR_OOM;
     MDJ_CUDA_TRY(cudaMemsetAsync(o.gsize, 0, (size_t)nL * 4, s));
     MDJ_CUDA_TRY(cudaMemsetAsync(o.hit, 0, (size_t)nL * 4, s));
   }
@@ -1018,6 +1023,20 @@ int group_and_index(Workspace &tmp, mdj_stream *h, const Side &L, const Side &R,
     }
     MDJ_LAUNCH_CHECK();
   }
+  *err_out = err;
+  return MDJ_OK;
+}
+
+template <typename KeyT>
+int group_and_index(Workspace &tmp, mdj_stream *h, const Side &L, const Side &R, uint32_t nb, int32_t how) {
+  const bool keep_left = how == MDJ_LEFT || how == MDJ_OUTER;
+  const bool keep_right = how == MDJ_RIGHT || how == MDJ_OUTER;
+  Workspace &keep = *h->ws;
+  cudaStream_t s = tmp.stream();
+  const uint32_t nL = (uint32_t)L.nrows, nR = (uint32_t)R.nrows;
+  GOut o;
+  int *err = nullptr;
+  MDJ_TRY(group_sides<KeyT>(tmp, keep, L, R, nb, keep_left, false, o, &err));
   // entries: the probe rows (matching ones, or all), then the unmatched groups
   EmitSrc &S = h->src;
   const size_t cap = (size_t)nR + (keep_left ? nL : 0);
@@ -1071,6 +1090,99 @@ int group_and_index(Workspace &tmp, mdj_stream *h, const Side &L, const Side &R,
   }
   return MDJ_OK;
 }
+
+// ------------------------------------------------------ count + checksum
+
+// f of every grouped build position (its key, input row id and first payload)
+template <typename KeyT>
+__global__ void k_count_f(const KeyT *__restrict__ gkey, const uint32_t *__restrict__ grid, const void *gpay, int pw,
+                          uint32_t n, uint64_t *__restrict__ f) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride)
+    f[p] = term_f(key_bits(gkey[p]), grid[p], pay_bits(gpay, pw, p));
+}
+
+// totals[0] += group sizes, totals[1] += g(r) * (F[start + size] - F[start])
+// over probe rows r (F: exclusive prefix sums of f, modulo 2^64)
+__global__ void k_count_probe(const uint32_t *__restrict__ cnt, const uint32_t *__restrict__ gbase,
+                              const uint64_t *__restrict__ F, const uint32_t *__restrict__ rrid, const void *rpay,
+                              int pw, uint32_t n, unsigned long long *totals) {
+  uint64_t acc = 0, csum = 0;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+    const uint32_t c = cnt[r];
+    if (!c) continue;
+    const uint32_t g0 = gbase[r];
+    acc += c;
+    csum += term_g(rrid ? rrid[r] : r, pay_bits(rpay, pw, r)) * (F[g0 + c] - F[g0]);
+  }
+  acc = warp_sum(acc);
+  csum = warp_sum(csum);
+  if ((threadIdx.x & 31) == 0) {
+    if (acc) atomicAdd(&totals[0], (unsigned long long)acc);
+    if (csum) atomicAdd(&totals[1], (unsigned long long)csum);
+  }
+}
+
+template <typename KeyT>
+int grouped_count_t(Workspace &ws, const Side &L, const Side &R, uint32_t nb, uint64_t *count, uint64_t *checksum) {
+  cudaStream_t s = ws.stream();
+  const uint32_t nL = (uint32_t)L.nrows, nR = (uint32_t)R.nrows;
+  GOut o;
+  int *err = nullptr;
+  MDJ_TRY(group_sides<KeyT>(ws, ws, L, R, nb, false, true, o, &err));
+  uint64_t *F = (uint64_t *)ws.get(((size_t)nL + 1) * 8);
+  unsigned long long *tot = (unsigned long long *)ws.get(16);
+  if (!F || !tot) return MDJ_ERR_OOM;
+  MDJ_CUDA_TRY(cudaMemsetAsync(F + nL, 0, 8, s));
+  MDJ_CUDA_TRY(cudaMemsetAsync(tot, 0, 16, s));
+  const unsigned grid = (unsigned)num_sms() * 8;
+  {
+    TraceScope tr("count_f", s);
+    k_count_f<KeyT><<<grid, 256, 0, s>>>((const KeyT *)o.gkey, o.grid, L.ncols ? o.gcols[0] : nullptr,
+                                         L.ncols ? L.widths[0] : 0, nL, F);
+  }
+  MDJ_LAUNCH_CHECK();
+  MDJ_TRY(exclusive_scan_u64(ws, F, F, (size_t)nL + 1));
+  {
+    TraceScope tr("count_probe", s);
+    k_count_probe<<<grid, 256, 0, s>>>(o.cnt, o.gbase, F, R.rid, R.ncols ? R.cols[0] : nullptr,
+                                       R.ncols ? R.widths[0] : 0, nR, tot);
+  }
+  MDJ_LAUNCH_CHECK();
+  unsigned long long host[2] = {0, 0};
+  int herr = 0;
+  MDJ_CUDA_TRY(cudaMemcpyAsync(host, tot, 16, cudaMemcpyDeviceToHost, s));
+  MDJ_CUDA_TRY(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, s));
+  MDJ_CUDA_TRY(cudaStreamSynchronize(s));
+  if (herr) return MDJ_ERR_INTERNAL;
+  *count = host[0];
+  *checksum = host[1];
+  return MDJ_OK;
+}
+
+}  // namespace
+
+int grouped_count_checksum(const mdj_table *left, int32_t lk, const mdj_table *right, int32_t rk, uint32_t P,
+                           const mdj_allocator *alloc, void *stream, uint64_t *count, uint64_t *checksum) {
+  if (!count || !checksum) return MDJ_ERR_INVALID_ARG;
+  MDJ_TRY(validate(left, lk));
+  MDJ_TRY(validate(right, rk));
+  if (P < 1 || P > MDJ_MAX_PARTITIONS) return MDJ_ERR_INVALID_ARG;
+  if (left->cols[lk].dtype != right->cols[rk].dtype) return MDJ_ERR_INVALID_ARG;
+  *count = 0;
+  *checksum = 0;
+  if (left->nrows == 0 || right->nrows == 0) return MDJ_OK;
+  Workspace ws(alloc, (cudaStream_t)stream);
+  const Plan plan = make_plan(left->nrows, P, kGCap, P > 1);
+  Side L, R;
+  MDJ_TRY(partition_side(ws, left, lk, plan, &L));
+  MDJ_TRY(partition_side(ws, right, rk, plan, &R));
+  return left->cols[lk].dtype == MDJ_I64 ? grouped_count_t<int64_t>(ws, L, R, plan.nbuckets, count, checksum)
+                                          : grouped_count_t<int32_t>(ws, L, R, plan.nbuckets, count, checksum);
+}
+
+namespace {
 
 int stream_open(const mdj_table *left, int32_t lk, const mdj_table *right, int32_t rk, uint32_t P, int32_t how,
                 const mdj_allocator *alloc, void *stream, mdj_stream **out, uint64_t *total_rows) {
