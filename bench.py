@@ -360,23 +360,28 @@ def run_gpu(args):
     }
     if host_tables is not None:
         line["host_tables"] = host_tables
-    if args.latency_calls > 0:
-        torch.cuda.empty_cache()
-        line["plain_1M"] = plain_1m_section(args, dev)
     if multi_key is not None:
         line["multi_key"] = multi_key
+
+    def section(name, fn):
+        # a section that fails reports its error in the line instead of
+        # taking the whole line with it
+        try:
+            torch.cuda.empty_cache()
+            line[name] = fn()
+        except Exception as e:  # noqa: BLE001
+            line[name] = {"error": f"{type(e).__name__}: {e}"}
+
+    if args.latency_calls > 0:
+        section("plain_1M", lambda: plain_1m_section(args, dev))
     if args.stream_windows > 0:
-        torch.cuda.empty_cache()
-        line["streamed"] = streamed_section(args, dev)
-        line["streamed"]["plain_workload_one_window"] = stream_plain
+        section("streamed", lambda: dict(streamed_section(args, dev), plain_workload_one_window=stream_plain))
     if args.transpose_steps > 0:
-        torch.cuda.empty_cache()
-        line["transpose_sum"] = transpose_section(args, dev)
+        section("transpose_sum", lambda: transpose_section(args, dev))
     if args.batch_pairs > 0:
-        line["batched"] = batched_section(args, dev)
+        section("batched", lambda: batched_section(args, dev))
     if args.serve_requests > 0:
-        torch.cuda.empty_cache()
-        line["served"] = served_section(args, dev)
+        section("served", lambda: served_section(args, dev))
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample)
     print(json.dumps(line), flush=True)
@@ -423,7 +428,8 @@ def e2e_section(args, dev, hl, hr, m_expect, dist, world):
     # spot check: the host copy holds joined rows (key equals the left key of its left row)
     lk_host = hl[0]
     idx = torch.randint(0, m_expect, (1000,))
-    assert torch.equal(out["key"][idx], lk_host[out["lrow"][idx].view(torch.int32).to(torch.int64) & 0xFFFFFFFF])
+    lrow = out["lrow"].view(torch.int32)[idx].to(torch.int64) & 0xFFFFFFFF
+    assert torch.equal(out["key"][idx], lk_host[lrow])
     h2d = sum(c.numel() * c.element_size() for c in list(hl) + list(hr))
     d2h = sum(t.numel() * t.element_size() for t in out.values())
     return {"value": whole_job_rate(N_LEFT + N_RIGHT, world, dt), "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -722,7 +728,7 @@ def batched_section(args, dev):
     expect = sum(int(np.count_nonzero(p[1][0] < p[0][0].size)) for p in pairs)
     del pairs
     tuner = BatchTuner()
-    tr, fp = tuner.choose(L, R, lo, ro)
+    tr, fp, jt = tuner.choose(L, R, lo, ro)
     stream = torch.cuda.current_stream(dev)
 
     def timed(fn, steps):
@@ -738,7 +744,7 @@ def batched_section(args, dev):
         return e0.elapsed_time(e1) / steps
 
     def batched():
-        res, po = mdj.mdj_join_batch(L, R, lo, ro, 0, 0, tr, fp)
+        res, po = mdj.mdj_join_batch(L, R, lo, ro, 0, 0, tr, fp, jt)
         assert res.nrows == expect
 
     def plain():
@@ -753,7 +759,9 @@ def batched_section(args, dev):
     return {"workload": f"{len(lo) - 1} pairs, sizes log-uniform [1K, 4M] per side, match U[0.1, 0.9], "
                         f"int64 key + float64 payload, {rows} input rows, {expect} output rows",
             "batched": {"value": rows / (ms_b / 1e3), "unit": UNIT, "ms_per_batch": round(ms_b, 3),
-                        "tuning": {"table_rows": tr, "fill_pct": fp}},
+                        "tuning": {"table_rows": tr, "fill_pct": fp, "join_threads": jt,
+                                   "searched": "table rows {2048, 4096, 8192} x fill {60, 75, 85, 95}% x "
+                                               "join block {256, 512} threads, timed on this batch"}},
             "plain_per_pair": {"value": rows / (ms_p / 1e3), "unit": UNIT, "ms_per_batch": round(ms_p, 3)},
             "speedup": round(ms_p / ms_b, 3)}
 
@@ -878,7 +886,8 @@ def _canonical(res):
     order = torch.argsort(res.right_row.view(torch.int32).to(torch.int64) & 0xFFFFFFFF, stable=True)
     for col in (res.left_row.view(torch.int32).to(torch.int64) & 0xFFFFFFFF, res.key.to(torch.int64)):
         order = order[torch.argsort(col[order], stable=True)]
-    return [t[order] for t in [res.key, res.left_row, res.right_row, *res.left_cols, *res.right_cols]]
+    as_indexable = (lambda t: t.view(torch.int32) if t.dtype == torch.uint32 else t)
+    return [as_indexable(t)[order] for t in [res.key, res.left_row, res.right_row, *res.left_cols, *res.right_cols]]
 
 
 def served_canonical_check(work, dev, max_batch_rows, groups: int = 8, per_group: int = 4):

@@ -208,11 +208,13 @@ MDJ_API int mdj_count_checksum(const mdj_table *left, int32_t left_key, const md
                        int32_t right_key, uint32_t P, const mdj_allocator *alloc, void *stream,
                        uint64_t *count, uint64_t *checksum);
 
-/* Tuning of the join tables (0 in a field = default). */
+/* Tuning of the join tables and blocks (0 in a field = default). */
 typedef struct {
-    uint32_t table_rows;  /* build rows per shared-memory hash table, 256..8192 (default 4096) */
-    uint32_t fill_pct;    /* target mean build rows per bucket, percent of table_rows, 10..100 (default 85) */
-    uint32_t reserved[6];
+    uint32_t table_rows;    /* build rows per shared-memory hash table, 256..8192 (default 4096) */
+    uint32_t fill_pct;      /* target mean build rows per bucket, percent of table_rows, 10..100 (default 85) */
+    uint32_t join_threads;  /* threads of a join block, 256 or 512 (default 512); each item probes
+                               8 rows per thread, so this also sets the probe rows per item */
+    uint32_t reserved[5];
 } mdj_tuning;
 
 /*

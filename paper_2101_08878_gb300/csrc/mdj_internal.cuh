@@ -305,6 +305,7 @@ struct Plan {
   bool partition = true; // false: no partitioning at all (P = 1, small build side)
   bool stable = false;   // stable passes (rows keep input order in a bucket)
   uint32_t cap = 4096;   // build rows per shared-memory table
+  uint32_t join_threads = 512;  // threads of a join block (256 or 512); probe rows per item = 8x
 };
 
 Plan make_plan(uint64_t n_build, uint32_t P, uint32_t cap, bool force_partition);

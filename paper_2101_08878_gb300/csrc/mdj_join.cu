@@ -72,8 +72,8 @@ __global__ void k_expand(const uint32_t *__restrict__ offL, const uint32_t *__re
 
 // bulk: the build side's staged columns (key, row ids, first payload) have
 // 16-byte-aligned bases, so items stage them by bulk copies.
-template <typename KeyT, bool HAVE_OFFSETS>
-__global__ void __launch_bounds__(kWT, 2)
+template <typename KeyT, bool HAVE_OFFSETS, int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT)
     k_join_write(JSide L, JSide R, const Item *__restrict__ desc, uint32_t nitems, uint32_t cap, uint32_t *ticket,
                  unsigned long long *state, uint64_t *__restrict__ item_off, unsigned long long *total,
                  uint64_t capacity, int *flags, int withhold_first, int ordered, int bulk, JOut out) {
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kWT, 2)
       nx = atomicAdd(ticket, 1u);
       if (nx < nitems) dn = desc[nx];
     }
-    if (!join_item<KeyT, HAVE_OFFSETS>(smem, cap, L, R, d, it, rs, out, js, bulk != 0, phase)) break;
+    if (!join_item<KeyT, HAVE_OFFSETS, NT>(smem, cap, L, R, d, it, rs, out, js, bulk != 0, phase)) break;
     if (tid == 0) {
       s_it = nx;
       if (nx < nitems) s_item = dn;
@@ -242,8 +242,8 @@ struct ItemMap {
   uint32_t nitems = 0;
 };
 
-template <typename KeyT>
-int run_join(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, mdj_result *res,
+template <typename KeyT, int NT>
+int run_join_t(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, mdj_result *res,
              bool force_ordered = false, ItemMap *map = nullptr) {
   cudaStream_t s = ws.stream();
   // the optimistic output buffer first: its allocation overlaps the device
@@ -254,7 +254,7 @@ int run_join(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, md
   MDJ_TRY(alloc_result(ws, Ls, Rs, sizeof(KeyT), cap_rows, &r, &o));
   Item *desc;
   uint32_t nitems;
-  int rc = make_items(ws, Ls, Rs, plan.nbuckets, plan.cap, kWriteChunk, &desc, &nitems,
+  int rc = make_items(ws, Ls, Rs, plan.nbuckets, plan.cap, (uint32_t)kWPF * NT, &desc, &nitems,
                       map ? &map->bucket_items : nullptr);
   // state[nitems] | item_off[nitems] | total | ticket | flags
   const size_t words = 2 * (size_t)nitems + 4;
@@ -273,9 +273,9 @@ int run_join(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, md
   const size_t sm = WriteLayout<KeyT>(plan.cap).total;  // ~105 KB at cap 4096: two blocks per SM
   if (nitems) {
     int grid;
-    MDJ_TRY(resident_grid(k_join_write<KeyT, false>, sm, nitems, &grid, kWT));
+    MDJ_TRY(resident_grid(k_join_write<KeyT, false, NT>, sm, nitems, &grid, NT));
     TraceScope tr("join_write", s);
-    k_join_write<KeyT, false><<<grid, kWT, sm, s>>>(to_jside(Ls), to_jside(Rs), desc, nitems, plan.cap, ticket,
+    k_join_write<KeyT, false, NT><<<grid, NT, sm, s>>>(to_jside(Ls), to_jside(Rs), desc, nitems, plan.cap, ticket,
                                                     state, item_off, total, cap_rows, flags, test_withhold_first(),
                                                     force_ordered ? 1 : ordered_output(), bulk_ok(Ls), o);
   }
@@ -301,11 +301,11 @@ int run_join(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, md
     MDJ_TRY(alloc_result(ws, Ls, Rs, sizeof(KeyT), m, &r, &o));
     if (m > 0) {
       int grid;
-      MDJ_TRY(resident_grid(k_join_write<KeyT, true>, sm, nitems, &grid, kWT));
+      MDJ_TRY(resident_grid(k_join_write<KeyT, true, NT>, sm, nitems, &grid, NT));
       MDJ_CUDA_TRY(cudaMemsetAsync(ticket, 0, 4, s));
       {
         TraceScope tr("join_write_exact", s);
-        k_join_write<KeyT, true><<<grid, kWT, sm, s>>>(to_jside(Ls), to_jside(Rs), desc, nitems, plan.cap, ticket,
+        k_join_write<KeyT, true, NT><<<grid, NT, sm, s>>>(to_jside(Ls), to_jside(Rs), desc, nitems, plan.cap, ticket,
                                                        state, item_off, total, m, flags, 0, 0, bulk_ok(Ls), o);
       }
       e = cudaGetLastError();
@@ -322,6 +322,13 @@ int run_join(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, md
     map->nitems = nitems;
   }
   return MDJ_OK;
+}
+
+template <typename KeyT>
+int run_join(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, mdj_result *res,
+             bool force_ordered = false, ItemMap *map = nullptr) {
+  if (plan.join_threads == 256) return run_join_t<KeyT, 256>(ws, Ls, Rs, plan, res, force_ordered, map);
+  return run_join_t<KeyT, kWT>(ws, Ls, Rs, plan, res, force_ordered, map);
 }
 
 // pair_off[i] = output offset of pair i's first item (or of the next pair's,
@@ -410,7 +417,12 @@ int batch_impl(const mdj_table *left, int32_t left_key, const uint64_t *left_off
   memset(out, 0, sizeof *out);
   uint32_t cap = cap_from_env();
   uint32_t fill = 85;
+  uint32_t join_threads = kWT;
   if (tuning) {
+    if (tuning->join_threads) {
+      if (tuning->join_threads != 256 && tuning->join_threads != 512) return MDJ_ERR_INVALID_ARG;
+      join_threads = tuning->join_threads;
+    }
     if (tuning->table_rows) {
       if (tuning->table_rows < 256 || tuning->table_rows > kMaxCap) return MDJ_ERR_INVALID_ARG;
       cap = tuning->table_rows;
@@ -446,6 +458,7 @@ int batch_impl(const mdj_table *left, int32_t left_key, const uint64_t *left_off
   plan.P = 1;
   plan.nbuckets = (uint32_t)nb;
   plan.cap = cap;
+  plan.join_threads = join_threads;
   ItemMap map;
   const bool k64 = left->cols[left_key].dtype == MDJ_I64;
   MDJ_TRY(k64 ? run_join<int64_t>(ws, L, R, plan, out, true, &map) : run_join<int32_t>(ws, L, R, plan, out, true, &map));

@@ -111,9 +111,9 @@ __device__ uint64_t look_back(unsigned long long *state, uint32_t it, uint64_t t
 //      values from shared memory, probe-side from registers.
 // The next item's ticket and descriptor are fetched while the current one runs.
 
-constexpr int kWT = 512;                        // threads of the write block
+constexpr int kWT = 512;                        // threads of the write block (default; 256 also built)
 constexpr int kWPF = 8;                         // probe rows per thread
-constexpr int kWW = kWT / 32;                   // warps of the write block
+constexpr int kWW = kWT / 32;                   // warps of the largest write block
 static_assert(kWPF * kWT == (int)kWriteChunk, "probe chunk = one round");
 constexpr uint64_t kStageWaitNs = 1000000000ull;  // bulk-copy wait bound: 1 s of device time
 
@@ -287,10 +287,11 @@ struct Resv {
 // `phase` is the mbarrier's phase, kept by every thread.  Leaves every thread
 // past the write, with no barrier after it; returns false if a bulk-copy
 // wait ran out (FLAG_TIMEOUT and FLAG_ABORT are then set).
-template <typename KeyT, bool HAVE_OFFSETS>
+template <typename KeyT, bool HAVE_OFFSETS, int NT>
 __device__ __forceinline__ bool join_item(unsigned char *smem, uint32_t cap, const JSide &L, const JSide &R,
                                           const Item &d, uint32_t it, const Resv &rs, const JOut &out,
                                           JoinShared &js, bool bulk, uint32_t &phase) {
+  constexpr int kWT = NT, kWW = NT / 32;  // this block's threads and warps
   const WriteLayout<KeyT> lay(cap);
   const KeyT *__restrict__ Lkey = (const KeyT *)L.key;
   const KeyT *__restrict__ Rkey = (const KeyT *)R.key;

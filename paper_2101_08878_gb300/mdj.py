@@ -91,7 +91,8 @@ SINK_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(MdjResult), ctypes.c_uin
 
 
 class MdjTuning(ctypes.Structure):
-    _fields_ = [("table_rows", ctypes.c_uint32), ("fill_pct", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 6)]
+    _fields_ = [("table_rows", ctypes.c_uint32), ("fill_pct", ctypes.c_uint32), ("join_threads", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 5)]
 
 
 _lib = None
@@ -349,7 +350,7 @@ def mdj_count_checksum(left_cols: Sequence[torch.Tensor], right_cols: Sequence[t
 
 def mdj_join_batch(left_cols: Sequence[torch.Tensor], right_cols: Sequence[torch.Tensor], left_offsets,
                    right_offsets, left_key: int = 0, right_key: int = 0, table_rows: int = 0,
-                   fill_pct: int = 0):
+                   fill_pct: int = 0, join_threads: int = 0):
     """Independent joins of pair i = left rows [left_offsets[i], left_offsets[i+1])
     with right rows [right_offsets[i], right_offsets[i+1]) (see mdj.h).
 
@@ -367,7 +368,7 @@ def mdj_join_batch(left_cols: Sequence[torch.Tensor], right_cols: Sequence[torch
     lo_c = (ctypes.c_uint64 * len(lo))(*lo)
     ro_c = (ctypes.c_uint64 * len(ro))(*ro)
     po_c = (ctypes.c_uint64 * len(lo))()
-    tun = MdjTuning(table_rows, fill_pct)
+    tun = MdjTuning(table_rows, fill_pct, join_threads)
     alloc = TorchAllocator(dev)
     res = MdjResult()
     rc = lib.mdj_join_batch(ctypes.byref(lt), left_key, lo_c, ctypes.byref(rt), right_key, ro_c, npairs,
@@ -379,7 +380,7 @@ def mdj_join_batch(left_cols: Sequence[torch.Tensor], right_cols: Sequence[torch
 
 def mdj_merge_batch(left_cols: Sequence[torch.Tensor], right_cols: Sequence[torch.Tensor], left_offsets,
                     right_offsets, P, left_key: int = 0, right_key: int = 0, table_rows: int = 0,
-                    fill_pct: int = 0):
+                    fill_pct: int = 0, join_threads: int = 0):
     """Independent merges: request i = left rows [left_offsets[i], left_offsets[i+1])
     and right rows [right_offsets[i], right_offsets[i+1]), shuffled into P[i]
     partitions and joined (see mdj.h).  Returns (JoinResult, req_offsets)."""
@@ -397,7 +398,7 @@ def mdj_merge_batch(left_cols: Sequence[torch.Tensor], right_cols: Sequence[torc
     ro_c = (ctypes.c_uint64 * len(ro))(*ro)
     p_c = (ctypes.c_uint32 * nreq)(*pp)
     out_c = (ctypes.c_uint64 * len(lo))()
-    tun = MdjTuning(table_rows, fill_pct)
+    tun = MdjTuning(table_rows, fill_pct, join_threads)
     alloc = TorchAllocator(dev)
     res = MdjResult()
     rc = lib.mdj_merge_batch(ctypes.byref(lt), left_key, lo_c, ctypes.byref(rt), right_key, ro_c, nreq, p_c,

@@ -164,6 +164,25 @@ def test_merge_batch_rejects_bad_P():
             mdj.mdj_merge_batch([k], [k], [0, 10], [0, 10], bad)
 
 
+@pytest.mark.parametrize("jt", [256, 512])
+def test_join_block_shapes_give_the_same_rows(jt):
+    # the tuner's block-shape knob: 256- and 512-thread join blocks (2048 and
+    # 4096 probe rows per item) give the same rows per pair as one join per pair
+    pairs = [datagen.match_fraction_tables(n, m, 0.4, seed=n) for n, m in ((3_000, 9_000), (50_000, 20_000),
+                                                                           (7_000, 70_000))]
+    (lk, lp), (rk, rp), lo, ro = _concat(pairs)
+    mdj = _mdj()
+    L = [torch.from_numpy(lk).to(DEV), torch.from_numpy(lp).to(DEV)]
+    R = [torch.from_numpy(rk).to(DEV), torch.from_numpy(rp).to(DEV)]
+    res, po = mdj.mdj_join_batch(L, R, lo, ro, 0, 0, 2048, 60, jt)
+    for i, ((a, b), (c, d)) in enumerate(pairs):
+        want = oracle.merge_table([a, b], [c, d])
+        assert po[i + 1] - po[i] == want["key"].size
+    with pytest.raises(mdj.MdjError) as e:
+        mdj.mdj_join_batch(L, R, lo, ro, 0, 0, 0, 0, 384)
+    assert e.value.status == -1
+
+
 def test_tuner_picks_and_caches(tmp_path):
     from paper_2101_08878_gb300.tuner import BatchTuner
     pairs = [datagen.match_fraction_tables(n, n, 0.5, seed=n) for n in (20_000, 80_000)]
@@ -174,7 +193,7 @@ def test_tuner_picks_and_caches(tmp_path):
     t = BatchTuner(path)
     assert t.lookup(L[0].dtype, int(lo[-1]), 2) is None
     best = t.choose(L, R, lo, ro)
-    assert best[0] in (2048, 4096, 8192) and best[1] in (60, 75, 85, 95)
+    assert best[0] in (2048, 4096, 8192) and best[1] in (60, 75, 85, 95) and best[2] in (256, 512)
     again = BatchTuner(path)  # reloaded from the cache file
     assert again.lookup(L[0].dtype, int(lo[-1]), 2) == best
     assert again.choose(L, R, lo, ro, search=False) == best
