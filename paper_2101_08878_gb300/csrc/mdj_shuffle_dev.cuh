@@ -61,8 +61,9 @@ __device__ void scatter_direct(const KeyT (&kv)[kRPL], uint32_t wrow0, uint32_t 
 // at most kShSpan local buckets per tile.  Shared memory per block:
 //   rec    [kShTile]  16 bytes: key bits, first non-key column (bucket order)
 //   meta   [kShTile]   4 bytes: pass 1: (row in tile << 10) | local bucket;
-//                               pass 2: the row id
-//   lbk    [kShTile]   2 bytes: pass 2: the local bucket
+//                               pass 2: the row id (the local bucket is
+//                               recomputed from the key at write-out: cheaper
+//                               than staging it, measured)
 //   cnt    [2][kShSpan] rank counters (two buffers, alternating tiles)
 //   lst    [kShSpan]   local start of each bucket in the staged tile
 //   gdelta [kShSpan]   destination - staged position, per bucket
@@ -76,8 +77,7 @@ static_assert(kShTile <= (1u << 22), "pass-1 metadata keeps the row in tile in 2
 struct ShLayout {
   static constexpr size_t rec = 0;
   static constexpr size_t meta = rec + (size_t)kShTile * 16;
-  static constexpr size_t lbk = meta + (size_t)kShTile * 4;
-  static constexpr size_t cnt = lbk + (size_t)kShTile * 2;
+  static constexpr size_t cnt = meta + (size_t)kShTile * 4;
   static constexpr size_t lst = cnt + (size_t)2 * kShSpan * 4;
   static constexpr size_t gdelta = lst + (size_t)kShSpan * 4;
   static constexpr size_t wsum = gdelta + (size_t)kShSpan * 4;
@@ -151,7 +151,6 @@ __device__ __forceinline__ void shuffle_tile(unsigned char *smem, const KeyT *__
                                              int parity) {
   ulonglong2 *rec = (ulonglong2 *)(smem + ShLayout::rec);
   uint32_t *meta = (uint32_t *)(smem + ShLayout::meta);
-  uint16_t *lbk = (uint16_t *)(smem + ShLayout::lbk);
   uint32_t *cnt = (uint32_t *)(smem + ShLayout::cnt) + (size_t)parity * kShSpan;
   uint32_t *cnt_next = (uint32_t *)(smem + ShLayout::cnt) + (size_t)(1 - parity) * kShSpan;
   uint32_t *lst = (uint32_t *)(smem + ShLayout::lst);
@@ -201,7 +200,6 @@ __device__ __forceinline__ void shuffle_tile(unsigned char *smem, const KeyT *__
       memcpy(&kb, &kv[c], sizeof(KeyT));
       rec[lp] = make_ulonglong2(kb, pv[c]);
       meta[lp] = PASS2 ? rv[c] : (((wl0 + c * 32 + lane) << 10) | lb);
-      if (PASS2) lbk[lp] = (uint16_t)lb;
     }
   }
   if (b < Floc) gdelta[b] = gb - ex;
@@ -216,7 +214,7 @@ __device__ __forceinline__ void shuffle_tile(unsigned char *smem, const KeyT *__
     const uint32_t m = meta[i];
     KeyT k;
     memcpy(&k, &r.x, sizeof(KeyT));
-    const uint32_t lb = PASS2 ? lbk[i] : (m & 0x3FFu);
+    const uint32_t lb = PASS2 ? sub_bucket_of(fmix64(key_bits(k)), bs) - lb0 : (m & 0x3FFu);
     const uint32_t d = i + gdelta[lb];
     kdst[d] = k;
     if (pw == 8) ((uint64_t *)cm.dst[reg_col])[d] = r.y;
@@ -245,7 +243,7 @@ __device__ __forceinline__ void shuffle_tile(unsigned char *smem, const KeyT *__
         const ulonglong2 r = rec[i];
         KeyT k;
         memcpy(&k, &r.x, sizeof(KeyT));
-        const uint32_t lb = PASS2 ? lbk[i] : (meta[i] & 0x3FFu);
+        const uint32_t lb = PASS2 ? sub_bucket_of(fmix64(key_bits(k)), bs) - lb0 : (meta[i] & 0x3FFu);
         const uint32_t d = i + gdelta[lb];
         if (w == 8)
           ((uint64_t *)cm.dst[j])[d] = r.y;
