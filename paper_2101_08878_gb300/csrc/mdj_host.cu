@@ -5,19 +5,33 @@
 //
 // Phase 1, per side: the host table goes to the device chunk by chunk, each
 // chunk is hash partitioned into B buckets (mdj_partition: h mod B, stable),
-// and each bucket's slice returns to host storage with the rows' global row
-// ids.  Equal keys land in the same bucket on both sides.
-// Phase 2, per bucket: both sides' bucket b go to the device, their merge is
-// opened as a stream (mdj_stream_open, any join type), and its rows are
-// written window by window into one device buffer; each window's row ids are
-// mapped back to the input tables and handed to the caller's sink.
+// its row ids are made input row ids, and the partitioned chunk returns to
+// a host staging area (one array per column, chunks in order) with its
+// bucket offsets.  Chunk c's copy back runs on a second stream while chunk
+// c + 1 is copied in and partitioned (two output buffer sets; every
+// allocation stays on the caller's stream).
+// Phase 2, per bucket: both sides' bucket b (its slice of every chunk) go to
+// the device, their merge is opened as a stream (mdj_stream_open, any join
+// type), and its rows are written window by window into one device buffer;
+// each window's row ids are mapped back to the input tables and handed to the
+// caller's sink.  Equal keys land in the same bucket on both sides.
+//
+// Host <-> device movement: where the device reads and writes pageable host
+// memory through the host's page tables (a coherent CPU-GPU link), copies run
+// as kernels, which never block the host thread and gather many slices per
+// launch; elsewhere they are cudaMemcpyAsync calls.  The staging area's pages
+// are touched by host threads before the device writes them (a device write
+// that faults a page in costs far more than a host first touch).
 //
 // B and the chunk and window sizes come from the caller's device budget, so
 // device memory stays bounded whatever the table sizes; a single key whose
 // rows exceed a bucket's share of the budget gives MDJ_ERR_OOM.
+#include <stdlib.h>
 #include <string.h>
+#include <unistd.h>
 
 #include <algorithm>
+#include <thread>
 #include <vector>
 
 #include "mdj_internal.cuh"
@@ -36,91 +50,267 @@ __global__ void k_map_rows(uint32_t *__restrict__ rows, uint64_t n, const uint32
   }
 }
 
-// One side's buckets in host memory: per bucket, every column's bytes and
-// the global row ids, in bucket order.
-struct HostBuckets {
-  std::vector<std::vector<std::vector<unsigned char>>> cols;  // [bucket][column]
-  std::vector<std::vector<uint32_t>> rid;                     // [bucket]
+// Chunk-local row ids to input row ids.
+__global__ void k_add_rows(uint32_t *__restrict__ rows, uint64_t n, uint32_t base) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) rows[i] += base;
+}
+
+// ---- copies between host and device memory
+
+// One contiguous copy; a launch carries up to kMaxSegs of them.
+struct Seg {
+  const unsigned char *src;
+  unsigned char *dst;
+  uint64_t bytes;
 };
+constexpr int kMaxSegs = 96;
+struct SegList {
+  Seg seg[kMaxSegs];
+  int n;
+};
+
+// Block row y copies segment y: 16-byte words when both ends and the size
+// allow, else bytes.  Grid-stride over the segment in x.
+__global__ void __launch_bounds__(512) k_copy_segs(SegList L) {
+  const Seg sg = L.seg[blockIdx.y];
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if ((((uintptr_t)sg.src | (uintptr_t)sg.dst | sg.bytes) & 15) == 0) {
+    const uint4 *__restrict__ s = (const uint4 *)sg.src;
+    uint4 *__restrict__ d = (uint4 *)sg.dst;
+    const uint64_t n = sg.bytes >> 4;
+    uint64_t i = t0;
+    for (; i + 3 * stride < n; i += 4 * stride) {  // four loads in flight per thread
+      const uint4 a = s[i], b = s[i + stride], c = s[i + 2 * stride], e = s[i + 3 * stride];
+      d[i] = a;
+      d[i + stride] = b;
+      d[i + 2 * stride] = c;
+      d[i + 3 * stride] = e;
+    }
+    for (; i < n; i += stride) d[i] = s[i];
+  } else {
+    for (uint64_t i = t0; i < sg.bytes; i += stride) sg.dst[i] = sg.src[i];
+  }
+}
+
+// The device reads and writes pageable host memory directly (and coherently).
+// MDJ_TEST_HOST_MEMCPY=1 (test hook) takes the cudaMemcpyAsync path anyway.
+bool direct_host_access() {
+  const char *e = getenv("MDJ_TEST_HOST_MEMCPY");
+  if (e && e[0] == '1') return false;
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess) return false;
+  return v == 1;
+}
+
+// Issues copies between host and device memory on `s`: batched into copy
+// kernels when `direct`, else one cudaMemcpyAsync each (kind cudaMemcpyDefault).
+class Copier {
+ public:
+  Copier(bool direct, cudaStream_t s) : direct_(direct), s_(s) { L_.n = 0; }
+  int add(void *dst, const void *src, uint64_t bytes) {
+    if (!bytes) return MDJ_OK;
+    if (!direct_) return cuda_status(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s_));
+    L_.seg[L_.n++] = {(const unsigned char *)src, (unsigned char *)dst, bytes};
+    total_ += bytes;
+    return L_.n == kMaxSegs ? flush() : MDJ_OK;
+  }
+  int flush() {
+    if (!L_.n) return MDJ_OK;
+    // ~64 KB per block in flight; a link-bound copy needs few SMs
+    const uint64_t per = total_ / L_.n;
+    unsigned bx = (unsigned)std::min<uint64_t>(std::max<uint64_t>(per >> 16, 1), 64);
+    while (bx > 1 && (uint64_t)bx * L_.n > 256) bx /= 2;
+    k_copy_segs<<<dim3(bx, L_.n), 512, 0, s_>>>(L_);
+    L_.n = 0;
+    total_ = 0;
+    return cuda_status(cudaGetLastError());
+  }
+
+ private:
+  bool direct_;
+  cudaStream_t s_;
+  SegList L_;
+  uint64_t total_ = 0;
+};
+
+// Touch every page of [p, p + bytes) once, from several host threads (this
+// thread alone when they cannot be started).
+void touch_pages(unsigned char *p, size_t bytes) {
+  const long pg = sysconf(_SC_PAGESIZE);
+  const size_t page = pg > 0 ? (size_t)pg : 4096;
+  const size_t pages = (bytes + page - 1) / page;
+  auto run = [p, page](size_t lo, size_t hi) {
+    volatile unsigned char *v = p;
+    for (size_t q = lo; q < hi; q++) v[q * page] = 0;
+  };
+  unsigned nt = std::max(1u, std::min(std::thread::hardware_concurrency(), 16u));
+  if (bytes < (64u << 20)) nt = 1;
+  std::vector<std::thread> th;
+  size_t started = 1;  // thread t touches pages [pages * t / nt, pages * (t + 1) / nt)
+  try {
+    for (unsigned t = 1; t < nt; t++, started++) th.emplace_back(run, pages * t / nt, pages * (t + 1) / nt);
+  } catch (...) {
+  }
+  run(0, pages / nt);
+  run(pages * started / nt, pages);  // ranges of threads that did not start
+  for (auto &t : th) t.join();
+}
+
+// One side's buckets in host memory: the partitioned chunks in chunk order,
+// each column (and the input row ids) as one array of nrows elements; chunk c
+// holds rows [c * chunk_rows, ...) and offs[c * (B + 1) + b] is the start of
+// its bucket b, relative to the chunk.
+struct HostStage {
+  unsigned char *mem = nullptr;
+  unsigned char *col[MDJ_MAX_COLS] = {};
+  uint32_t *rid = nullptr;
+  std::vector<int64_t> offs;
+  uint64_t chunk_rows = 0, nchunks = 0;
+  HostStage() = default;
+  HostStage(const HostStage &) = delete;
+  HostStage &operator=(const HostStage &) = delete;
+  ~HostStage() { free(mem); }
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // A device block for `bytes`, freed by the owning workspace.
 unsigned char *dev_block(Workspace &ws, size_t bytes) { return (unsigned char *)ws.get(bytes ? bytes : 1); }
 
 int partition_to_host(const mdj_table *t, int32_t key_col, uint32_t B, uint64_t chunk_rows, const mdj_allocator *alloc,
-                      cudaStream_t s, HostBuckets *hb) {
+                      cudaStream_t s, bool direct, HostStage *hs) {
   const int nc = t->ncols;
   int w[MDJ_MAX_COLS];
   for (int j = 0; j < nc; j++) w[j] = dtype_width(t->cols[j].dtype);
-  hb->cols.assign(B, std::vector<std::vector<unsigned char>>(nc));
-  hb->rid.assign(B, {});
   const uint64_t n = t->nrows;
-  if (n == 0) return MDJ_OK;
-  const uint64_t C = std::min<uint64_t>(chunk_rows, n);
-  Workspace ws(alloc, s);
-  unsigned char *din[MDJ_MAX_COLS], *dout[MDJ_MAX_COLS];
-  for (int j = 0; j < nc; j++) {
-    din[j] = dev_block(ws, C * w[j]);
-    dout[j] = dev_block(ws, C * w[j]);
-    if (!din[j] || !dout[j]) return MDJ_ERR_OOM;
+  if (n == 0) {
+    hs->nchunks = 0;
+    return MDJ_OK;
   }
-  uint32_t *drid = (uint32_t *)dev_block(ws, C * 4);
-  int64_t *doff = (int64_t *)dev_block(ws, (size_t)(B + 1) * 8);
-  if (!drid || !doff) return MDJ_ERR_OOM;
-  std::vector<int64_t> off(B + 1);
-  std::vector<uint32_t> rbuf;
-  for (uint64_t c0 = 0; c0 < n; c0 += C) {
-    const uint64_t cnt = std::min(C, n - c0);
+  const uint64_t C = std::min<uint64_t>(chunk_rows, n);
+  const uint64_t nchunks = (n + C - 1) / C;
+  hs->chunk_rows = C;
+  hs->nchunks = nchunks;
+  hs->offs.assign(nchunks * (B + 1), 0);
+  size_t bytes = align256((size_t)n * 4);
+  for (int j = 0; j < nc; j++) bytes += align256((size_t)n * w[j]);
+  hs->mem = (unsigned char *)malloc(bytes);
+  if (!hs->mem) return MDJ_ERR_OOM;
+  touch_pages(hs->mem, bytes);
+  size_t at = 0;
+  for (int j = 0; j < nc; j++) {
+    hs->col[j] = hs->mem + at;
+    at += align256((size_t)n * w[j]);
+  }
+  hs->rid = (uint32_t *)(hs->mem + at);
+
+  Workspace ws(alloc, s);
+  unsigned char *din[MDJ_MAX_COLS], *dout[2][MDJ_MAX_COLS];
+  uint32_t *drid[2];
+  int64_t *doff[2];
+  for (int j = 0; j < nc; j++)
+    if (!(din[j] = dev_block(ws, C * w[j]))) return MDJ_ERR_OOM;
+  for (int k = 0; k < 2; k++) {
+    for (int j = 0; j < nc; j++)
+      if (!(dout[k][j] = dev_block(ws, C * w[j]))) return MDJ_ERR_OOM;
+    drid[k] = (uint32_t *)dev_block(ws, C * 4);
+    doff[k] = (int64_t *)dev_block(ws, (size_t)(B + 1) * 8);
+    if (!drid[k] || !doff[k]) return MDJ_ERR_OOM;
+  }
+  // copy-back stream and its events; freed on every path
+  struct Side2 {
+    cudaStream_t sc = nullptr;
+    cudaEvent_t ready[2] = {nullptr, nullptr}, done[2] = {nullptr, nullptr};
+    ~Side2() {
+      for (int k = 0; k < 2; k++) {
+        if (ready[k]) cudaEventDestroy(ready[k]);
+        if (done[k]) cudaEventDestroy(done[k]);
+      }
+      if (sc) cudaStreamDestroy(sc);
+    }
+  } x;
+  MDJ_CUDA_TRY(cudaStreamCreateWithFlags(&x.sc, cudaStreamNonBlocking));
+  for (int k = 0; k < 2; k++) {
+    MDJ_CUDA_TRY(cudaEventCreateWithFlags(&x.ready[k], cudaEventDisableTiming));
+    MDJ_CUDA_TRY(cudaEventCreateWithFlags(&x.done[k], cudaEventDisableTiming));
+  }
+  Copier in(direct, s), back(direct, x.sc);
+  int rc = MDJ_OK;
+  for (uint64_t c = 0; c < nchunks && rc == MDJ_OK; c++) {
+    const int k = (int)(c & 1);
+    const uint64_t c0 = c * C, cnt = std::min(C, n - c0);
+    if (c >= 2) rc = cuda_status(cudaStreamWaitEvent(s, x.done[k], 0));  // chunk c - 2's copy back is done
     mdj_col cols[MDJ_MAX_COLS];
     void *outs[MDJ_MAX_COLS];
-    for (int j = 0; j < nc; j++) {
-      MDJ_CUDA_TRY(cudaMemcpyAsync(din[j], (const unsigned char *)t->cols[j].data + c0 * w[j], cnt * w[j],
-                                   cudaMemcpyHostToDevice, s));
+    for (int j = 0; j < nc && rc == MDJ_OK; j++) {
+      rc = in.add(din[j], (const unsigned char *)t->cols[j].data + c0 * w[j], cnt * w[j]);
       cols[j].data = din[j];
       cols[j].dtype = t->cols[j].dtype;
-      outs[j] = dout[j];
+      outs[j] = dout[k][j];
     }
+    if (rc == MDJ_OK) rc = in.flush();
     const mdj_table chunk = {cols, nc, cnt};
-    MDJ_TRY(mdj_partition(&chunk, key_col, B, outs, drid, doff, alloc, s));
-    MDJ_CUDA_TRY(cudaMemcpyAsync(off.data(), doff, (size_t)(B + 1) * 8, cudaMemcpyDeviceToHost, s));
-    MDJ_CUDA_TRY(cudaStreamSynchronize(s));
-    for (uint32_t b = 0; b < B; b++) {
-      const uint64_t lo = (uint64_t)off[b], nb = (uint64_t)(off[b + 1] - off[b]);
-      if (nb == 0) continue;
-      for (int j = 0; j < nc; j++) {
-        std::vector<unsigned char> &v = hb->cols[b][j];
-        const size_t at = v.size();
-        v.resize(at + nb * w[j]);
-        MDJ_CUDA_TRY(cudaMemcpyAsync(v.data() + at, dout[j] + lo * w[j], nb * w[j], cudaMemcpyDeviceToHost, s));
-      }
-      rbuf.resize(nb);
-      MDJ_CUDA_TRY(cudaMemcpyAsync(rbuf.data(), drid + lo, nb * 4, cudaMemcpyDeviceToHost, s));
-      MDJ_CUDA_TRY(cudaStreamSynchronize(s));
-      std::vector<uint32_t> &r = hb->rid[b];
-      const size_t at = r.size();
-      r.resize(at + nb);
-      for (uint64_t i = 0; i < nb; i++) r[at + i] = rbuf[i] + (uint32_t)c0;  // chunk-local -> input row
+    if (rc == MDJ_OK) rc = mdj_partition(&chunk, key_col, B, outs, drid[k], doff[k], alloc, s);
+    if (rc == MDJ_OK && c0) {
+      const unsigned g = (unsigned)std::min<uint64_t>((cnt + 511) / 512, (uint64_t)num_sms() * 4);
+      k_add_rows<<<g, 512, 0, s>>>(drid[k], cnt, (uint32_t)c0);
+      rc = cuda_status(cudaGetLastError());
     }
+    if (rc == MDJ_OK) rc = cuda_status(cudaEventRecord(x.ready[k], s));
+    if (rc == MDJ_OK) rc = cuda_status(cudaStreamWaitEvent(x.sc, x.ready[k], 0));
+    for (int j = 0; j < nc && rc == MDJ_OK; j++) rc = back.add(hs->col[j] + c0 * w[j], dout[k][j], cnt * w[j]);
+    if (rc == MDJ_OK) rc = back.add(hs->rid + c0, drid[k], cnt * 4);
+    if (rc == MDJ_OK) rc = back.add(&hs->offs[c * (B + 1)], doff[k], (size_t)(B + 1) * 8);
+    if (rc == MDJ_OK) rc = back.flush();
+    if (rc == MDJ_OK) rc = cuda_status(cudaEventRecord(x.done[k], x.sc));
   }
-  return MDJ_OK;
+  // the caller's stream (and the release of this workspace) follows the
+  // copies back; the host reads the offsets after them
+  const int k_last = (int)((nchunks - 1) & 1);
+  if (rc == MDJ_OK) rc = cuda_status(cudaStreamWaitEvent(s, x.done[k_last], 0));
+  if (nchunks >= 2 && rc == MDJ_OK) rc = cuda_status(cudaStreamWaitEvent(s, x.done[k_last ^ 1], 0));
+  const int rs = cuda_status(cudaStreamSynchronize(x.sc));
+  return rc != MDJ_OK ? rc : rs;
 }
 
-// Bucket b of one side on the device: every column and the global row ids.
-int bucket_to_device(Workspace &ws, const mdj_table *t, const HostBuckets &hb, uint32_t b, mdj_col *cols,
-                     mdj_table *out, uint32_t **rid) {
-  const uint64_t nb = hb.rid[b].size();
+// Rows of bucket b in every chunk of one side.
+uint64_t bucket_rows(const HostStage &hs, uint32_t B, uint32_t b) {
+  uint64_t nb = 0;
+  for (uint64_t c = 0; c < hs.nchunks; c++) nb += (uint64_t)(hs.offs[c * (B + 1) + b + 1] - hs.offs[c * (B + 1) + b]);
+  return nb;
+}
+
+// Bucket b of one side on the device: every column and the input row ids.
+int bucket_to_device(Workspace &ws, const mdj_table *t, const HostStage &hs, uint32_t B, uint32_t b, bool direct,
+                     mdj_col *cols, mdj_table *out, uint32_t **rid) {
+  const uint64_t nb = bucket_rows(hs, B, b);
   cudaStream_t s = ws.stream();
-  for (int j = 0; j < t->ncols; j++) {
-    const std::vector<unsigned char> &v = hb.cols[b][j];
-    unsigned char *d = dev_block(ws, v.size());
-    if (!d) return MDJ_ERR_OOM;
-    if (!v.empty()) MDJ_CUDA_TRY(cudaMemcpyAsync(d, v.data(), v.size(), cudaMemcpyHostToDevice, s));
-    cols[j].data = d;
+  const int nc = t->ncols;
+  int w[MDJ_MAX_COLS];
+  unsigned char *d[MDJ_MAX_COLS];
+  for (int j = 0; j < nc; j++) {
+    w[j] = dtype_width(t->cols[j].dtype);
+    if (!(d[j] = dev_block(ws, nb * w[j]))) return MDJ_ERR_OOM;
+    cols[j].data = d[j];
     cols[j].dtype = t->cols[j].dtype;
   }
   *rid = (uint32_t *)dev_block(ws, nb * 4);
   if (!*rid) return MDJ_ERR_OOM;
-  if (nb) MDJ_CUDA_TRY(cudaMemcpyAsync(*rid, hb.rid[b].data(), nb * 4, cudaMemcpyHostToDevice, s));
-  *out = {cols, t->ncols, nb};
+  Copier cp(direct, s);
+  uint64_t pos = 0;
+  for (uint64_t c = 0; c < hs.nchunks; c++) {
+    const int64_t *o = &hs.offs[c * (B + 1)];
+    const uint64_t lo = c * hs.chunk_rows + (uint64_t)o[b], cnt = (uint64_t)(o[b + 1] - o[b]);
+    if (!cnt) continue;
+    for (int j = 0; j < nc; j++) MDJ_TRY(cp.add(d[j] + pos * w[j], hs.col[j] + lo * w[j], cnt * w[j]));
+    MDJ_TRY(cp.add(*rid + pos, hs.rid + lo, cnt * 4));
+    pos += cnt;
+  }
+  MDJ_TRY(cp.flush());
+  *out = {cols, nc, nb};
   return MDJ_OK;
 }
 
@@ -257,15 +447,20 @@ int merge_host_impl(const mdj_table *left, int32_t lk, const mdj_table *right, i
   const uint64_t in_bytes = left->nrows * (wl + 4) + right->nrows * (wr + 4);
   uint64_t B = 1;
   while (B < MDJ_MAX_PARTITIONS && in_bytes > B * (budget / 6)) B *= 2;
-  const uint64_t chunk_rows = std::max<uint64_t>(1, (budget / 4) / (2 * std::max(wl, wr) + 4));
+  // a chunk's input, two output sets and their row ids: a quarter of the
+  // budget; a multiple of 16 rows, so every chunk's columns start 16-byte
+  // aligned in the staging area
+  const uint64_t chunk_rows =
+      std::max<uint64_t>(16, ((budget / 4) / (3 * std::max(wl, wr) + 8)) & ~(uint64_t)15);
   const uint64_t out_row = wl + wr + 8 - dtype_width(kd);  // key once, both row ids, every other column
   const uint64_t window = std::max<uint64_t>(1, (budget / 6) / out_row);
 
   if (B == 1) return merge_resident(left, lk, right, rk, P, how, window, sink, sink_ctx, alloc, s, total_rows);
 
-  HostBuckets hl, hr;
-  MDJ_TRY(partition_to_host(left, lk, (uint32_t)B, chunk_rows, alloc, s, &hl));
-  MDJ_TRY(partition_to_host(right, rk, (uint32_t)B, chunk_rows, alloc, s, &hr));
+  const bool direct = direct_host_access();
+  HostStage hl, hr;
+  MDJ_TRY(partition_to_host(left, lk, (uint32_t)B, chunk_rows, alloc, s, direct, &hl));
+  MDJ_TRY(partition_to_host(right, rk, (uint32_t)B, chunk_rows, alloc, s, direct, &hr));
 
   Workspace wbuf(alloc, s);  // one window, reused by every bucket
   mdj_result piece;
@@ -305,14 +500,14 @@ int merge_host_impl(const mdj_table *left, int32_t lk, const mdj_table *right, i
   const uint32_t Pb = ((P & (P - 1)) == 0 && (uint64_t)P <= B) ? 1u : P;
   uint64_t produced = 0;
   for (uint32_t b = 0; b < B; b++) {
-    const uint64_t nl = hl.rid[b].size(), nr = hr.rid[b].size();
+    const uint64_t nl = bucket_rows(hl, (uint32_t)B, b), nr = bucket_rows(hr, (uint32_t)B, b);
     if (!((nl && nr) || (nl && keep_left) || (nr && keep_right))) continue;
     Workspace ws(alloc, s);  // this bucket's tables, released before the next bucket
     mdj_col lc[MDJ_MAX_COLS], rc[MDJ_MAX_COLS];
     mdj_table lt, rt;
     uint32_t *lrid, *rrid;
-    MDJ_TRY(bucket_to_device(ws, left, hl, b, lc, &lt, &lrid));
-    MDJ_TRY(bucket_to_device(ws, right, hr, b, rc, &rt, &rrid));
+    MDJ_TRY(bucket_to_device(ws, left, hl, (uint32_t)B, b, direct, lc, &lt, &lrid));
+    MDJ_TRY(bucket_to_device(ws, right, hr, (uint32_t)B, b, direct, rc, &rt, &rrid));
     mdj_stream *h = nullptr;
     uint64_t m = 0;
     MDJ_TRY(mdj_stream_open(&lt, lk, &rt, rk, Pb, how, alloc, stream, &h, &m));

@@ -44,6 +44,19 @@ def test_host_tables_beyond_the_budget(how):
         assert total == 900_000
 
 
+@pytest.mark.parametrize("memcpy", ["0", "1"])
+def test_host_copy_paths_and_unaligned_columns(monkeypatch, memcpy):
+    # copy kernels (device access to pageable memory) or cudaMemcpyAsync; the
+    # input columns start 4 bytes past a 16-byte boundary, and the 6 and 5
+    # phase-1 chunks of the two sides cycle both copy-back buffer sets
+    monkeypatch.setenv("MDJ_TEST_HOST_MEMCPY", memcpy)
+    (lk, lp), (rk, rp) = datagen.random_tables(3_000_001, 2_500_001, 4_000_000, seed=55, key_dtype=np.int32,
+                                               pay_dtype=np.float32)
+    left, right = [lk[1:], lp[1:]], [rk[1:], rp[1:]]
+    assert all(c.ctypes.data % 16 == 4 for c in left + right)
+    _check(left, right, 8, "inner")
+
+
 @pytest.mark.parametrize("how", ["inner", "outer"])
 def test_host_heavy_key_spans_many_windows(how):
     rng = np.random.default_rng(52)

@@ -196,10 +196,13 @@ def test_invalid_arguments():
     assert e.value.status == -2
 
 
-def test_output_buffer_overflow_takes_exact_pass(monkeypatch):
+@pytest.mark.parametrize("ordered", ["0", "1"])
+def test_output_buffer_overflow_takes_exact_pass(monkeypatch, ordered):
     # an optimistic buffer smaller than the join forces the exact second pass
+    # at the item offsets the first pass recorded (atomic or looked-back)
     (lk, lp), (rk, rp) = datagen.match_fraction_tables(50_000, 70_000, 0.5, seed=21)
     monkeypatch.setenv("MDJ_OUTPUT_ROWS", "1000")
+    monkeypatch.setenv("MDJ_ORDERED_OUTPUT", ordered)
     got = _check([lk, lp], [rk, rp], 8)
     assert got["key"].size == 35_000
 
