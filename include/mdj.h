@@ -358,18 +358,22 @@ MDJ_API int mdj_merge_multi(const mdj_table *left, const int32_t *left_keys, con
  * 1 GB chunks (Sec. IV-B); here the tables themselves pass through the device
  * in pieces bounded by `device_budget`:
  *   1. each table goes to the device in chunks; every chunk is hash
- *      partitioned into B buckets (bucket = h mod B, as mdj_partition) and the
- *      buckets return to host memory with the rows' input row ids;
- *   2. for each bucket b, both tables' bucket b go to the device, their merge
- *      is opened as a stream (mdj_stream_open with P and `how`; with one
- *      partition when P is a power of two no larger than B, since every row
- *      of the bucket would then share one partition), and its rows
- *      are written window by window; each window's row ids are mapped back to
- *      the input tables and the window is handed to `sink`.
- * When both tables together (with 4-byte row ids) take at most a sixth of the
- * budget, B = 1: phase 1 is skipped, each column goes to the device with one
- * copy, and an inner merge runs mdj_merge there and hands its result to the
- * sink in windows that point into it (other join types stream as in 2.).
+ *      partitioned into B buckets (bucket = h mod B, as mdj_partition) and
+ *      returns to a host staging area with the rows' input row ids;
+ *   2. for each bucket b, both tables' bucket b go to the device (bucket b + 1
+ *      is copied in meanwhile), their merge is opened as a stream
+ *      (mdj_stream_open with P and `how`; with one partition when P is a
+ *      power of two no larger than B, since every row of the bucket would then
+ *      share one partition), and its rows are written window by window; each
+ *      window's row ids are mapped back to the input tables and the window is
+ *      handed to `sink`.
+ * When both tables together (with 4-byte row ids) take at most a seventh of
+ * the budget, B = 1: phase 1 is skipped, each column goes to the device with
+ * one copy, and an inner merge runs mdj_merge there and hands its result to
+ * the sink in windows that point into it (other join types stream as in 2.).
+ * Where the device reads pageable host memory directly, reads of host memory
+ * are copy kernels and copies back go through the copy engines; elsewhere
+ * every copy is a cudaMemcpyAsync.
  *   left, right   : tables whose column pointers are HOST pointers (pageable
  *                   or pinned), read only
  *   device_budget : bytes of device memory the call sizes its pieces for
@@ -383,7 +387,7 @@ MDJ_API int mdj_merge_multi(const mdj_table *left, const int32_t *left_keys, con
  * Row ids index the input tables; a missing side (outer joins) is
  * 0xFFFFFFFF as in mdj_stream_open.  Rows arrive bucket by bucket, each
  * bucket in its stream order.  All rows of one key share a bucket, so a key
- * whose rows exceed about a sixth of the budget gives MDJ_ERR_OOM.  Host
+ * whose rows exceed about a seventh of the budget gives MDJ_ERR_OOM.  Host
  * memory for the buckets (the tables' size again, plus 4 bytes per row) is
  * the library's own.  Synchronises `stream`.
  */

@@ -31,6 +31,8 @@
 #include <unistd.h>
 
 #include <algorithm>
+#include <atomic>
+#include <memory>
 #include <thread>
 #include <vector>
 
@@ -119,10 +121,11 @@ class Copier {
   }
   int flush() {
     if (!L_.n) return MDJ_OK;
-    // ~64 KB per block in flight; a link-bound copy needs few SMs
+    // about four blocks per SM over all segments (copies over the host link
+    // are latency bound: many loads in flight), at least 32 KB per block
     const uint64_t per = total_ / L_.n;
-    unsigned bx = (unsigned)std::min<uint64_t>(std::max<uint64_t>(per >> 16, 1), 64);
-    while (bx > 1 && (uint64_t)bx * L_.n > 256) bx /= 2;
+    const uint64_t want = std::max<uint64_t>(1, (uint64_t)4 * num_sms() / L_.n);
+    const unsigned bx = (unsigned)std::min<uint64_t>(std::min(want, std::max<uint64_t>(per >> 15, 1)), 128);
     k_copy_segs<<<dim3(bx, L_.n), 512, 0, s_>>>(L_);
     L_.n = 0;
     total_ = 0;
@@ -136,28 +139,79 @@ class Copier {
   uint64_t total_ = 0;
 };
 
-// Touch every page of [p, p + bytes) once, from several host threads (this
-// thread alone when they cannot be started).
-void touch_pages(unsigned char *p, size_t bytes) {
-  const long pg = sysconf(_SC_PAGESIZE);
-  const size_t page = pg > 0 ? (size_t)pg : 4096;
-  const size_t pages = (bytes + page - 1) / page;
-  auto run = [p, page](size_t lo, size_t hi) {
-    volatile unsigned char *v = p;
-    for (size_t q = lo; q < hi; q++) v[q * page] = 0;
+// Touches the pages of host staging memory from background threads, task by
+// task in order (a task: the byte ranges one phase-1 chunk writes), so that
+// the device never writes a page the host has not faulted in and the host
+// faults pages in while the device works on earlier chunks.  Every touched
+// byte lies inside its own task's ranges, so touching never races with a
+// device copy into another task's ranges.  Runs in the calling thread when
+// threads cannot be started.
+class PageToucher {
+ public:
+  struct Range {
+    unsigned char *p;
+    size_t bytes;
   };
-  unsigned nt = std::max(1u, std::min(std::thread::hardware_concurrency(), 16u));
-  if (bytes < (64u << 20)) nt = 1;
-  std::vector<std::thread> th;
-  size_t started = 1;  // thread t touches pages [pages * t / nt, pages * (t + 1) / nt)
-  try {
-    for (unsigned t = 1; t < nt; t++, started++) th.emplace_back(run, pages * t / nt, pages * (t + 1) / nt);
-  } catch (...) {
+  // Ranges of task `task` (tasks numbered 0, 1, ... in the order they are added).
+  void add(size_t task, unsigned char *p, size_t bytes) {
+    if (!bytes) return;
+    if (task >= tasks_.size()) tasks_.resize(task + 1);
+    // granules of at most 4 MiB, so that threads share large ranges
+    for (size_t off = 0; off < bytes; off += kGranule)
+      tasks_[task].push_back({p + off, std::min(kGranule, bytes - off)});
   }
-  run(0, pages / nt);
-  run(pages * started / nt, pages);  // ranges of threads that did not start
-  for (auto &t : th) t.join();
-}
+  void start() {
+    const long pg = sysconf(_SC_PAGESIZE);
+    page_ = pg > 0 ? (size_t)pg : 4096;
+    for (size_t t = 0; t < tasks_.size(); t++)
+      for (const Range &r : tasks_[t]) gran_.push_back({r, t});
+    left_.reset(new std::atomic<size_t>[tasks_.size()]);
+    for (size_t t = 0; t < tasks_.size(); t++) left_[t].store(tasks_[t].size());
+    unsigned nt = std::max(1u, std::min(std::thread::hardware_concurrency(), 16u));
+    try {
+      for (unsigned i = 0; i < nt; i++) th_.emplace_back([this] { work(); });
+    } catch (...) {
+    }
+    if (th_.empty()) work();
+  }
+  // Blocks until every page of task `task` is touched.
+  void wait(size_t task) {
+    if (task >= tasks_.size()) return;
+    while (left_[task].load(std::memory_order_acquire) != 0) std::this_thread::yield();
+  }
+  ~PageToucher() {
+    stop_.store(true);
+    for (auto &t : th_) t.join();
+  }
+
+ private:
+  static constexpr size_t kGranule = 4u << 20;
+  struct Gran {
+    Range r;
+    size_t task;
+  };
+  void work() {
+    for (;;) {
+      if (stop_.load(std::memory_order_relaxed)) return;
+      const size_t g = next_.fetch_add(1);
+      if (g >= gran_.size()) return;
+      const Range r = gran_[g].r;
+      volatile unsigned char *v = r.p;
+      // one byte in every page the range overlaps, the range's own byte
+      const uintptr_t a = (uintptr_t)r.p;
+      const uintptr_t first_page = a - a % page_;
+      for (uintptr_t q = first_page; q < a + r.bytes; q += page_) v[(q < a ? a : q) - a] = 0;
+      left_[gran_[g].task].fetch_sub(1, std::memory_order_release);
+    }
+  }
+  std::vector<std::vector<Range>> tasks_;
+  std::vector<Gran> gran_;
+  std::unique_ptr<std::atomic<size_t>[]> left_;
+  std::atomic<size_t> next_{0};
+  std::atomic<bool> stop_{false};
+  std::vector<std::thread> th_;
+  size_t page_ = 4096;
+};
 
 // One side's buckets in host memory: the partitioned chunks in chunk order,
 // each column (and the input row ids) as one array of nrows elements; chunk c
@@ -180,32 +234,51 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // A device block for `bytes`, freed by the owning workspace.
 unsigned char *dev_block(Workspace &ws, size_t bytes) { return (unsigned char *)ws.get(bytes ? bytes : 1); }
 
-int partition_to_host(const mdj_table *t, int32_t key_col, uint32_t B, uint64_t chunk_rows, const mdj_allocator *alloc,
-                      cudaStream_t s, bool direct, HostStage *hs) {
+// One side's staging area (uninitialised host memory) for chunks of
+// `chunk_rows` rows; chunk c's ranges become toucher task task0 + c.
+int stage_alloc(const mdj_table *t, uint32_t B, uint64_t chunk_rows, HostStage *hs, PageToucher &pt, size_t task0) {
   const int nc = t->ncols;
-  int w[MDJ_MAX_COLS];
-  for (int j = 0; j < nc; j++) w[j] = dtype_width(t->cols[j].dtype);
   const uint64_t n = t->nrows;
-  if (n == 0) {
-    hs->nchunks = 0;
-    return MDJ_OK;
-  }
+  hs->nchunks = 0;
+  if (n == 0) return MDJ_OK;
   const uint64_t C = std::min<uint64_t>(chunk_rows, n);
-  const uint64_t nchunks = (n + C - 1) / C;
   hs->chunk_rows = C;
-  hs->nchunks = nchunks;
-  hs->offs.assign(nchunks * (B + 1), 0);
+  hs->nchunks = (n + C - 1) / C;
+  hs->offs.assign(hs->nchunks * (B + 1), 0);
   size_t bytes = align256((size_t)n * 4);
-  for (int j = 0; j < nc; j++) bytes += align256((size_t)n * w[j]);
+  for (int j = 0; j < nc; j++) bytes += align256((size_t)n * dtype_width(t->cols[j].dtype));
   hs->mem = (unsigned char *)malloc(bytes);
   if (!hs->mem) return MDJ_ERR_OOM;
-  touch_pages(hs->mem, bytes);
   size_t at = 0;
   for (int j = 0; j < nc; j++) {
     hs->col[j] = hs->mem + at;
-    at += align256((size_t)n * w[j]);
+    at += align256((size_t)n * dtype_width(t->cols[j].dtype));
   }
   hs->rid = (uint32_t *)(hs->mem + at);
+  for (uint64_t c = 0; c < hs->nchunks; c++) {
+    const uint64_t c0 = c * C, cnt = std::min(C, n - c0);
+    for (int j = 0; j < nc; j++) {
+      const int w = dtype_width(t->cols[j].dtype);
+      pt.add(task0 + c, hs->col[j] + c0 * w, cnt * w);
+    }
+    pt.add(task0 + c, (unsigned char *)(hs->rid + c0), cnt * 4);
+  }
+  return MDJ_OK;
+}
+
+// Phase 1 of one side into its staging area.  Chunk c is copied in and
+// partitioned on the caller's stream `s`; its copy back runs on a second
+// stream after its pages are touched, issued once chunk c + 1's work is
+// queued (a copy into pageable memory may hold the host thread until it
+// ends), through the copy engines, so that it overlaps the partition kernels
+// (which fill every SM).  Two output buffer sets alternate.
+int partition_to_host(const mdj_table *t, int32_t key_col, uint32_t B, const mdj_allocator *alloc, cudaStream_t s,
+                      bool direct, HostStage *hs, PageToucher &pt, size_t task0) {
+  const int nc = t->ncols;
+  int w[MDJ_MAX_COLS];
+  for (int j = 0; j < nc; j++) w[j] = dtype_width(t->cols[j].dtype);
+  const uint64_t n = t->nrows, nchunks = hs->nchunks, C = hs->chunk_rows;
+  if (nchunks == 0) return MDJ_OK;
 
   Workspace ws(alloc, s);
   unsigned char *din[MDJ_MAX_COLS], *dout[2][MDJ_MAX_COLS];
@@ -237,7 +310,18 @@ int partition_to_host(const mdj_table *t, int32_t key_col, uint32_t B, uint64_t 
     MDJ_CUDA_TRY(cudaEventCreateWithFlags(&x.ready[k], cudaEventDisableTiming));
     MDJ_CUDA_TRY(cudaEventCreateWithFlags(&x.done[k], cudaEventDisableTiming));
   }
-  Copier in(direct, s), back(direct, x.sc);
+  Copier in(direct, s), back(false, x.sc);
+  auto copy_back = [&](uint64_t c) {
+    const int k = (int)(c & 1);
+    const uint64_t c0 = c * C, cnt = std::min(C, n - c0);
+    pt.wait(task0 + c);
+    int rc = cuda_status(cudaStreamWaitEvent(x.sc, x.ready[k], 0));
+    for (int j = 0; j < nc && rc == MDJ_OK; j++) rc = back.add(hs->col[j] + c0 * w[j], dout[k][j], cnt * w[j]);
+    if (rc == MDJ_OK) rc = back.add(hs->rid + c0, drid[k], cnt * 4);
+    if (rc == MDJ_OK) rc = back.add(&hs->offs[c * (B + 1)], doff[k], (size_t)(B + 1) * 8);
+    if (rc == MDJ_OK) rc = cuda_status(cudaEventRecord(x.done[k], x.sc));
+    return rc;
+  };
   int rc = MDJ_OK;
   for (uint64_t c = 0; c < nchunks && rc == MDJ_OK; c++) {
     const int k = (int)(c & 1);
@@ -260,13 +344,9 @@ int partition_to_host(const mdj_table *t, int32_t key_col, uint32_t B, uint64_t 
       rc = cuda_status(cudaGetLastError());
     }
     if (rc == MDJ_OK) rc = cuda_status(cudaEventRecord(x.ready[k], s));
-    if (rc == MDJ_OK) rc = cuda_status(cudaStreamWaitEvent(x.sc, x.ready[k], 0));
-    for (int j = 0; j < nc && rc == MDJ_OK; j++) rc = back.add(hs->col[j] + c0 * w[j], dout[k][j], cnt * w[j]);
-    if (rc == MDJ_OK) rc = back.add(hs->rid + c0, drid[k], cnt * 4);
-    if (rc == MDJ_OK) rc = back.add(&hs->offs[c * (B + 1)], doff[k], (size_t)(B + 1) * 8);
-    if (rc == MDJ_OK) rc = back.flush();
-    if (rc == MDJ_OK) rc = cuda_status(cudaEventRecord(x.done[k], x.sc));
+    if (rc == MDJ_OK && c >= 1) rc = copy_back(c - 1);
   }
+  if (rc == MDJ_OK) rc = copy_back(nchunks - 1);
   // the caller's stream (and the release of this workspace) follows the
   // copies back; the host reads the offsets after them
   const int k_last = (int)((nchunks - 1) & 1);
@@ -283,36 +363,52 @@ uint64_t bucket_rows(const HostStage &hs, uint32_t B, uint32_t b) {
   return nb;
 }
 
-// Bucket b of one side on the device: every column and the input row ids.
-int bucket_to_device(Workspace &ws, const mdj_table *t, const HostStage &hs, uint32_t B, uint32_t b, bool direct,
-                     mdj_col *cols, mdj_table *out, uint32_t **rid) {
+// Bucket b of one side on the device: every column and the input row ids
+// (allocated in `ws`, on the caller's stream).
+int bucket_alloc(Workspace &ws, const mdj_table *t, const HostStage &hs, uint32_t B, uint32_t b, mdj_col *cols,
+                 mdj_table *out, uint32_t **rid) {
   const uint64_t nb = bucket_rows(hs, B, b);
-  cudaStream_t s = ws.stream();
   const int nc = t->ncols;
-  int w[MDJ_MAX_COLS];
-  unsigned char *d[MDJ_MAX_COLS];
   for (int j = 0; j < nc; j++) {
-    w[j] = dtype_width(t->cols[j].dtype);
-    if (!(d[j] = dev_block(ws, nb * w[j]))) return MDJ_ERR_OOM;
-    cols[j].data = d[j];
+    unsigned char *d = dev_block(ws, nb * dtype_width(t->cols[j].dtype));
+    if (!d) return MDJ_ERR_OOM;
+    cols[j].data = d;
     cols[j].dtype = t->cols[j].dtype;
   }
   *rid = (uint32_t *)dev_block(ws, nb * 4);
   if (!*rid) return MDJ_ERR_OOM;
-  Copier cp(direct, s);
+  *out = {cols, nc, nb};
+  return MDJ_OK;
+}
+
+// Gathers bucket b's slice of every chunk into the buffers bucket_alloc gave.
+int bucket_copy(Copier &cp, const mdj_table *t, const HostStage &hs, uint32_t B, uint32_t b, const mdj_col *cols,
+                uint32_t *rid) {
+  const int nc = t->ncols;
   uint64_t pos = 0;
   for (uint64_t c = 0; c < hs.nchunks; c++) {
     const int64_t *o = &hs.offs[c * (B + 1)];
     const uint64_t lo = c * hs.chunk_rows + (uint64_t)o[b], cnt = (uint64_t)(o[b + 1] - o[b]);
     if (!cnt) continue;
-    for (int j = 0; j < nc; j++) MDJ_TRY(cp.add(d[j] + pos * w[j], hs.col[j] + lo * w[j], cnt * w[j]));
-    MDJ_TRY(cp.add(*rid + pos, hs.rid + lo, cnt * 4));
+    for (int j = 0; j < nc; j++) {
+      const int w = dtype_width(t->cols[j].dtype);
+      MDJ_TRY(cp.add((unsigned char *)cols[j].data + pos * w, hs.col[j] + lo * w, cnt * w));
+    }
+    MDJ_TRY(cp.add(rid + pos, hs.rid + lo, cnt * 4));
     pos += cnt;
   }
-  MDJ_TRY(cp.flush());
-  *out = {cols, nc, nb};
-  return MDJ_OK;
+  return cp.flush();
 }
+
+// Both sides' bucket b on the device, in a workspace of its own.
+struct BucketPair {
+  Workspace ws;
+  mdj_col lc[MDJ_MAX_COLS], rc[MDJ_MAX_COLS];
+  mdj_table lt, rt;
+  uint32_t *lrid = nullptr, *rrid = nullptr;
+  uint32_t b = 0;
+  BucketPair(const mdj_allocator *a, cudaStream_t s) : ws(a, s) {}
+};
 
 // A whole host table on the device: one block and one copy per column.
 int table_to_device(Workspace &ws, const mdj_table *t, mdj_col *cols, mdj_table *out) {
@@ -441,26 +537,33 @@ int merge_host_impl(const mdj_table *left, int32_t lk, const mdj_table *right, i
   cudaStream_t s = (cudaStream_t)stream;
 
   // sizes from the budget: a bucket pair's rows (with row ids) take at most
-  // a sixth of it (the stream open holds about four times its inputs), a
-  // chunk of phase 1 a quarter, a window a sixth
+  // a seventh of it (the stream open holds about four times its inputs, the
+  // next bucket pair is copied in meanwhile), a chunk of phase 1 a quarter, a
+  // window a seventh
   const uint64_t wl = row_bytes(left), wr = row_bytes(right);
   const uint64_t in_bytes = left->nrows * (wl + 4) + right->nrows * (wr + 4);
   uint64_t B = 1;
-  while (B < MDJ_MAX_PARTITIONS && in_bytes > B * (budget / 6)) B *= 2;
+  while (B < MDJ_MAX_PARTITIONS && in_bytes > B * (budget / 7)) B *= 2;
   // a chunk's input, two output sets and their row ids: a quarter of the
   // budget; a multiple of 16 rows, so every chunk's columns start 16-byte
   // aligned in the staging area
   const uint64_t chunk_rows =
       std::max<uint64_t>(16, ((budget / 4) / (3 * std::max(wl, wr) + 8)) & ~(uint64_t)15);
   const uint64_t out_row = wl + wr + 8 - dtype_width(kd);  // key once, both row ids, every other column
-  const uint64_t window = std::max<uint64_t>(1, (budget / 6) / out_row);
+  const uint64_t window = std::max<uint64_t>(1, (budget / 7) / out_row);
 
   if (B == 1) return merge_resident(left, lk, right, rk, P, how, window, sink, sink_ctx, alloc, s, total_rows);
 
   const bool direct = direct_host_access();
   HostStage hl, hr;
-  MDJ_TRY(partition_to_host(left, lk, (uint32_t)B, chunk_rows, alloc, s, direct, &hl));
-  MDJ_TRY(partition_to_host(right, rk, (uint32_t)B, chunk_rows, alloc, s, direct, &hr));
+  {
+    PageToucher pt;  // destroyed (threads joined) before the staging areas
+    MDJ_TRY(stage_alloc(left, (uint32_t)B, chunk_rows, &hl, pt, 0));
+    MDJ_TRY(stage_alloc(right, (uint32_t)B, chunk_rows, &hr, pt, hl.nchunks));
+    pt.start();
+    MDJ_TRY(partition_to_host(left, lk, (uint32_t)B, alloc, s, direct, &hl, pt, 0));
+    MDJ_TRY(partition_to_host(right, rk, (uint32_t)B, alloc, s, direct, &hr, pt, hl.nchunks));
+  }
 
   Workspace wbuf(alloc, s);  // one window, reused by every bucket
   mdj_result piece;
@@ -498,27 +601,59 @@ int merge_host_impl(const mdj_table *left, int32_t lk, const mdj_table *right, i
   // merge's own sub-buckets come from the high hash bits, so the work still
   // spreads over the device).  The joined rows do not depend on P.
   const uint32_t Pb = ((P & (P - 1)) == 0 && (uint64_t)P <= B) ? 1u : P;
-  uint64_t produced = 0;
+  std::vector<uint32_t> todo;  // buckets with output
   for (uint32_t b = 0; b < B; b++) {
     const uint64_t nl = bucket_rows(hl, (uint32_t)B, b), nr = bucket_rows(hr, (uint32_t)B, b);
-    if (!((nl && nr) || (nl && keep_left) || (nr && keep_right))) continue;
-    Workspace ws(alloc, s);  // this bucket's tables, released before the next bucket
-    mdj_col lc[MDJ_MAX_COLS], rc[MDJ_MAX_COLS];
-    mdj_table lt, rt;
-    uint32_t *lrid, *rrid;
-    MDJ_TRY(bucket_to_device(ws, left, hl, (uint32_t)B, b, direct, lc, &lt, &lrid));
-    MDJ_TRY(bucket_to_device(ws, right, hr, (uint32_t)B, b, direct, rc, &rt, &rrid));
+    if ((nl && nr) || (nl && keep_left) || (nr && keep_right)) todo.push_back(b);
+  }
+  // Bucket i + 1 is allocated on the caller's stream and copied in on a
+  // prefetch stream while bucket i merges.  The guard drains the prefetch
+  // stream before any bucket's buffers are released (it is destroyed first).
+  std::unique_ptr<BucketPair> cur, nxt;
+  struct Prefetch {
+    cudaStream_t sp = nullptr;
+    cudaEvent_t alloced = nullptr, ready[2] = {nullptr, nullptr};
+    ~Prefetch() {
+      if (sp) cudaStreamSynchronize(sp);
+      if (alloced) cudaEventDestroy(alloced);
+      for (int k = 0; k < 2; k++)
+        if (ready[k]) cudaEventDestroy(ready[k]);
+      if (sp) cudaStreamDestroy(sp);
+    }
+  } pf;
+  MDJ_CUDA_TRY(cudaStreamCreateWithFlags(&pf.sp, cudaStreamNonBlocking));
+  MDJ_CUDA_TRY(cudaEventCreateWithFlags(&pf.alloced, cudaEventDisableTiming));
+  for (int k = 0; k < 2; k++) MDJ_CUDA_TRY(cudaEventCreateWithFlags(&pf.ready[k], cudaEventDisableTiming));
+  auto prefetch = [&](std::unique_ptr<BucketPair> &bp, uint32_t b, int slot) {
+    bp.reset(new BucketPair(alloc, s));
+    bp->b = b;
+    MDJ_TRY(bucket_alloc(bp->ws, left, hl, (uint32_t)B, b, bp->lc, &bp->lt, &bp->lrid));
+    MDJ_TRY(bucket_alloc(bp->ws, right, hr, (uint32_t)B, b, bp->rc, &bp->rt, &bp->rrid));
+    // the blocks may have served earlier work of the caller's stream
+    MDJ_CUDA_TRY(cudaEventRecord(pf.alloced, s));
+    MDJ_CUDA_TRY(cudaStreamWaitEvent(pf.sp, pf.alloced, 0));
+    Copier cp(direct, pf.sp);
+    MDJ_TRY(bucket_copy(cp, left, hl, (uint32_t)B, b, bp->lc, bp->lrid));
+    MDJ_TRY(bucket_copy(cp, right, hr, (uint32_t)B, b, bp->rc, bp->rrid));
+    MDJ_CUDA_TRY(cudaEventRecord(pf.ready[slot], pf.sp));
+    return (int)MDJ_OK;
+  };
+  uint64_t produced = 0;
+  if (!todo.empty()) MDJ_TRY(prefetch(cur, todo[0], 0));
+  for (size_t i = 0; i < todo.size(); i++) {
+    if (i + 1 < todo.size()) MDJ_TRY(prefetch(nxt, todo[i + 1], (int)((i + 1) & 1)));
+    MDJ_CUDA_TRY(cudaStreamWaitEvent(s, pf.ready[i & 1], 0));
     mdj_stream *h = nullptr;
     uint64_t m = 0;
-    MDJ_TRY(mdj_stream_open(&lt, lk, &rt, rk, Pb, how, alloc, stream, &h, &m));
+    MDJ_TRY(mdj_stream_open(&cur->lt, lk, &cur->rt, rk, Pb, how, alloc, stream, &h, &m));
     int rc2 = MDJ_OK;
     for (uint64_t q0 = 0; q0 < m && rc2 == MDJ_OK; q0 += window) {
       const uint64_t n = std::min(window, m - q0);
       rc2 = mdj_stream_emit(h, q0, n, &win);
       if (rc2 != MDJ_OK) break;
       const unsigned grid = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)num_sms() * 8);
-      k_map_rows<<<grid, 256, 0, s>>>(piece.left_row, n, lrid);
-      k_map_rows<<<grid, 256, 0, s>>>(piece.right_row, n, rrid);
+      k_map_rows<<<grid, 256, 0, s>>>(piece.left_row, n, cur->lrid);
+      k_map_rows<<<grid, 256, 0, s>>>(piece.right_row, n, cur->rrid);
       rc2 = cuda_status(cudaGetLastError());
       if (rc2 == MDJ_OK) rc2 = cuda_status(cudaStreamSynchronize(s));
       if (rc2 != MDJ_OK) break;
@@ -528,6 +663,7 @@ int merge_host_impl(const mdj_table *left, int32_t lk, const mdj_table *right, i
     }
     mdj_stream_close(h);
     MDJ_TRY(rc2);
+    cur = std::move(nxt);  // this bucket's tables go back on the caller's stream
   }
   MDJ_CUDA_TRY(cudaStreamSynchronize(s));
   *total_rows = produced;
