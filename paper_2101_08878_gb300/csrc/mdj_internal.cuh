@@ -234,7 +234,8 @@ class Workspace {
   void raw_free(void *p);
   const mdj_allocator *alloc_;
   cudaStream_t stream_;
-  std::vector<void *> owned_;
+  std::vector<void *> owned_;       // buffers allocated on their own
+  std::vector<void *> chunks_;      // arena chunks for small buffers
   unsigned char *arena_ = nullptr;  // current chunk
   size_t arena_used_ = 0;
   static constexpr size_t kArenaMax = 1u << 20;

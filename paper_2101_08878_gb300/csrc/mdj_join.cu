@@ -19,7 +19,10 @@
 // The pair count and checksum of a join (mdj_count_checksum) come from the
 // streamed output's grouping instead (mdj_stream.cu), which handles key groups
 // of any size without re-reading probe rows.
+#include <stdlib.h>
 #include <string.h>
+
+#include <algorithm>
 
 #include "mdj_internal.cuh"
 #include "mdj_join_dev.cuh"
@@ -44,10 +47,18 @@ __global__ void k_items(const uint32_t *__restrict__ offL, const uint32_t *__res
   }
 }
 
-// One descriptor per item: its build and probe row ranges.
+// One descriptor per item: its build and probe row ranges.  The item count
+// is item_off[nb]; more than `ulim` items (the descriptor array's size) sets
+// FLAG_ITEMS and writes nothing.
 __global__ void k_expand(const uint32_t *__restrict__ offL, const uint32_t *__restrict__ offR, uint32_t nb,
-                         uint32_t cap, uint32_t rch, const uint64_t *__restrict__ item_off, uint32_t nitems,
-                         Item *__restrict__ desc) {
+                         uint32_t cap, uint32_t rch, const uint64_t *__restrict__ item_off, uint32_t ulim,
+                         Item *__restrict__ desc, int *flags) {
+  const uint64_t total = item_off[nb];
+  if (total > ulim) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) flags[FLAG_ITEMS] = 1;
+    return;
+  }
+  const uint32_t nitems = (uint32_t)total;
   for (uint32_t it = blockIdx.x * blockDim.x + threadIdx.x; it < nitems; it += gridDim.x * blockDim.x) {
     uint32_t lo = 0, hi = nb - 1;  // last bucket b with item_off[b] <= it
     while (lo < hi) {
@@ -71,17 +82,22 @@ __global__ void k_expand(const uint32_t *__restrict__ offL, const uint32_t *__re
 }
 
 // bulk: the build side's staged columns (key, row ids, first payload) have
-// 16-byte-aligned bases, so items stage them by bulk copies.
+// 16-byte-aligned bases, so items stage them by bulk copies.  The item count
+// is read from *nitems_dev (no work when it exceeds `ulim`: k_expand has set
+// FLAG_ITEMS and the host reruns the join with exact arrays).
 template <typename KeyT, bool HAVE_OFFSETS, int NT>
 __global__ void __launch_bounds__(NT, 1024 / NT)
-    k_join_write(JSide L, JSide R, const Item *__restrict__ desc, uint32_t nitems, uint32_t cap, uint32_t *ticket,
-                 unsigned long long *state, uint64_t *__restrict__ item_off, unsigned long long *total,
-                 uint64_t capacity, int *flags, int withhold_first, int ordered, int bulk, JOut out) {
+    k_join_write(JSide L, JSide R, const Item *__restrict__ desc, const uint64_t *nitems_dev, uint32_t ulim,
+                 uint32_t cap, uint32_t *ticket, unsigned long long *state, uint64_t *__restrict__ item_off,
+                 unsigned long long *total, uint64_t capacity, int *flags, int withhold_first, int ordered, int bulk,
+                 JOut out) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Item s_item;
   __shared__ uint32_t s_it;
   __shared__ __align__(8) JoinShared js;
   const uint32_t tid = threadIdx.x;
+  const uint64_t nit = *nitems_dev;
+  const uint32_t nitems = nit > ulim ? 0u : (uint32_t)nit;
   const Resv rs = {state, item_off, total, capacity, flags, withhold_first, ordered};
   uint32_t phase = 0;
   if (tid == 0) {
@@ -144,37 +160,44 @@ int resident_grid(KernelT kernel, size_t smem, uint64_t nitems, int *grid, int t
   return MDJ_OK;
 }
 
-// Work items of the whole join, with `rch` probe rows per item at most.
-int make_items(Workspace &ws, const Side &Ls, const Side &Rs, uint32_t nb, uint32_t cap, uint32_t rch, Item **desc,
-               uint32_t *nitems_out, uint64_t **bucket_items = nullptr) {
+// Work items of the whole join, with `rch` probe rows per item at most, into
+// a descriptor array of `ulim` items.  No host wait: the count stays on the
+// device at (*item_off)[nb] (per-bucket item prefix in *item_off), and a count
+// above ulim sets FLAG_ITEMS instead of writing descriptors.
+int make_items(Workspace &ws, const Side &Ls, const Side &Rs, uint32_t nb, uint32_t cap, uint32_t rch, uint32_t ulim,
+               int *flags, Item **desc, uint64_t **item_off_out) {
   cudaStream_t s = ws.stream();
   uint64_t *item_off = (uint64_t *)ws.get((size_t)(nb + 1) * 8);
-  if (!item_off) return MDJ_ERR_OOM;
+  *desc = (Item *)ws.get((size_t)(ulim ? ulim : 1) * sizeof(Item));
+  if (!item_off || !*desc) return MDJ_ERR_OOM;
   {
     TraceScope tr("join_items", s);
     k_items<<<(nb + 1 + 255) / 256, 256, 0, s>>>(Ls.off, Rs.off, nb, cap, rch, item_off);
   }
   MDJ_LAUNCH_CHECK();
   MDJ_TRY(exclusive_scan_u64(ws, item_off, item_off, nb + 1));
-  uint64_t nitems = 0;
-  MDJ_CUDA_TRY(cudaMemcpyAsync(&nitems, item_off + nb, 8, cudaMemcpyDeviceToHost, s));
-  MDJ_CUDA_TRY(cudaStreamSynchronize(s));
-  if (nitems >= (1ull << 31)) return MDJ_ERR_TOO_LARGE;
-  *nitems_out = (uint32_t)nitems;
-  *desc = (Item *)ws.get((size_t)(nitems ? nitems : 1) * sizeof(Item));
-  if (!*desc) return MDJ_ERR_OOM;
-  if (nitems) {
+  {
     TraceScope tr("join_expand", s);
-    const uint64_t want = (nitems + 255) / 256, most = (uint64_t)num_sms() * 8;
-    const unsigned g = (unsigned)(want < most ? want : most);
-    k_expand<<<g, 256, 0, s>>>(Ls.off, Rs.off, nb, cap, rch, item_off, (uint32_t)nitems, *desc);
+    const uint64_t want = ((uint64_t)ulim + 255) / 256, most = (uint64_t)num_sms() * 8;
+    const unsigned g = (unsigned)std::max<uint64_t>(1, want < most ? want : most);
+    k_expand<<<g, 256, 0, s>>>(Ls.off, Rs.off, nb, cap, rch, item_off, ulim, *desc, flags);
   }
   MDJ_LAUNCH_CHECK();
-  if (bucket_items)
-    *bucket_items = item_off;
-  else
-    ws.give_back(item_off);
+  *item_off_out = item_off;
   return MDJ_OK;
+}
+
+// Descriptor slots for a join without reading its item count: every bucket
+// one item, plus room for buckets that split into several (a count above it
+// costs one rerun with exact arrays).  MDJ_TEST_ITEM_BOUND (test hook) sets it.
+uint32_t item_bound(uint32_t nb, uint64_t nl, uint64_t nr, uint32_t cap, uint32_t rch) {
+  const char *e = getenv("MDJ_TEST_ITEM_BOUND");
+  if (e) {
+    const long long v = atoll(e);
+    if (v >= 1) return (uint32_t)std::min<long long>(v, (1ll << 31) - 1);
+  }
+  const uint64_t u = (uint64_t)nb + 2 * ((nl + cap - 1) / cap + (nr + rch - 1) / rch) + 1024;
+  return (uint32_t)std::min<uint64_t>(u, (1ull << 31) - 1);
 }
 
 int alloc_result(Workspace &ws, const Side &Ls, const Side &Rs, size_t key_width, uint64_t rows, mdj_result *r,
@@ -244,71 +267,85 @@ struct ItemMap {
 
 template <typename KeyT, int NT>
 int run_join_t(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, mdj_result *res,
-             bool force_ordered = false, ItemMap *map = nullptr) {
+               bool force_ordered = false, ItemMap *map = nullptr, uint32_t exact_items = 0) {
   cudaStream_t s = ws.stream();
-  // the optimistic output buffer first: its allocation overlaps the device
-  // work still queued, before make_items waits for the item count
+  const uint32_t rch = (uint32_t)kWPF * NT;
+  const uint32_t ulim = exact_items ? exact_items : item_bound(plan.nbuckets, Ls.nrows, Rs.nrows, plan.cap, rch);
+  const int ordered = force_ordered || ordered_output() ? 1 : 0;
+  // the optimistic output buffer; nothing below waits for the device until
+  // the join has run
   const uint64_t cap_rows = output_capacity_hint(Ls.nrows, Rs.nrows);
   mdj_result r;
   JOut o;
   MDJ_TRY(alloc_result(ws, Ls, Rs, sizeof(KeyT), cap_rows, &r, &o));
-  Item *desc;
-  uint32_t nitems;
-  int rc = make_items(ws, Ls, Rs, plan.nbuckets, plan.cap, (uint32_t)kWPF * NT, &desc, &nitems,
-                      map ? &map->bucket_items : nullptr);
-  // state[nitems] | item_off[nitems] | total | ticket | flags
-  const size_t words = 2 * (size_t)nitems + 4;
-  unsigned long long *state = rc == MDJ_OK ? (unsigned long long *)ws.get(words * 8) : nullptr;
-  if (rc == MDJ_OK && !state) rc = MDJ_ERR_OOM;
-  if (rc == MDJ_OK) rc = cuda_status(cudaMemsetAsync(state, 0, words * 8, s));
+  // state[ulim] | item_off[ulim] | total | ticket | flags
+  const size_t words = 2 * (size_t)ulim + 4;
+  unsigned long long *state = (unsigned long long *)ws.get(words * 8);
+  int rc = state ? MDJ_OK : MDJ_ERR_OOM;
+  uint64_t *item_off = state ? (uint64_t *)(state + ulim) : nullptr;
+  unsigned long long *total = state ? state + 2 * (size_t)ulim : nullptr;
+  uint32_t *ticket = (uint32_t *)(total + 1);
+  int *flags = (int *)(total + 2);
+  // the look-back slots start empty (ordered); the counters always
+  if (rc == MDJ_OK && ordered) rc = cuda_status(cudaMemsetAsync(state, 0, (size_t)ulim * 8, s));
+  if (rc == MDJ_OK) rc = cuda_status(cudaMemsetAsync(total, 0, 4 * 8, s));
+  Item *desc = nullptr;
+  uint64_t *bucket_items = nullptr;
+  if (rc == MDJ_OK) rc = make_items(ws, Ls, Rs, plan.nbuckets, plan.cap, rch, ulim, flags, &desc, &bucket_items);
   if (rc != MDJ_OK) {
     mdj_result_release(&r, ws.allocator(), (void *)s);
     return rc;
   }
-  uint64_t *item_off = (uint64_t *)(state + nitems);
-  unsigned long long *total = state + 2 * (size_t)nitems;
-  uint32_t *ticket = (uint32_t *)(total + 1);
-  int *flags = (int *)(total + 2);
+  const uint64_t *nitems_dev = bucket_items + plan.nbuckets;
 
   const size_t sm = WriteLayout<KeyT>(plan.cap).total;  // ~105 KB at cap 4096: two blocks per SM
-  if (nitems) {
-    int grid;
-    MDJ_TRY(resident_grid(k_join_write<KeyT, false, NT>, sm, nitems, &grid, NT));
+  int grid;
+  rc = resident_grid(k_join_write<KeyT, false, NT>, sm, ulim, &grid, NT);
+  if (rc == MDJ_OK) {
     TraceScope tr("join_write", s);
-    k_join_write<KeyT, false, NT><<<grid, NT, sm, s>>>(to_jside(Ls), to_jside(Rs), desc, nitems, plan.cap, ticket,
-                                                    state, item_off, total, cap_rows, flags, test_withhold_first(),
-                                                    force_ordered ? 1 : ordered_output(), bulk_ok(Ls), o);
+    k_join_write<KeyT, false, NT><<<grid, NT, sm, s>>>(to_jside(Ls), to_jside(Rs), desc, nitems_dev, ulim, plan.cap,
+                                                    ticket, state, item_off, total, cap_rows, flags,
+                                                    test_withhold_first(), ordered, bulk_ok(Ls), o);
+    rc = cuda_status(cudaGetLastError());
   }
-  cudaError_t e = cudaGetLastError();
   unsigned long long host_total = 0;
+  uint64_t host_items = 0;
   int host_flags[FLAG_WORDS] = {0, 0, 0, 0};
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&host_total, total, 8, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(host_flags, flags, sizeof host_flags, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) {
+  if (rc == MDJ_OK) rc = cuda_status(cudaMemcpyAsync(&host_total, total, 8, cudaMemcpyDeviceToHost, s));
+  if (rc == MDJ_OK) rc = cuda_status(cudaMemcpyAsync(host_flags, flags, sizeof host_flags, cudaMemcpyDeviceToHost, s));
+  if (rc == MDJ_OK) rc = cuda_status(cudaMemcpyAsync(&host_items, nitems_dev, 8, cudaMemcpyDeviceToHost, s));
+  if (rc == MDJ_OK) rc = cuda_status(cudaStreamSynchronize(s));
+  if (rc == MDJ_OK && host_flags[FLAG_TIMEOUT]) rc = MDJ_ERR_DEVICE_TIMEOUT;
+  if (rc == MDJ_OK && host_flags[FLAG_ITEMS]) {
+    // more items than the bound: again, with arrays of the exact count
     mdj_result_release(&r, ws.allocator(), (void *)s);
-    return cuda_status(e);
+    if (host_items >= (1ull << 31)) return MDJ_ERR_TOO_LARGE;
+    ws.give_back(desc);
+    ws.give_back(bucket_items);
+    ws.give_back(state);
+    return run_join_t<KeyT, NT>(ws, Ls, Rs, plan, res, force_ordered, map, (uint32_t)host_items);
   }
-  if (host_flags[FLAG_TIMEOUT]) {
+  if (rc != MDJ_OK) {
     mdj_result_release(&r, ws.allocator(), (void *)s);
-    return MDJ_ERR_DEVICE_TIMEOUT;
+    return rc;
   }
+  const uint32_t nitems = (uint32_t)host_items;
   const uint64_t m = host_total;
   if (m > cap_rows || m == 0) {
     // the join outgrew the optimistic buffer (or is empty): exact buffers,
-    // then one write pass at the offsets the fused pass recorded
+    // then one write pass at the offsets the first pass recorded
     mdj_result_release(&r, ws.allocator(), (void *)s);
     MDJ_TRY(alloc_result(ws, Ls, Rs, sizeof(KeyT), m, &r, &o));
     if (m > 0) {
-      int grid;
       MDJ_TRY(resident_grid(k_join_write<KeyT, true, NT>, sm, nitems, &grid, NT));
       MDJ_CUDA_TRY(cudaMemsetAsync(ticket, 0, 4, s));
       {
         TraceScope tr("join_write_exact", s);
-        k_join_write<KeyT, true, NT><<<grid, NT, sm, s>>>(to_jside(Ls), to_jside(Rs), desc, nitems, plan.cap, ticket,
-                                                       state, item_off, total, m, flags, 0, 0, bulk_ok(Ls), o);
+        k_join_write<KeyT, true, NT><<<grid, NT, sm, s>>>(to_jside(Ls), to_jside(Rs), desc, nitems_dev, ulim,
+                                                       plan.cap, ticket, state, item_off, total, m, flags, 0, 0,
+                                                       bulk_ok(Ls), o);
       }
-      e = cudaGetLastError();
+      const cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) {
         mdj_result_release(&r, ws.allocator(), (void *)s);
         return cuda_status(e);
@@ -318,6 +355,7 @@ int run_join_t(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, 
   r.nrows = m;
   *res = r;
   if (map) {
+    map->bucket_items = bucket_items;
     map->item_out = item_off;
     map->nitems = nitems;
   }

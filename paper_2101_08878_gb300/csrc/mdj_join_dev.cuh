@@ -41,7 +41,8 @@ struct Item {
 };
 
 // flags[] words shared by the join kernels and the host
-enum { FLAG_OVERFLOW = 0, FLAG_TIMEOUT = 1, FLAG_ABORT = 2, FLAG_WORDS = 4 };
+// (FLAG_ITEMS: the join has more work items than the arrays sized for it)
+enum { FLAG_OVERFLOW = 0, FLAG_TIMEOUT = 1, FLAG_ABORT = 2, FLAG_ITEMS = 3, FLAG_WORDS = 4 };
 
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 

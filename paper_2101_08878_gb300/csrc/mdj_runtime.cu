@@ -41,7 +41,7 @@ void *Workspace::get(size_t bytes) {
     if (!arena_ || arena_used_ + need > kArenaChunk) {
       void *c = raw_alloc(kArenaChunk);
       if (!c) return nullptr;
-      owned_.push_back(c);
+      chunks_.push_back(c);
       arena_ = (unsigned char *)c;
       arena_used_ = 0;
     }
@@ -54,6 +54,9 @@ void *Workspace::get(size_t bytes) {
   return p;
 }
 
+// Only buffers allocated on their own go back early; a small buffer lives in
+// an arena chunk (whose base may equal the buffer's address) until
+// release_all.
 void Workspace::give_back(void *p) {
   for (size_t i = 0; i < owned_.size(); i++)
     if (owned_[i] == p) {
@@ -69,6 +72,8 @@ void Workspace::release_caller(void *p) { raw_free(p); }
 void Workspace::release_all() {
   for (size_t i = owned_.size(); i-- > 0;) raw_free(owned_[i]);
   owned_.clear();
+  for (size_t i = chunks_.size(); i-- > 0;) raw_free(chunks_[i]);
+  chunks_.clear();
   arena_ = nullptr;
   arena_used_ = 0;
 }

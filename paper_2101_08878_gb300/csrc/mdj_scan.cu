@@ -1,9 +1,11 @@
 // Device-wide exclusive scan (prefix sum), used for partition offsets, the
 // per-(bucket, tile) scatter bases, work-item offsets and output offsets.
 //
-// Three launches, no inter-block waits: (1) each block reduces one chunk,
-// (2) one block scans the chunk sums, (3) each block rescans its chunk and adds
-// its chunk's base.  Each element is read twice and written once.
+// Up to kSmallScanMax elements: one launch of one block (each warp reduces
+// its span, a block scan of the warp sums, each warp rescans its span).
+// Larger: three launches, no inter-block waits: (1) each block reduces one
+// chunk, (2) one block scans the chunk sums, (3) each block rescans its chunk
+// and adds its chunk's base.  Each element is read twice and written once.
 #include "mdj_internal.cuh"
 
 namespace mdj {
@@ -64,9 +66,60 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const T *__restrict_
     }
 }
 
+constexpr int kSmallScanThreads = 1024;
+constexpr size_t kSmallScanMax = 1u << 15;
+constexpr int kSmallRows = 8;  // 32-element rows a warp loads per step
+
+// One block.  Warp w owns [w * per, (w + 1) * per); a step loads kSmallRows
+// rows of 32 consecutive elements (coalesced, all loads in flight at once).
+// `in` may equal `out`: every lane reads its elements before writing them.
+template <typename T>
+__global__ void __launch_bounds__(kSmallScanThreads) k_scan_small(const T *in, T *out, size_t n) {
+  __shared__ T scratch[33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr size_t step = 32 * kSmallRows;
+  const size_t per = ((n + 31) / 32 + step - 1) / step * step;
+  const size_t lo = min(n, (size_t)warp * per), hi = min(n, lo + per);
+  T s = 0;
+  for (size_t i0 = lo; i0 < hi; i0 += step) {
+    T v[kSmallRows];
+#pragma unroll
+    for (int j = 0; j < kSmallRows; j++) {
+      const size_t i = i0 + j * 32 + lane;
+      v[j] = i < hi ? in[i] : T(0);
+    }
+#pragma unroll
+    for (int j = 0; j < kSmallRows; j++) s += v[j];
+  }
+  const T wt = __shfl_sync(0xffffffffu, warp_inclusive_scan(s), 31);
+  T tot;
+  T carry = block_exclusive_scan<T>(lane == 31 ? wt : T(0), scratch, &tot);  // the warps before this one
+  for (size_t i0 = lo; i0 < hi; i0 += step) {
+    T v[kSmallRows];
+#pragma unroll
+    for (int j = 0; j < kSmallRows; j++) {
+      const size_t i = i0 + j * 32 + lane;
+      v[j] = i < hi ? in[i] : T(0);
+    }
+#pragma unroll
+    for (int j = 0; j < kSmallRows; j++) {
+      const T inc = warp_inclusive_scan(v[j]);
+      const size_t i = i0 + j * 32 + lane;
+      if (i < hi) out[i] = carry + inc - v[j];
+      carry += __shfl_sync(0xffffffffu, inc, 31);
+    }
+  }
+}
+
 template <typename T>
 int exclusive_scan(Workspace &ws, const T *in, T *out, size_t n) {
   if (n == 0) return MDJ_OK;
+  if (n <= kSmallScanMax) {
+    TraceScope tr("scan_small", ws.stream());
+    k_scan_small<T><<<1, kSmallScanThreads, 0, ws.stream()>>>(in, out, n);
+    MDJ_LAUNCH_CHECK();
+    return MDJ_OK;
+  }
   const size_t nb = (n + kScanChunk - 1) / kScanChunk;
   T *sums = (T *)ws.get(nb * sizeof(T));
   if (!sums) return MDJ_ERR_OOM;

@@ -229,6 +229,47 @@ def test_compaction_position_width_gate(tmp_path):
     assert out == ["0", "0", "0", "0", "1", "1"]
 
 
+def test_workspace_give_back_keeps_arena_chunks(tmp_path):
+    # Workspace (the library's per-call device memory) carves small buffers out
+    # of arena chunks; the first buffer of a chunk has the chunk's address, and
+    # giving it back early must not free the chunk the later buffers live in.
+    # Host code only: compiled with nvcc, run with a fake allocator that
+    # tracks live blocks (no GPU).
+    import shutil
+    import subprocess
+    nvcc = shutil.which("nvcc") or ("/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else None)
+    if not nvcc:
+        pytest.skip("no nvcc")
+    csrc = os.path.join(ROOT, "paper_2101_08878_gb300", "csrc")
+    src = tmp_path / "ws_test.cu"
+    src.write_text(
+        '#include <stdio.h>\n#include <set>\n#include "mdj_internal.cuh"\n'
+        'static std::set<void *> live;\n'
+        'static void *fa(size_t b, void *, void *) { void *p = malloc(b); live.insert(p); return p; }\n'
+        'static void fr(void *p, void *, void *) { live.erase(p); free(p); }\n'
+        'int main() {\n'
+        '  mdj_allocator a = {fa, fr, nullptr};\n'
+        '  {\n'
+        '    mdj::Workspace ws(&a, nullptr);\n'
+        '    void *s1 = ws.get(64);\n'
+        '    void *big = ws.get(4u << 20);\n'
+        '    ws.give_back(s1);\n'
+        '    void *s2 = ws.get(64);\n'
+        '    printf("%d %d %d\\n", (int)live.size(), (int)live.count(s1), s2 != nullptr);\n'
+        '    ws.give_back(big);\n'
+        '    printf("%d\\n", (int)live.size());\n'
+        '  }\n'
+        '  printf("%d\\n", (int)live.size());\n'
+        '  return 0;\n}\n')
+    exe = tmp_path / "ws_test"
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-I", os.path.join(ROOT, "include"),
+                    "-I", csrc, str(src), os.path.join(csrc, "mdj_runtime.cu"), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    # chunk + large buffer live, the chunk (at s1's address) kept; then the
+    # large buffer alone released; nothing left after the workspace
+    assert out == ["2", "1", "1", "1", "0"]
+
+
 def test_noalloc_size_limit_at_p8(lib):
     # mdj_partition_noalloc's fixed array holds P*T + ceil(P*T/4096) + P + 1
     # words (T = ceil(nrows / 4096)) of 4 Mi; at P = 8 that admits

@@ -207,6 +207,16 @@ def test_output_buffer_overflow_takes_exact_pass(monkeypatch, ordered):
     assert got["key"].size == 35_000
 
 
+@pytest.mark.parametrize("ordered", ["0", "1"])
+def test_item_count_above_bound_reruns_exactly(monkeypatch, ordered):
+    # the join's descriptor arrays are sized without reading its item count;
+    # a bound of one item forces the rerun with exact arrays
+    monkeypatch.setenv("MDJ_TEST_ITEM_BOUND", "1")
+    monkeypatch.setenv("MDJ_ORDERED_OUTPUT", ordered)
+    (lk, lp), (rk, rp) = datagen.zipf_tables(30_000, 50_000, 40_000, 1.1, seed=24)
+    _check([lk, lp], [rk, rp], 8)
+
+
 def test_bounded_wait_reports_timeout_and_context_survives(monkeypatch):
     # item 0 withholds its count (test hook): every look-back wait must give up
     # after its bound, the call must say so, and the next call must work
