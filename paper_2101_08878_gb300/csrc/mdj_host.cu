@@ -439,23 +439,69 @@ mdj_result result_piece(const mdj_result &r, uint64_t q0, uint64_t n) {
   return p;
 }
 
+// The right table's copies in, issued on their own stream once the left
+// side's partition is queued (merge_steps' hook): the link carries them while
+// the device partitions the left side.
+struct LateRight {
+  const mdj_table *host;
+  mdj_col *cols;
+  cudaStream_t s, sc;
+  cudaEvent_t alloced, ready;
+};
+int copy_right_in(void *ctx) {
+  LateRight &x = *(LateRight *)ctx;
+  MDJ_CUDA_TRY(cudaStreamWaitEvent(x.sc, x.alloced, 0));
+  for (int j = 0; j < x.host->ncols; j++) {
+    const size_t bytes = x.host->nrows * (size_t)dtype_width(x.host->cols[j].dtype);
+    if (bytes)
+      MDJ_CUDA_TRY(cudaMemcpyAsync((void *)x.cols[j].data, x.host->cols[j].data, bytes, cudaMemcpyHostToDevice, x.sc));
+  }
+  MDJ_CUDA_TRY(cudaEventRecord(x.ready, x.sc));
+  MDJ_CUDA_TRY(cudaStreamWaitEvent(x.s, x.ready, 0));
+  return MDJ_OK;
+}
+
 // Both tables fit one bucket of the budget: they go to the device once and
-// are merged in place.  An inner merge runs mdj_merge and hands its result to
-// the sink in windows that point into it; the other join types stream their
-// rows through one window buffer.  Row ids are already input row ids.
+// are merged in place.  An inner merge runs mdj_merge's steps, the right
+// table's copies overlapping the left side's partition, and hands its result
+// to the sink in windows that point into it; the other join types stream
+// their rows through one window buffer.  Row ids are already input row ids.
 int merge_resident(const mdj_table *left, int32_t lk, const mdj_table *right, int32_t rk, uint32_t P, int32_t how,
                    uint64_t window, mdj_sink sink, void *sink_ctx, const mdj_allocator *alloc, cudaStream_t s,
                    uint64_t *total_rows) {
+  // the copy stream and events; drained before the workspace releases the
+  // right table's buffers (declared after it, destroyed first)
   Workspace ws(alloc, s);
+  struct CopyStream {
+    cudaStream_t sc = nullptr;
+    cudaEvent_t alloced = nullptr, ready = nullptr;
+    ~CopyStream() {
+      if (sc) cudaStreamSynchronize(sc);
+      if (alloced) cudaEventDestroy(alloced);
+      if (ready) cudaEventDestroy(ready);
+      if (sc) cudaStreamDestroy(sc);
+    }
+  } cs;
   mdj_col lc[MDJ_MAX_COLS], rc[MDJ_MAX_COLS];
   mdj_table lt, rt;
   MDJ_TRY(table_to_device(ws, left, lc, &lt));
-  MDJ_TRY(table_to_device(ws, right, rc, &rt));
   uint64_t produced = 0;
   int rc2 = MDJ_OK;
   if (how == MDJ_INNER) {
+    for (int j = 0; j < right->ncols; j++) {
+      unsigned char *d = dev_block(ws, right->nrows * (size_t)dtype_width(right->cols[j].dtype));
+      if (!d) return MDJ_ERR_OOM;
+      rc[j].data = d;
+      rc[j].dtype = right->cols[j].dtype;
+    }
+    rt = {rc, right->ncols, right->nrows};
+    MDJ_CUDA_TRY(cudaStreamCreateWithFlags(&cs.sc, cudaStreamNonBlocking));
+    MDJ_CUDA_TRY(cudaEventCreateWithFlags(&cs.alloced, cudaEventDisableTiming));
+    MDJ_CUDA_TRY(cudaEventCreateWithFlags(&cs.ready, cudaEventDisableTiming));
+    MDJ_CUDA_TRY(cudaEventRecord(cs.alloced, s));  // the blocks may have served earlier work of s
+    LateRight late = {right, rc, s, cs.sc, cs.alloced, cs.ready};
     mdj_result res;
-    MDJ_TRY(mdj_merge(&lt, lk, &rt, rk, P, alloc, (void *)s, &res));
+    MDJ_TRY(merge_steps(&lt, lk, &rt, rk, P, alloc, (void *)s, &res, copy_right_in, &late));
     rc2 = cuda_status(cudaStreamSynchronize(s));
     for (uint64_t q0 = 0; q0 < res.nrows && rc2 == MDJ_OK; q0 += window) {
       const uint64_t n = std::min(window, res.nrows - q0);
@@ -465,6 +511,7 @@ int merge_resident(const mdj_table *left, int32_t lk, const mdj_table *right, in
     }
     mdj_result_release(&res, alloc, (void *)s);
   } else {
+    MDJ_TRY(table_to_device(ws, right, rc, &rt));
     Workspace wbuf(alloc, s);
     mdj_result piece;
     memset(&piece, 0, sizeof piece);

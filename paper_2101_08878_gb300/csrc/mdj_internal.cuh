@@ -337,6 +337,11 @@ int stable_partition_scratch(const mdj_table *t, int32_t key_col, uint32_t P, vo
                              uint32_t *out_rid, int64_t *out_offsets, uint32_t *scratch, size_t scratch_words,
                              cudaStream_t s);
 
+// mdj_merge's steps with a hook between the two sides' partitions
+// (csrc/mdj_join.cu).
+int merge_steps(const mdj_table *left, int32_t lk, const mdj_table *right, int32_t rk, uint32_t P,
+                const mdj_allocator *alloc, void *stream, mdj_result *out, int (*after_left)(void *), void *ctx);
+
 // mdj_count_checksum: the pair count and checksum of the inner join, from
 // the streamed output's grouping (every key group of the build side gathered
 // once, each probe row told its group): count = sum of the probe rows' group

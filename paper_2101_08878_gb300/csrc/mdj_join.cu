@@ -409,6 +409,33 @@ uint32_t cap_from_env() {
   return cap;
 }
 
+}  // namespace
+
+// The merge's steps; `after_left` (if set) runs once the left side's
+// partition is queued and before the right side's is, so that a caller can
+// bring the right side's columns in meanwhile.
+int merge_steps(const mdj_table *left, int32_t lk, const mdj_table *right, int32_t rk, uint32_t P,
+                const mdj_allocator *alloc, void *stream, mdj_result *out, int (*after_left)(void *), void *ctx) {
+  MDJ_TRY(check_table(left, lk));
+  MDJ_TRY(check_table(right, rk));
+  if (P < 1 || P > MDJ_MAX_PARTITIONS) return MDJ_ERR_INVALID_ARG;
+  if (left->cols[lk].dtype != right->cols[rk].dtype) return MDJ_ERR_INVALID_ARG;
+  if (!out) return MDJ_ERR_INVALID_ARG;
+  memset(out, 0, sizeof *out);
+  Workspace ws(alloc, (cudaStream_t)stream);
+  Plan plan = make_plan(left->nrows, P, cap_from_env(), P > 1);
+  // ordered output is deterministic only over stable partition passes
+  plan.stable = ordered_output() != 0;
+  const bool k64 = left->cols[lk].dtype == MDJ_I64;
+  Side L, R;
+  MDJ_TRY(partition_side(ws, left, lk, plan, &L));
+  if (after_left) MDJ_TRY(after_left(ctx));
+  MDJ_TRY(partition_side(ws, right, rk, plan, &R));
+  return k64 ? run_join<int64_t>(ws, L, R, plan, out) : run_join<int32_t>(ws, L, R, plan, out);
+}
+
+namespace {
+
 int merge_impl(const mdj_table *left, int32_t lk, const mdj_table *right, int32_t rk, uint32_t P,
                const mdj_allocator *alloc, void *stream, mdj_result *out, bool checksum_mode, uint64_t *count,
                uint64_t *checksum) {
@@ -421,15 +448,7 @@ int merge_impl(const mdj_table *left, int32_t lk, const mdj_table *right, int32_
   if (out) memset(out, 0, sizeof *out);
 
   if (checksum_mode) return grouped_count_checksum(left, lk, right, rk, P, alloc, stream, count, checksum);
-  Workspace ws(alloc, (cudaStream_t)stream);
-  Plan plan = make_plan(left->nrows, P, cap_from_env(), P > 1);
-  // ordered output is deterministic only over stable partition passes
-  plan.stable = ordered_output() != 0;
-  const bool k64 = left->cols[lk].dtype == MDJ_I64;
-  Side L, R;
-  MDJ_TRY(partition_side(ws, left, lk, plan, &L));
-  MDJ_TRY(partition_side(ws, right, rk, plan, &R));
-  return k64 ? run_join<int64_t>(ws, L, R, plan, out) : run_join<int32_t>(ws, L, R, plan, out);
+  return merge_steps(left, lk, right, rk, P, alloc, stream, out, nullptr, nullptr);
 }
 
 
