@@ -57,6 +57,16 @@ def test_host_copy_paths_and_unaligned_columns(monkeypatch, memcpy):
     _check(left, right, 8, "inner")
 
 
+@pytest.mark.parametrize("kd", [np.int64, np.int32])
+def test_host_tables_that_fit_copy_right_while_left_partitions(kd):
+    # a budget that holds both tables: one bucket, the right table copied in
+    # on its own stream while the left side is partitioned
+    (lk, lp), (rk, rp) = datagen.random_tables(2_000_000, 3_000_000, 2_500_000, seed=56, key_dtype=kd,
+                                               pay_dtype=np.float64)
+    extra = np.arange(rk.size, dtype=np.int32) * 3
+    _check([lk, lp], [rp, rk, extra], 8, "inner", lk=0, rk=1, budget=1 << 30)
+
+
 @pytest.mark.parametrize("how", ["inner", "outer"])
 def test_host_heavy_key_spans_many_windows(how):
     rng = np.random.default_rng(52)
