@@ -217,6 +217,44 @@ def merge_multi(left_cols, right_cols, left_keys, right_keys):
     return lrow[order], rrow[order]
 
 
+def merge_multi_how(left_cols, right_cols, left_keys, right_keys, how: str):
+    """The merge variants on key tuples (a merge variant, as merge_table_how on
+    a single key).  "inner" is merge_multi; "left" adds every left row that no
+    right row matches on the whole tuple, once, with no right row; "right"
+    adds every unmatched right row, with no left row; "outer" adds both.
+    Returns a dict: left_row, right_row (NO_ROW for a missing side) and the
+    output columns in the order of mdj_merge_multi: left_cols = the key
+    columns in left_keys order, then the left table's other columns; right_cols
+    = the right table's other columns.  A missing side's columns are all-zero
+    bits, except that the key columns of a right-only row hold the right
+    row's tuple (the key is the present side's).  Canonical order: (left_row,
+    right_row) with NO_ROW last."""
+    if how not in ("inner", "left", "right", "outer"):
+        raise ValueError(f"unknown join type {how!r}")
+    lrow, rrow = merge_multi(left_cols, right_cols, left_keys, right_keys)
+    nl = len(left_cols[0]) if len(left_cols) else 0
+    nr = len(right_cols[0]) if len(right_cols) else 0
+    ul = np.setdiff1d(np.arange(nl), lrow) if how in ("left", "outer") else np.empty(0, np.int64)
+    ur = np.setdiff1d(np.arange(nr), rrow) if how in ("right", "outer") else np.empty(0, np.int64)
+    lrow_all = np.concatenate([lrow.astype(np.int64), ul, np.full(ur.size, NO_ROW, np.int64)])
+    rrow_all = np.concatenate([rrow.astype(np.int64), np.full(ul.size, NO_ROW, np.int64), ur])
+    lorder = list(left_keys) + [j for j in range(len(left_cols)) if j not in left_keys]
+    rorder = [j for j in range(len(right_cols)) if j not in right_keys]
+    left_out = []
+    for pos, j in enumerate(lorder):
+        c = np.asarray(left_cols[j])
+        right_part = (np.asarray(right_cols[right_keys[pos]])[ur] if pos < len(left_keys)
+                      else np.zeros(ur.size, c.dtype))
+        left_out.append(np.concatenate([c[lrow.astype(np.int64)], c[ul], right_part.astype(c.dtype)]))
+    right_out = []
+    for j in rorder:
+        c = np.asarray(right_cols[j])
+        right_out.append(np.concatenate([c[rrow.astype(np.int64)], np.zeros(ul.size, c.dtype), c[ur]]))
+    order = np.lexsort((rrow_all, lrow_all))
+    return {"left_row": lrow_all[order].astype(np.uint32), "right_row": rrow_all[order].astype(np.uint32),
+            "left_cols": [c[order] for c in left_out], "right_cols": [c[order] for c in right_out]}
+
+
 def brute_force(lkeys, rkeys):
     """Nested-loop inner join (independent of the C code) for tiny inputs.
 

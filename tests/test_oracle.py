@@ -480,3 +480,49 @@ def test_merge_multi_is_not_a_merge_on_the_first_column():
     rb = np.array([6, 5, 9], np.int64)
     lrow, rrow = oracle.merge_multi([a, b], [a, rb], [0, 1], [0, 1])
     assert list(zip(lrow.tolist(), rrow.tolist())) == [(0, 1), (1, 0)]
+
+
+# ------------------------------------------------------ outer joins on tuples
+
+@pytest.mark.parametrize("how", ["inner", "left", "right", "outer"])
+def test_merge_multi_how_on_one_key_is_the_single_key_merge(how):
+    # with one key column the tuple merge is the plain merge: same row pairs,
+    # the same unmatched rows and the same zeroed or coalesced columns
+    rng = np.random.default_rng(81)
+    left = [rng.integers(0, 60, 400).astype(np.int64), rng.random(400)]
+    right = [rng.random(300), rng.integers(30, 90, 300).astype(np.int64)]
+    a = oracle.merge_multi_how(left, right, [0], [1], how)
+    b = oracle.merge_table_how(left, right, how, 0, 1)
+    ka = np.lexsort((a["right_row"], a["left_row"]))
+    kb = np.lexsort((b["right_row"], b["left_row"]))
+    assert np.array_equal(a["left_row"][ka], b["left_row"][kb])
+    assert np.array_equal(a["right_row"][ka], b["right_row"][kb])
+    assert np.array_equal(a["left_cols"][0][ka], b["key"][kb])
+    assert np.array_equal(a["left_cols"][1][ka].view(np.uint64), b["left_cols"][0][kb].view(np.uint64))
+    assert np.array_equal(a["right_cols"][0][ka].view(np.uint64), b["right_cols"][0][kb].view(np.uint64))
+
+
+@pytest.mark.parametrize("how", ["inner", "left", "right", "outer"])
+def test_merge_multi_how_matches_nested_loops_on_pairs(how):
+    # the definition written out on tiny tables: (i, j) joins when both key
+    # columns agree; a row with no partner on the kept side appears once
+    rng = np.random.default_rng(82)
+    la, lb = rng.integers(0, 4, 40).astype(np.int32), rng.integers(0, 3, 40).astype(np.int64)
+    ra, rb = rng.integers(1, 5, 30).astype(np.int32), rng.integers(0, 3, 30).astype(np.int64)
+    left, right = [la, lb, np.arange(40, dtype=np.int64) * 10], [rb, ra, np.arange(30, dtype=np.int64) + 7]
+    got = oracle.merge_multi_how(left, right, [0, 1], [1, 0], how)
+    pairs = [(i, j) for i in range(40) for j in range(30) if la[i] == ra[j] and lb[i] == rb[j]]
+    rows = list(pairs)
+    if how in ("left", "outer"):
+        rows += [(i, oracle.NO_ROW) for i in range(40) if not any(p[0] == i for p in pairs)]
+    if how in ("right", "outer"):
+        rows += [(oracle.NO_ROW, j) for j in range(30) if not any(p[1] == j for p in pairs)]
+    rows.sort()
+    assert list(zip(got["left_row"].tolist(), got["right_row"].tolist())) == rows
+    for k, (i, j) in enumerate(rows):
+        # key columns: the present side's tuple; other columns: zero when missing
+        want_a = la[i] if i != oracle.NO_ROW else ra[j]
+        want_b = lb[i] if i != oracle.NO_ROW else rb[j]
+        assert got["left_cols"][0][k] == want_a and got["left_cols"][1][k] == want_b
+        assert got["left_cols"][2][k] == (i * 10 if i != oracle.NO_ROW else 0)
+        assert got["right_cols"][0][k] == (j + 7 if j != oracle.NO_ROW else 0)
