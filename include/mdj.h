@@ -353,6 +353,23 @@ MDJ_API int mdj_merge_multi(const mdj_table *left, const int32_t *left_keys, con
                             void *stream, mdj_result *out);
 
 /*
+ * mdj_merge_multi_how - mdj_merge_multi for every join type (`how`: inner,
+ * left, right or outer; a merge variant on key tuples).  The inner merge's
+ * verified pairs come first; then, for left and outer, every left row that no
+ * right row matches on the whole tuple, once; then, for right and outer,
+ * every unmatched right row, once.  Layout as mdj_merge_multi: left_cols =
+ * the key columns in left_keys order, then the left table's other columns;
+ * right_cols = the right table's other columns.  A missing side has row id
+ * 0xFFFFFFFF and all-zero bits in its columns, except that the key columns
+ * of a right-only row hold that row's tuple (the key is the present side's,
+ * as in mdj_stream_open).  Errors as mdj_merge_multi, and MDJ_ERR_INVALID_ARG
+ * for another `how`.  Synchronises `stream`.
+ */
+MDJ_API int mdj_merge_multi_how(const mdj_table *left, const int32_t *left_keys, const mdj_table *right,
+                                const int32_t *right_keys, int32_t nkeys, uint32_t P, int32_t how,
+                                const mdj_allocator *alloc, void *stream, mdj_result *out);
+
+/*
  * mdj_merge_host - the merge of HOST-resident tables that need not fit device
  * memory.  The paper's runtime sends messages above MPI's 2 GB count limit as
  * 1 GB chunks (Sec. IV-B); here the tables themselves pass through the device

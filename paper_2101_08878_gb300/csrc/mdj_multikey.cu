@@ -258,8 +258,176 @@ int merge_multi_impl(const mdj_table *left, const int32_t *lkeys, const mdj_tabl
   return MDJ_OK;
 }
 
+// ------------------------------------------------ outer joins on tuples
+//
+// The inner merge's verified pairs mark the rows they use; the rows of a kept
+// side that no pair uses follow the pairs, each once, with its own row id,
+// NO_ROW for the other side and zeroed columns for it, and the key columns
+// filled from the present side's tuple.
+
+constexpr uint32_t kNoRowId = 0xFFFFFFFFu;
+
+// flag[rows[i]] = 1 for every pair i (plain stores; equal values race benignly).
+__global__ void k_mark_rows(const uint32_t *__restrict__ rows, uint64_t m, uint32_t *__restrict__ flag) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) flag[rows[i]] = 1u;
+}
+
+// flag[i] = 1 for the rows no pair used (i < n), flag[n] = 0: the scan input
+// of their output positions.
+__global__ void k_unmarked(uint32_t *__restrict__ flag, uint64_t n) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += stride)
+    flag[i] = i < n ? (flag[i] ^ 1u) : 0u;
+}
+
+struct EmitCols {
+  const void *src[2 * MDJ_MAX_COLS];  // NULL: zero for these rows
+  void *dst[2 * MDJ_MAX_COLS];
+  int32_t width[2 * MDJ_MAX_COLS];
+  int32_t n;
+};
+
+// Unmatched row i (pos[i + 1] != pos[i]) goes to base + pos[i].
+__global__ void k_emit_unmatched(const uint32_t *__restrict__ pos, uint64_t n, uint64_t base,
+                                 uint32_t *__restrict__ own_row, uint32_t *__restrict__ other_row,
+                                 const __grid_constant__ EmitCols C) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint32_t p = pos[i];
+    if (pos[i + 1] == p) continue;
+    const uint64_t o = base + p;
+    own_row[o] = (uint32_t)i;
+    other_row[o] = kNoRowId;
+    for (int c = 0; c < C.n; c++) {
+      if (C.width[c] == 8)
+        ((uint64_t *)C.dst[c])[o] = C.src[c] ? ((const uint64_t *)C.src[c])[i] : 0ull;
+      else
+        ((uint32_t *)C.dst[c])[o] = C.src[c] ? ((const uint32_t *)C.src[c])[i] : 0u;
+    }
+  }
+}
+
+int merge_multi_how_impl(const mdj_table *left, const int32_t *lkeys, const mdj_table *right, const int32_t *rkeys,
+                         int32_t nkeys, uint32_t P, int32_t how, const mdj_allocator *alloc, void *stream,
+                         mdj_result *out) {
+  if (how < MDJ_INNER || how > MDJ_OUTER) return MDJ_ERR_INVALID_ARG;
+  mdj_result in;
+  MDJ_TRY(merge_multi_impl(left, lkeys, right, rkeys, nkeys, P, alloc, stream, &in));
+  if (how == MDJ_INNER) {
+    *out = in;
+    return MDJ_OK;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace ws(alloc, s);
+  const bool keep_l = how == MDJ_LEFT || how == MDJ_OUTER, keep_r = how == MDJ_RIGHT || how == MDJ_OUTER;
+  const uint64_t m = in.nrows;
+  // unmatched rows of each kept side: marks, then positions by a scan
+  uint32_t *pos[2] = {nullptr, nullptr};
+  uint64_t cnt[2] = {0, 0};
+  int rc = MDJ_OK;
+  for (int side = 0; side < 2 && rc == MDJ_OK; side++) {
+    if (!(side == 0 ? keep_l : keep_r)) continue;
+    const uint64_t n = side == 0 ? left->nrows : right->nrows;
+    uint32_t *flag = (uint32_t *)ws.get((size_t)(n + 1) * 4);
+    pos[side] = (uint32_t *)ws.get((size_t)(n + 1) * 4);
+    if (!flag || !pos[side]) rc = MDJ_ERR_OOM;
+    if (rc == MDJ_OK) rc = cuda_status(cudaMemsetAsync(flag, 0, (size_t)(n + 1) * 4, s));
+    if (rc == MDJ_OK && m) {
+      TraceScope tr("tuple_mark", s);
+      k_mark_rows<<<grid_of(m), 256, 0, s>>>(side == 0 ? in.left_row : in.right_row, m, flag);
+      rc = cuda_status(cudaGetLastError());
+    }
+    if (rc == MDJ_OK) {
+      k_unmarked<<<grid_of(n + 1), 256, 0, s>>>(flag, n);
+      rc = cuda_status(cudaGetLastError());
+    }
+    if (rc == MDJ_OK) rc = exclusive_scan_u32(ws, flag, pos[side], (size_t)n + 1);
+    uint32_t host_cnt = 0;
+    if (rc == MDJ_OK) rc = cuda_status(cudaMemcpyAsync(&host_cnt, pos[side] + n, 4, cudaMemcpyDeviceToHost, s));
+    if (rc == MDJ_OK) rc = cuda_status(cudaStreamSynchronize(s));
+    cnt[side] = host_cnt;
+  }
+  // the result: the pairs, then left-only rows, then right-only rows
+  mdj_result r;
+  memset(&r, 0, sizeof r);
+  r.key_dtype = 0;
+  r.n_left_cols = in.n_left_cols;
+  r.n_right_cols = in.n_right_cols;
+  for (int j = 0; j < r.n_left_cols; j++) r.left_dtypes[j] = in.left_dtypes[j];
+  for (int j = 0; j < r.n_right_cols; j++) r.right_dtypes[j] = in.right_dtypes[j];
+  const uint64_t M = m + cnt[0] + cnt[1];
+  r.nrows = M;
+  auto alloc_copy = [&](void **dst, const void *src, int width) -> int {
+    *dst = M ? ws.get_owned_by_caller((size_t)M * width) : nullptr;
+    if (M && !*dst) return MDJ_ERR_OOM;
+    if (m) return cuda_status(cudaMemcpyAsync(*dst, src, (size_t)m * width, cudaMemcpyDeviceToDevice, s));
+    return MDJ_OK;
+  };
+  if (rc == MDJ_OK) rc = alloc_copy((void **)&r.left_row, in.left_row, 4);
+  if (rc == MDJ_OK) rc = alloc_copy((void **)&r.right_row, in.right_row, 4);
+  for (int j = 0; rc == MDJ_OK && j < r.n_left_cols; j++)
+    rc = alloc_copy(&r.left_cols[j], in.left_cols[j], dtype_width(r.left_dtypes[j]));
+  for (int j = 0; rc == MDJ_OK && j < r.n_right_cols; j++)
+    rc = alloc_copy(&r.right_cols[j], in.right_cols[j], dtype_width(r.right_dtypes[j]));
+  // source columns of the output, side by side: left output column c is the
+  // left table's column lsrc[c] (keys in lkeys order, then the others); right
+  // output column c is the right table's column rsrc[c]
+  int lsrc[MDJ_MAX_COLS], rsrc[MDJ_MAX_COLS];
+  {
+    int c = 0;
+    for (int a = 0; a < nkeys; a++) lsrc[c++] = lkeys[a];
+    for (int j = 0; j < left->ncols; j++)
+      if (!is_key(lkeys, nkeys, j)) lsrc[c++] = j;
+    c = 0;
+    for (int j = 0; j < right->ncols; j++)
+      if (!is_key(rkeys, nkeys, j)) rsrc[c++] = j;
+  }
+  for (int side = 0; side < 2 && rc == MDJ_OK; side++) {
+    if (!cnt[side]) continue;
+    EmitCols C;
+    memset(&C, 0, sizeof C);
+    for (int c = 0; c < r.n_left_cols; c++) {
+      C.dst[C.n] = r.left_cols[c];
+      C.width[C.n] = dtype_width(r.left_dtypes[c]);
+      if (side == 0)
+        C.src[C.n] = left->cols[lsrc[c]].data;
+      else
+        C.src[C.n] = c < nkeys ? right->cols[rkeys[c]].data : nullptr;  // the right row's tuple
+      C.n++;
+    }
+    for (int c = 0; c < r.n_right_cols; c++) {
+      C.dst[C.n] = r.right_cols[c];
+      C.width[C.n] = dtype_width(r.right_dtypes[c]);
+      C.src[C.n] = side == 1 ? right->cols[rsrc[c]].data : nullptr;
+      C.n++;
+    }
+    const uint64_t n = side == 0 ? left->nrows : right->nrows;
+    const uint64_t base = side == 0 ? m : m + cnt[0];
+    TraceScope tr("tuple_unmatched", s);
+    k_emit_unmatched<<<grid_of(n), 256, 0, s>>>(pos[side], n, base, side == 0 ? r.left_row : r.right_row,
+                                                side == 0 ? r.right_row : r.left_row, C);
+    rc = cuda_status(cudaGetLastError());
+  }
+  if (rc == MDJ_OK) rc = cuda_status(cudaStreamSynchronize(s));
+  mdj_result_release(&in, alloc, stream);
+  if (rc != MDJ_OK) {
+    mdj_result_release(&r, alloc, stream);
+    return rc;
+  }
+  *out = r;
+  return MDJ_OK;
+}
+
 }  // namespace
 }  // namespace mdj
+
+extern "C" int mdj_merge_multi_how(const mdj_table *left, const int32_t *left_keys, const mdj_table *right,
+                                   const int32_t *right_keys, int32_t nkeys, uint32_t P, int32_t how,
+                                   const mdj_allocator *alloc, void *stream, mdj_result *out) {
+  if (out) memset(out, 0, sizeof *out);
+  return mdj::merge_multi_how_impl(left, left_keys, right, right_keys, nkeys, P, how, alloc, stream, out);
+}
 
 extern "C" int mdj_merge_multi(const mdj_table *left, const int32_t *left_keys, const mdj_table *right,
                                const int32_t *right_keys, int32_t nkeys, uint32_t P, const mdj_allocator *alloc,

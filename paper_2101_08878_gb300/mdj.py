@@ -39,7 +39,7 @@ _MDJ_TO_TORCH = {v: k for k, v in _TORCH_TO_MDJ.items()}
 EXPORTED = [
     "mdj_partition", "mdj_partition_noalloc", "mdj_join", "mdj_merge", "mdj_count_checksum", "mdj_join_batch",
     "mdj_merge_batch", "mdj_stream_open", "mdj_stream_emit", "mdj_stream_next", "mdj_stream_rows",
-    "mdj_stream_close", "mdj_transpose_add", "mdj_merge_host", "mdj_merge_multi",
+    "mdj_stream_close", "mdj_transpose_add", "mdj_merge_host", "mdj_merge_multi", "mdj_merge_multi_how",
     "mdj_result_release",
     "mdj_status_string", "mdj_last_error", "mdj_version", "mdj_profile_enable", "mdj_profile_reset",
     "mdj_profile_collect", "mdj_profile_count", "mdj_profile_get",
@@ -144,6 +144,9 @@ def load(path: str = LIB_PATH):
         lib.mdj_merge_multi.restype = ctypes.c_int
         lib.mdj_merge_multi.argtypes = [P(MdjTable), P(i32), P(MdjTable), P(i32), i32, u32, P(MdjAllocator), vp,
                                         P(MdjResult)]
+        lib.mdj_merge_multi_how.restype = ctypes.c_int
+        lib.mdj_merge_multi_how.argtypes = [P(MdjTable), P(i32), P(MdjTable), P(i32), i32, u32, i32,
+                                            P(MdjAllocator), vp, P(MdjResult)]
         lib.mdj_merge_host.restype = ctypes.c_int
         lib.mdj_merge_host.argtypes = [P(MdjTable), i32, P(MdjTable), i32, u32, i32, u64, SINK_FN, vp,
                                        P(MdjAllocator), vp, P(u64)]
@@ -311,10 +314,15 @@ def mdj_merge(left_cols: Sequence[torch.Tensor], right_cols: Sequence[torch.Tens
 
 
 def mdj_merge_multi(left_cols: Sequence[torch.Tensor], right_cols: Sequence[torch.Tensor], left_keys: Sequence[int],
-                    right_keys: Sequence[int], P: int) -> JoinResult:
-    """Inner merge on several key columns (see mdj.h).  The result's key is
+                    right_keys: Sequence[int], P: int, how: str = "inner") -> JoinResult:
+    """Merge on several key columns (mdj_merge_multi / mdj_merge_multi_how in
+    mdj.h), `how` one of inner, left, right, outer.  The result's key is
     empty; left_cols = the left key columns (in left_keys order), then the
-    left table's other columns; right_cols = the right table's other columns."""
+    left table's other columns; right_cols = the right table's other columns.
+    A missing side has row id NO_ROW and zeroed columns; a right-only row's
+    key columns hold its own tuple."""
+    if how not in HOW:
+        raise ValueError(f"how must be one of {sorted(HOW)}")
     lib = load()
     dev = left_cols[0].device
     lt, lkeep = _table(left_cols)
@@ -326,8 +334,12 @@ def mdj_merge_multi(left_cols: Sequence[torch.Tensor], right_cols: Sequence[torc
     rk = (ctypes.c_int32 * max(nk, 1))(*right_keys)
     alloc = TorchAllocator(dev)
     res = MdjResult()
-    rc = lib.mdj_merge_multi(ctypes.byref(lt), lk, ctypes.byref(rt), rk, nk, P, ctypes.byref(alloc.struct),
-                             _stream_handle(dev), ctypes.byref(res))
+    if how == "inner":
+        rc = lib.mdj_merge_multi(ctypes.byref(lt), lk, ctypes.byref(rt), rk, nk, P, ctypes.byref(alloc.struct),
+                                 _stream_handle(dev), ctypes.byref(res))
+    else:
+        rc = lib.mdj_merge_multi_how(ctypes.byref(lt), lk, ctypes.byref(rt), rk, nk, P, HOW[how],
+                                     ctypes.byref(alloc.struct), _stream_handle(dev), ctypes.byref(res))
     _check(rc, "mdj_merge_multi")
     return _adopt_result(res, alloc)
 

@@ -81,3 +81,61 @@ def test_no_match_and_empty():
     b = np.zeros(1000, np.int64)
     assert _run_and_check([a, b], [a, b + 1], [0, 1], [0, 1], 4) == 0
     assert _run_and_check([a[:0], b[:0]], [a, b], [0, 1], [0, 1], 4) == 0
+
+
+# ------------------------------------------------------ outer joins on tuples
+
+def _run_how(left, right, lkeys, rkeys, P, how):
+    mdj = _mdj()
+    res = mdj.mdj_merge_multi([torch.from_numpy(c).to(DEV) for c in left],
+                              [torch.from_numpy(c).to(DEV) for c in right], lkeys, rkeys, P, how=how)
+    torch.cuda.synchronize()
+    want = oracle.merge_multi_how(left, right, lkeys, rkeys, how)
+    assert res.nrows == want["left_row"].size
+    lrow = res.left_row.cpu().numpy().view(np.uint32)
+    rrow = res.right_row.cpu().numpy().view(np.uint32)
+    order = np.lexsort((rrow, lrow))
+    assert np.array_equal(lrow[order], want["left_row"]) and np.array_equal(rrow[order], want["right_row"])
+    bits = (lambda a: a.view(np.uint32 if a.dtype.itemsize == 4 else np.uint64))
+    assert len(res.left_cols) == len(want["left_cols"]) and len(res.right_cols) == len(want["right_cols"])
+    for got, w in zip(res.left_cols, want["left_cols"]):
+        assert np.array_equal(bits(got.cpu().numpy())[order], bits(w))
+    for got, w in zip(res.right_cols, want["right_cols"]):
+        assert np.array_equal(bits(got.cpu().numpy())[order], bits(w))
+    return res.nrows
+
+
+@pytest.mark.parametrize("how", ["left", "right", "outer"])
+@pytest.mark.parametrize("P", [1, 8])
+def test_outer_joins_on_two_keys(how, P):
+    rng, (a, b, _), (ra, rb, _) = _tables(74, 60_000, 80_000)
+    left = [a, b, rng.random(a.size)]
+    right = [rng.random(ra.size), rb, ra]
+    inner = _run_and_check(left, right, [0, 1], [2, 1], P)
+    assert _run_how(left, right, [0, 1], [2, 1], P, how) > inner
+
+
+@pytest.mark.parametrize("how", ["left", "right", "outer"])
+def test_outer_joins_on_three_keys_mixed_types(how):
+    rng, (a, b, c), (ra, rb, rc) = _tables(75, 30_000, 50_000)
+    left = [rng.random(a.size).astype(np.float32), c, a, b]
+    right = [rb, ra, rc, rng.integers(0, 9, ra.size).astype(np.int64)]
+    _run_how(left, right, [2, 3, 1], [1, 0, 2], 8, how)
+
+
+@pytest.mark.parametrize("how", ["left", "outer"])
+def test_outer_rows_whose_only_candidates_collide(monkeypatch, how):
+    # with the weak surrogate a left row can have candidates but no true
+    # partner: it must come out unmatched, once
+    monkeypatch.setenv("MDJ_TEST_WEAK_TUPLE_HASH", "1")
+    rng, (a, b, _), (ra, rb, _) = _tables(76, 20_000, 20_000)
+    _run_how([a, b, rng.random(a.size)], [ra, rb + 40, rng.random(ra.size)], [0, 1], [0, 1], 8, how)
+
+
+@pytest.mark.parametrize("how", ["left", "right", "outer"])
+def test_outer_on_tuples_with_empty_or_unmatched_sides(how):
+    a = np.arange(1000, dtype=np.int64)
+    b = np.zeros(1000, np.int64)
+    assert _run_how([a, b], [a, b + 1], [0, 1], [0, 1], 4, how) == (2000 if how == "outer" else 1000)
+    n = _run_how([a[:0], b[:0]], [a, b], [0, 1], [0, 1], 4, how)
+    assert n == (0 if how == "left" else 1000)
