@@ -85,7 +85,7 @@ __global__ void k_expand(const uint32_t *__restrict__ offL, const uint32_t *__re
 // 16-byte-aligned bases, so items stage them by bulk copies.  The item count
 // is read from *nitems_dev (no work when it exceeds `ulim`: k_expand has set
 // FLAG_ITEMS and the host reruns the join with exact arrays).
-template <typename KeyT, bool HAVE_OFFSETS, int NT>
+template <typename KeyT, bool HAVE_OFFSETS, int NT, bool COUNT = false>
 __global__ void __launch_bounds__(NT, 1024 / NT)
     k_join_write(JSide L, JSide R, const Item *__restrict__ desc, const uint64_t *nitems_dev, uint32_t ulim,
                  uint32_t cap, uint32_t *ticket, unsigned long long *state, uint64_t *__restrict__ item_off,
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
       nx = atomicAdd(ticket, 1u);
       if (nx < nitems) dn = desc[nx];
     }
-    if (!join_item<KeyT, HAVE_OFFSETS, NT>(smem, cap, L, R, d, it, rs, out, js, bulk != 0, phase)) break;
+    if (!join_item<KeyT, HAVE_OFFSETS, NT, COUNT>(smem, cap, L, R, d, it, rs, out, js, bulk != 0, phase)) break;
     if (tid == 0) {
       s_it = nx;
       if (nx < nitems) s_item = dn;
@@ -272,9 +272,9 @@ int run_join_t(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, 
   const uint32_t rch = (uint32_t)kWPF * NT;
   const uint32_t ulim = exact_items ? exact_items : item_bound(plan.nbuckets, Ls.nrows, Rs.nrows, plan.cap, rch);
   const int ordered = force_ordered || ordered_output() ? 1 : 0;
-  // the optimistic output buffer; nothing below waits for the device until
-  // the join has run
-  const uint64_t cap_rows = output_capacity_hint(Ls.nrows, Rs.nrows);
+  // the optimistic output buffer (none for two-pass output); nothing below
+  // waits for the device until the join has run
+  const uint64_t cap_rows = force_ordered ? 0 : output_capacity_hint(Ls.nrows, Rs.nrows);
   mdj_result r;
   JOut o;
   MDJ_TRY(alloc_result(ws, Ls, Rs, sizeof(KeyT), cap_rows, &r, &o));
@@ -299,6 +299,66 @@ int run_join_t(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, 
   const uint64_t *nitems_dev = bucket_items + plan.nbuckets;
 
   const size_t sm = WriteLayout<KeyT>(plan.cap).total;  // ~105 KB at cap 4096: two blocks per SM
+  if (force_ordered) {
+    // two-pass ordered output (the batched joins): a count pass records every
+    // item's rows, a scan places the items in item order (item_off[ulim] is
+    // `total`, which receives the sum), and the exact pass writes each item
+    // at its offset; no item waits on another
+    int grid;
+    unsigned long long host_total = 0;
+    uint64_t host_items = 0;
+    int host_flags[FLAG_WORDS] = {0, 0, 0, 0};
+    rc = cuda_status(cudaMemsetAsync(item_off, 0, ((size_t)ulim + 1) * 8, s));
+    if (rc == MDJ_OK) rc = resident_grid(k_join_write<KeyT, false, NT, true>, sm, ulim, &grid, NT);
+    if (rc == MDJ_OK) {
+      TraceScope tr("join_count", s);
+      k_join_write<KeyT, false, NT, true><<<grid, NT, sm, s>>>(to_jside(Ls), to_jside(Rs), desc, nitems_dev, ulim,
+                                                            plan.cap, ticket, state, item_off, total, 0, flags, 0,
+                                                            0, bulk_ok(Ls), o);
+      rc = cuda_status(cudaGetLastError());
+    }
+    if (rc == MDJ_OK) rc = exclusive_scan_u64(ws, item_off, item_off, (size_t)ulim + 1);
+    if (rc == MDJ_OK) rc = cuda_status(cudaMemcpyAsync(&host_total, total, 8, cudaMemcpyDeviceToHost, s));
+    if (rc == MDJ_OK)
+      rc = cuda_status(cudaMemcpyAsync(host_flags, flags, sizeof host_flags, cudaMemcpyDeviceToHost, s));
+    if (rc == MDJ_OK) rc = cuda_status(cudaMemcpyAsync(&host_items, nitems_dev, 8, cudaMemcpyDeviceToHost, s));
+    if (rc == MDJ_OK) rc = cuda_status(cudaStreamSynchronize(s));
+    if (rc == MDJ_OK && host_flags[FLAG_TIMEOUT]) rc = MDJ_ERR_DEVICE_TIMEOUT;
+    mdj_result_release(&r, ws.allocator(), (void *)s);
+    if (rc != MDJ_OK) return rc;
+    if (host_flags[FLAG_ITEMS]) {
+      if (host_items >= (1ull << 31)) return MDJ_ERR_TOO_LARGE;
+      ws.give_back(desc);
+      ws.give_back(bucket_items);
+      ws.give_back(state);
+      return run_join_t<KeyT, NT>(ws, Ls, Rs, plan, res, force_ordered, map, (uint32_t)host_items);
+    }
+    const uint64_t m = host_total;
+    MDJ_TRY(alloc_result(ws, Ls, Rs, sizeof(KeyT), m, &r, &o));
+    if (m > 0) {
+      rc = resident_grid(k_join_write<KeyT, true, NT>, sm, ulim, &grid, NT);
+      if (rc == MDJ_OK) rc = cuda_status(cudaMemsetAsync(ticket, 0, 4, s));
+      if (rc == MDJ_OK) {
+        TraceScope tr("join_write_exact", s);
+        k_join_write<KeyT, true, NT><<<grid, NT, sm, s>>>(to_jside(Ls), to_jside(Rs), desc, nitems_dev, ulim,
+                                                       plan.cap, ticket, state, item_off, total, m, flags, 0, 0,
+                                                       bulk_ok(Ls), o);
+        rc = cuda_status(cudaGetLastError());
+      }
+      if (rc != MDJ_OK) {
+        mdj_result_release(&r, ws.allocator(), (void *)s);
+        return rc;
+      }
+    }
+    r.nrows = m;
+    *res = r;
+    if (map) {
+      map->bucket_items = bucket_items;
+      map->item_out = item_off;
+      map->nitems = (uint32_t)host_items;
+    }
+    return MDJ_OK;
+  }
   int grid;
   rc = resident_grid(k_join_write<KeyT, false, NT>, sm, ulim, &grid, NT);
   if (rc == MDJ_OK) {

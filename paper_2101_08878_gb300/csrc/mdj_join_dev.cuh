@@ -288,7 +288,9 @@ struct Resv {
 // `phase` is the mbarrier's phase, kept by every thread.  Leaves every thread
 // past the write, with no barrier after it; returns false if a bulk-copy
 // wait ran out (FLAG_TIMEOUT and FLAG_ABORT are then set).
-template <typename KeyT, bool HAVE_OFFSETS, int NT>
+// COUNT: build and probe only; the item's output row count goes to
+// item_off[it] (the count pass of two-pass ordered output).
+template <typename KeyT, bool HAVE_OFFSETS, int NT, bool COUNT = false>
 __device__ __forceinline__ bool join_item(unsigned char *smem, uint32_t cap, const JSide &L, const JSide &R,
                                           const Item &d, uint32_t it, const Resv &rs, const JOut &out,
                                           JoinShared &js, bool bulk, uint32_t &phase) {
@@ -423,7 +425,7 @@ __device__ __forceinline__ bool join_item(unsigned char *smem, uint32_t cap, con
   for (int j = 0; j < kWPF; j++) {
     rr[j] = 0;
     rp[j] = 0;
-    if (ch[j]) {
+    if (!COUNT && ch[j]) {
       const uint32_t r = d.rbeg + j * kWT + tid;
       rr[j] = R.rid ? R.rid[r] : r;
       if (rpw == 8) rp[j] = ((const uint64_t *)R.cols[0])[r];
@@ -455,7 +457,10 @@ __device__ __forceinline__ bool join_item(unsigned char *smem, uint32_t cap, con
     if (lane == 0) {
       const uint64_t item_total = S + M;
       uint64_t base;
-      if (HAVE_OFFSETS) {
+      if (COUNT) {
+        rs.item_off[it] = item_total;
+        base = ~0ull;
+      } else if (HAVE_OFFSETS) {
         base = rs.item_off[it];
       } else {
         if (rs.ordered) {
@@ -475,6 +480,7 @@ __device__ __forceinline__ bool join_item(unsigned char *smem, uint32_t cap, con
     }
   }
   __syncthreads();
+  if (COUNT) return true;
 
   // 6. write (an item that overflows the optimistic buffer writes nothing:
   // the exact second pass places it)

@@ -91,6 +91,22 @@ def test_batch_ragged_pairs_match_oracle(seed):
         _check_pair(res_np, po, i, pair, lo, ro)
 
 
+def test_batch_pair_ranges_are_fixed_and_survive_a_small_item_bound(monkeypatch):
+    # two-pass ordered output: item offsets from a scan of counted items, so
+    # every pair's range is the same in every run (rows within a pair follow
+    # the unstable segmented scatter); a bound of one item forces the rerun
+    # with exact arrays and must give the same ranges and rows
+    pairs = _ragged_pairs(3)
+    _, a_np, po_a, lo, ro = _run_batch(pairs)
+    _, b_np, po_b, _, _ = _run_batch(pairs)
+    monkeypatch.setenv("MDJ_TEST_ITEM_BOUND", "1")
+    _, c_np, po_c, _, _ = _run_batch(pairs)
+    assert list(po_a) == list(po_b) == list(po_c)
+    for res_np, po in ((a_np, po_a), (b_np, po_b), (c_np, po_c)):
+        for i, pair in enumerate(pairs):
+            _check_pair(res_np, po, i, pair, lo, ro)
+
+
 @pytest.mark.parametrize("table_rows,fill_pct", [(1024, 50), (2048, 85), (8192, 95), (8192, 30)])
 def test_batch_tuning_does_not_change_rows(table_rows, fill_pct):
     pairs = [datagen.match_fraction_tables(n, 2 * n, 0.5, seed=n) for n in (100, 5_000, 60_000, 150_000)]
