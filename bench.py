@@ -272,8 +272,7 @@ def run_gpu(args):
 
     stream = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    mdj.profile_reset()
-    mdj.profile_enable(True)
+    # the timed region: K steps without launch tracing (value, ms_per_step)
     with ClockSampler(local) as clk:
         barrier()
         torch.cuda.synchronize()
@@ -284,9 +283,22 @@ def run_gpu(args):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
+    ms_total = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    # K more steps with every launch bracketed by CUDA events on its stream:
+    # the per-kernel times (rooflines, launch list, launch count)
+    mdj.profile_reset()
+    mdj.profile_enable(True)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        res = step()
+        del res
+    t1.record(stream)
+    torch.cuda.synchronize()
     mdj.profile_enable(False)
     prof = mdj.profile_collect()
-    ms_total = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    ms_traced_step = t0.elapsed_time(t1) / args.steps
     ms_step = ms_total / args.steps
     value = whole_job_rate(N_LEFT + N_RIGHT, world, ms_step / 1e3)
 
@@ -356,6 +368,9 @@ def run_gpu(args):
                    "output_rows": m_expect, "seed": SEED, "l2": "inputs (3.2 GB) larger than L2; no flush",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline, "step_roofline": step_roof, "kernels": kernels, "gpu_launches": launches,
+        "timing": {"value_from": f"{args.steps} steps without launch tracing",
+                   "kernels_from": f"{args.steps} further steps with CUDA events around every launch "
+                                   f"({round(ms_traced_step, 4)} ms per step with the tracing)"},
         "e2e": e2e, "clocks": clk.summary(),
     }
     if host_tables is not None:

@@ -36,14 +36,17 @@ namespace {
 
 // Items of bucket b: ceil(nl / cap) build chunks x ceil(nr / rch) probe chunks
 // (0 when either side is empty).
+// The thread past the last bucket also clears the join's counters `tail`
+// (total, ticket, flags, item count: five words).
 __global__ void k_items(const uint32_t *__restrict__ offL, const uint32_t *__restrict__ offR, uint32_t nb, uint32_t cap,
-                        uint32_t rch, uint64_t *__restrict__ items) {
+                        uint32_t rch, uint64_t *__restrict__ items, unsigned long long *__restrict__ tail) {
   uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b < nb) {
     uint64_t nl = offL[b + 1] - offL[b], nr = offR[b + 1] - offR[b];
     items[b] = (nl && nr) ? ((nl + cap - 1) / cap) * ((nr + rch - 1) / rch) : 0ull;
   } else if (b == nb) {
     items[nb] = 0;
+    for (int w = 0; w < 5; w++) tail[w] = 0;
   }
 }
 
@@ -98,6 +101,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
   const uint32_t tid = threadIdx.x;
   const uint64_t nit = *nitems_dev;
   const uint32_t nitems = nit > ulim ? 0u : (uint32_t)nit;
+  if (blockIdx.x == 0 && threadIdx.x == 0) total[4] = nit;  // read back with the total and the flags
   const Resv rs = {state, item_off, total, capacity, flags, withhold_first, ordered};
   uint32_t phase = 0;
   if (tid == 0) {
@@ -165,14 +169,15 @@ int resident_grid(KernelT kernel, size_t smem, uint64_t nitems, int *grid, int t
 // device at (*item_off)[nb] (per-bucket item prefix in *item_off), and a count
 // above ulim sets FLAG_ITEMS instead of writing descriptors.
 int make_items(Workspace &ws, const Side &Ls, const Side &Rs, uint32_t nb, uint32_t cap, uint32_t rch, uint32_t ulim,
-               int *flags, Item **desc, uint64_t **item_off_out) {
+               unsigned long long *tail, Item **desc, uint64_t **item_off_out) {
+  int *flags = (int *)(tail + 2);
   cudaStream_t s = ws.stream();
   uint64_t *item_off = (uint64_t *)ws.get((size_t)(nb + 1) * 8);
   *desc = (Item *)ws.get((size_t)(ulim ? ulim : 1) * sizeof(Item));
   if (!item_off || !*desc) return MDJ_ERR_OOM;
   {
     TraceScope tr("join_items", s);
-    k_items<<<(nb + 1 + 255) / 256, 256, 0, s>>>(Ls.off, Rs.off, nb, cap, rch, item_off);
+    k_items<<<(nb + 1 + 255) / 256, 256, 0, s>>>(Ls.off, Rs.off, nb, cap, rch, item_off, tail);
   }
   MDJ_LAUNCH_CHECK();
   MDJ_TRY(exclusive_scan_u64(ws, item_off, item_off, nb + 1));
@@ -265,6 +270,18 @@ struct ItemMap {
   uint32_t nitems = 0;
 };
 
+// The join's counters in one read: output total, flags, item count.
+int read_tail(const unsigned long long *tail, cudaStream_t s, unsigned long long *total, int *flags,
+              uint64_t *items) {
+  unsigned long long t[5];
+  MDJ_CUDA_TRY(cudaMemcpyAsync(t, tail, sizeof t, cudaMemcpyDeviceToHost, s));
+  MDJ_CUDA_TRY(cudaStreamSynchronize(s));
+  *total = t[0];
+  memcpy(flags, &t[2], FLAG_WORDS * sizeof(int));
+  *items = t[4];
+  return MDJ_OK;
+}
+
 template <typename KeyT, int NT>
 int run_join_t(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, mdj_result *res,
                bool force_ordered = false, ItemMap *map = nullptr, uint32_t exact_items = 0) {
@@ -278,20 +295,19 @@ int run_join_t(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, 
   mdj_result r;
   JOut o;
   MDJ_TRY(alloc_result(ws, Ls, Rs, sizeof(KeyT), cap_rows, &r, &o));
-  // state[ulim] | item_off[ulim] | total | ticket | flags
-  const size_t words = 2 * (size_t)ulim + 4;
+  // state[ulim] | item_off[ulim] | total | ticket | flags (2 words) | item count
+  const size_t words = 2 * (size_t)ulim + 5;
   unsigned long long *state = (unsigned long long *)ws.get(words * 8);
   int rc = state ? MDJ_OK : MDJ_ERR_OOM;
   uint64_t *item_off = state ? (uint64_t *)(state + ulim) : nullptr;
   unsigned long long *total = state ? state + 2 * (size_t)ulim : nullptr;
   uint32_t *ticket = (uint32_t *)(total + 1);
   int *flags = (int *)(total + 2);
-  // the look-back slots start empty (ordered); the counters always
+  // the look-back slots start empty (ordered); k_items clears the counters
   if (rc == MDJ_OK && ordered) rc = cuda_status(cudaMemsetAsync(state, 0, (size_t)ulim * 8, s));
-  if (rc == MDJ_OK) rc = cuda_status(cudaMemsetAsync(total, 0, 4 * 8, s));
   Item *desc = nullptr;
   uint64_t *bucket_items = nullptr;
-  if (rc == MDJ_OK) rc = make_items(ws, Ls, Rs, plan.nbuckets, plan.cap, rch, ulim, flags, &desc, &bucket_items);
+  if (rc == MDJ_OK) rc = make_items(ws, Ls, Rs, plan.nbuckets, plan.cap, rch, ulim, total, &desc, &bucket_items);
   if (rc != MDJ_OK) {
     mdj_result_release(&r, ws.allocator(), (void *)s);
     return rc;
@@ -318,11 +334,7 @@ int run_join_t(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, 
       rc = cuda_status(cudaGetLastError());
     }
     if (rc == MDJ_OK) rc = exclusive_scan_u64(ws, item_off, item_off, (size_t)ulim + 1);
-    if (rc == MDJ_OK) rc = cuda_status(cudaMemcpyAsync(&host_total, total, 8, cudaMemcpyDeviceToHost, s));
-    if (rc == MDJ_OK)
-      rc = cuda_status(cudaMemcpyAsync(host_flags, flags, sizeof host_flags, cudaMemcpyDeviceToHost, s));
-    if (rc == MDJ_OK) rc = cuda_status(cudaMemcpyAsync(&host_items, nitems_dev, 8, cudaMemcpyDeviceToHost, s));
-    if (rc == MDJ_OK) rc = cuda_status(cudaStreamSynchronize(s));
+    if (rc == MDJ_OK) rc = read_tail(total, s, &host_total, host_flags, &host_items);
     if (rc == MDJ_OK && host_flags[FLAG_TIMEOUT]) rc = MDJ_ERR_DEVICE_TIMEOUT;
     mdj_result_release(&r, ws.allocator(), (void *)s);
     if (rc != MDJ_OK) return rc;
@@ -371,10 +383,7 @@ int run_join_t(Workspace &ws, const Side &Ls, const Side &Rs, const Plan &plan, 
   unsigned long long host_total = 0;
   uint64_t host_items = 0;
   int host_flags[FLAG_WORDS] = {0, 0, 0, 0};
-  if (rc == MDJ_OK) rc = cuda_status(cudaMemcpyAsync(&host_total, total, 8, cudaMemcpyDeviceToHost, s));
-  if (rc == MDJ_OK) rc = cuda_status(cudaMemcpyAsync(host_flags, flags, sizeof host_flags, cudaMemcpyDeviceToHost, s));
-  if (rc == MDJ_OK) rc = cuda_status(cudaMemcpyAsync(&host_items, nitems_dev, 8, cudaMemcpyDeviceToHost, s));
-  if (rc == MDJ_OK) rc = cuda_status(cudaStreamSynchronize(s));
+  if (rc == MDJ_OK) rc = read_tail(total, s, &host_total, host_flags, &host_items);
   if (rc == MDJ_OK && host_flags[FLAG_TIMEOUT]) rc = MDJ_ERR_DEVICE_TIMEOUT;
   if (rc == MDJ_OK && host_flags[FLAG_ITEMS]) {
     // more items than the bound: again, with arrays of the exact count

@@ -315,10 +315,13 @@ __global__ void __launch_bounds__(kTotThreads) k_tot(const KeyT *__restrict__ ke
 }
 
 // cur[b] = off[b * F2]: the first row of pass-1 bucket b
+// Pass-1 cursors (the first row of every pass-1 bucket) and, for two-level
+// plans, pass 2's: the first row of every sub-bucket (cur2 may be NULL).
 __global__ void k_pass1_cursors(const uint32_t *__restrict__ off, uint32_t F1, uint32_t F2,
-                                uint32_t *__restrict__ cur) {
+                                uint32_t *__restrict__ cur, uint32_t *__restrict__ cur2, uint32_t nsub) {
   const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b < F1) cur[b] = off[(size_t)b * F2];
+  if (cur2 && b < nsub) cur2[b] = off[b];
 }
 
 // Persistent: block b takes tiles b, b + gridDim.x, ...  Once a tile is
@@ -584,9 +587,11 @@ int shuffle_pass(Workspace &ws, const KeyT *keys, uint32_t n, const BucketSpec &
 // The merge's partition of one side with the unstable passes, first half:
 // count the final sub-buckets, scan them into `off`, then the only pass
 // (F2 == 1) or pass 1 (two-level plans) into freshly allocated `out`.
+// cur2 (two-level plans): pass 2's cursors, allocated here and filled from
+// the offsets by the same kernel as pass 1's.
 template <typename KeyT>
 int shuffle_count_pass1_t(Workspace &ws, const mdj_table *t, int32_t key_col, const Plan &plan, uint32_t *off,
-                          TableBufs *out) {
+                          TableBufs *out, uint32_t **cur2 = nullptr) {
   cudaStream_t s = ws.stream();
   MDJ_TRY(set_shuffle_attrs<KeyT>());
   const uint32_t n = (uint32_t)t->nrows;
@@ -602,6 +607,7 @@ int shuffle_count_pass1_t(Workspace &ws, const mdj_table *t, int32_t key_col, co
   if (n == 0) return MDJ_OK;
   uint32_t *cur = (uint32_t *)ws.get((size_t)(nsub + 1) * 4);
   if (!cur) return MDJ_ERR_OOM;
+  if (cur2 && !(*cur2 = (uint32_t *)ws.get((size_t)(nsub + 1) * 4))) return MDJ_ERR_OOM;
   {
     const size_t smem = (size_t)nsub * 4;
     int per_sm = 0;
@@ -618,7 +624,8 @@ int shuffle_count_pass1_t(Workspace &ws, const mdj_table *t, int32_t key_col, co
   {
     // pass-1 cursors: the first row of every pass-1 bucket
     TraceScope tr("pass1_cursors", s);
-    k_pass1_cursors<<<(F1 + 255) / 256, 256, 0, s>>>(off, F1, plan.F2, cur);
+    const uint32_t nk = cur2 ? (F1 > nsub ? F1 : nsub) : F1;
+    k_pass1_cursors<<<(nk + 255) / 256, 256, 0, s>>>(off, F1, plan.F2, cur, cur2 ? *cur2 : nullptr, nsub);
   }
   MDJ_LAUNCH_CHECK();
   ColMove cm = make_move(t, key_col, src, out->cols);
@@ -631,16 +638,11 @@ int shuffle_count_pass1_t(Workspace &ws, const mdj_table *t, int32_t key_col, co
 // Second half of a two-level plan: pass 2 from the pass-1 copy `p1` into
 // freshly allocated `fin` (sub-bucket offsets `off` from the first half).
 template <typename KeyT>
-int shuffle_pass2_t(Workspace &ws, const mdj_table *t, int32_t key_col, const Plan &plan, const uint32_t *off,
+int shuffle_pass2_t(Workspace &ws, const mdj_table *t, int32_t key_col, const Plan &plan, uint32_t *cur,
                     const TableBufs &p1, TableBufs *fin) {
-  cudaStream_t s = ws.stream();
   const uint32_t n = (uint32_t)t->nrows;
-  const uint32_t nsub = plan.nbuckets;
   MDJ_TRY(alloc_table_bufs(ws, t, fin, true));
   if (n == 0) return MDJ_OK;
-  uint32_t *cur = (uint32_t *)ws.get((size_t)(nsub + 1) * 4);
-  if (!cur) return MDJ_ERR_OOM;
-  MDJ_CUDA_TRY(cudaMemcpyAsync(cur, off, (size_t)nsub * 4, cudaMemcpyDeviceToDevice, s));
   ColMove cm2 = make_move(t, key_col, p1.cols, fin->cols);
   MDJ_TRY((shuffle_pass<KeyT, true>(ws, (const KeyT *)p1.cols[key_col], n, make_spec(plan.P, plan.S, 1), 0, plan.F2,
                                     cur, cm2, p1.rid, fin->rid)));
@@ -653,8 +655,9 @@ int shuffle_side_t(Workspace &ws, const mdj_table *t, int32_t key_col, const Pla
                    TableBufs *fin) {
   if (plan.F2 == 1) return shuffle_count_pass1_t<KeyT>(ws, t, key_col, plan, off, fin);
   TableBufs p1;
-  MDJ_TRY(shuffle_count_pass1_t<KeyT>(ws, t, key_col, plan, off, &p1));
-  MDJ_TRY(shuffle_pass2_t<KeyT>(ws, t, key_col, plan, off, p1, fin));
+  uint32_t *cur2 = nullptr;
+  MDJ_TRY(shuffle_count_pass1_t<KeyT>(ws, t, key_col, plan, off, &p1, &cur2));
+  MDJ_TRY(shuffle_pass2_t<KeyT>(ws, t, key_col, plan, cur2, p1, fin));
   release_table_bufs(ws, t, &p1);
   return MDJ_OK;
 }
