@@ -1,6 +1,7 @@
 /*
  * mdj.h - C ABI of libmdj.so: a GB300 (sm_103a) hash-partitioned shuffle and
- * inner hash join of two key/payload tables.
+ * hash join of two key/payload tables (inner, and its left / right / outer
+ * and key-tuple variants).
  *
  * What the calls compute comes from the cuDF merge workload of arXiv 2101.08878
  * (Sec. V-B "cuDF Merge", Fig. 8, and Sec. V-C, Fig. 9(b,c)): tables are
@@ -18,9 +19,10 @@
  *    HOST memory.  Input columns are read-only and remain owned by the caller.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *    Every call is asynchronous on that stream, except mdj_join / mdj_merge /
- *    mdj_count_checksum and the batch calls, which read small counts back to
- *    the host (the number of work items, then the output row count: stream
- *    synchronisations) to size their outputs.
+ *    mdj_count_checksum, the batch, stream, tuple and host calls, which read
+ *    small counts back to the host to size their outputs (the joins: the output
+ *    row count, with the work-item count and flags, in one stream
+ *    synchronisation; one more pass when an optimistic size was too small).
  *  - Workspace and join outputs come from the caller's allocator (mdj_allocator);
  *    a NULL allocator means cudaMallocAsync / cudaFreeAsync on `stream`.
  *  - Keys are signed integers (MDJ_I32 or MDJ_I64); both sides of a join must use
