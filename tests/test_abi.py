@@ -270,6 +270,26 @@ def test_workspace_give_back_keeps_arena_chunks(tmp_path):
     assert out == ["2", "1", "1", "1", "0"]
 
 
+def test_merge_multi_how_refuses_bad_arguments_before_device_work(lib):
+    # an unknown join type, or no key columns, is refused before any device
+    # work (the column pointers are stand-ins, never dereferenced)
+    from paper_2101_08878_gb300.mdj import MdjCol, MdjResult, MdjTable
+    cols = (MdjCol * 2)()
+    cols[0].data = ctypes.c_void_p(0x1000)
+    cols[0].dtype = 2
+    cols[1].data = ctypes.c_void_p(0x2000)
+    cols[1].dtype = 4
+    tab = MdjTable(cols, 2, 1000)
+    keys = (ctypes.c_int32 * 1)(0)
+    out = MdjResult()
+    for how in (-1, 4, 99):
+        assert lib.mdj_merge_multi_how(ctypes.byref(tab), keys, ctypes.byref(tab), keys, 1, 8, how, None, None,
+                                       ctypes.byref(out)) == -1
+    assert lib.mdj_merge_multi_how(ctypes.byref(tab), keys, ctypes.byref(tab), keys, 0, 8, 3, None, None,
+                                   ctypes.byref(out)) == -1
+    assert out.nrows == 0
+
+
 def test_noalloc_size_limit_at_p8(lib):
     # mdj_partition_noalloc's fixed array holds P*T + ceil(P*T/4096) + P + 1
     # words (T = ceil(nrows / 4096)) of 4 Mi; at P = 8 that admits
