@@ -107,6 +107,20 @@ def test_batch_pair_ranges_are_fixed_and_survive_a_small_item_bound(monkeypatch)
             _check_pair(res_np, po, i, pair, lo, ro)
 
 
+def test_batch_int32_keys_and_float32_payloads():
+    # the 4-byte key and payload instantiations of the count and exact passes
+    rng = np.random.default_rng(12)
+    pairs = []
+    for i in range(24):
+        nl, nr = int(rng.integers(1, 40_000)), int(rng.integers(1, 40_000))
+        pairs.append(datagen.random_tables(nl, nr, int(rng.choice([40, 20_000, 10**9])), seed=700 + i,
+                                           key_dtype=np.int32, pay_dtype=np.float32))
+    res, res_np, po, lo, ro = _run_batch(pairs)
+    assert res.key.dtype == torch.int32 and res.left_cols[0].dtype == torch.float32
+    for i, pair in enumerate(pairs):
+        _check_pair(res_np, po, i, pair, lo, ro)
+
+
 @pytest.mark.parametrize("table_rows,fill_pct", [(1024, 50), (2048, 85), (8192, 95), (8192, 30)])
 def test_batch_tuning_does_not_change_rows(table_rows, fill_pct):
     pairs = [datagen.match_fraction_tables(n, 2 * n, 0.5, seed=n) for n in (100, 5_000, 60_000, 150_000)]
