@@ -97,6 +97,7 @@ constexpr int kGT = 512;                   // threads of a grouping block
 constexpr uint32_t kGCap = 4096;           // build rows of a shared-memory group table
 constexpr int kGRows = kGCap / kGT;        // build rows per thread
 constexpr uint32_t kGTab = 2 * kGCap;      // slots of the largest shared-memory table
+static_assert(kGTab * 4 >= kGCap * 8, "the slot table stages a sub-bucket's 8-byte keys");
 constexpr uint32_t kProbeChunk = 65536;    // probe rows per grouping unit
 constexpr int kHT = 256;                   // threads of a global-table block
 constexpr uint32_t kHChunk = 8192;         // rows per global-table unit
@@ -356,13 +357,20 @@ __global__ void __launch_bounds__(kGT, 2)
       pr[k] = base[rep] + rank;
     }
     __syncthreads();
-    stage_column<uint32_t>(o.grid, L.rid, lb, nl, pr, smem);
     if (o.gkey) {
-      if (sizeof(KeyT) == 8)
-        stage_column<uint64_t>((uint64_t *)o.gkey, (const uint64_t *)L.key, lb, nl, pr, smem);
-      else
-        stage_column<uint32_t>((uint32_t *)o.gkey, (const uint32_t *)L.key, lb, nl, pr, smem);
+      // the keys are still in shared memory: staged into the dead slot table
+      // (kGTab words hold kGCap keys) rather than read again from memory
+      KeyT *st = (KeyT *)(smem + group_slots_at<KeyT>());
+#pragma unroll
+      for (int k = 0; k < kGRows; k++) {
+        const uint32_t i = threadIdx.x + k * kGT;
+        if (i < nl) st[pr[k]] = keys[i];
+      }
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < nl; i += kGT) ((KeyT *)o.gkey)[lb + i] = st[i];
+      __syncthreads();
     }
+    stage_column<uint32_t>(o.grid, L.rid, lb, nl, pr, smem);
 #pragma unroll 1
     for (int c = 0; c < L.ncols; c++) {
       if (L.width[c] == 8)
